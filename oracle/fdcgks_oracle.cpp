@@ -1,0 +1,1147 @@
+// FD-CGKS reference oracle: plain, slow, FP64 CPU implementation.
+//
+// TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call, link or
+// load this file: only tests/, __graft_entry__.smoke() and bench.py's
+// cpu_baseline / --impl reference legs use it.  It shares no code, header,
+// table or helper with the CUDA library in paper_2606_17772_gb300/.
+//
+// Paper: "Finite Difference Implementation of a High-order Space-Time Coupled
+// Compact Gas-Kinetic Scheme" (Zhao, Chen, Xu).  Every function cites the
+// section / equation it follows.  The kinetic interface solution (App. A) is
+// only referenced by the paper; it is restated here from the BGK integral
+// solution Eq. (eq:integral_f) with the usual Chapman-Enskog initial data and
+// linear equilibrium, and every velocity moment is taken by generic
+// polynomial algebra over Maxwellian moment tables (no hand-expanded moment
+// formulas), so that it can be checked against quadrature by eye.
+//
+// Readings of the paper that this file takes (listed with reasons in the
+// design notes of the repository):
+//   * 6-4 flux low-order part carries the factor 1/6 (Eq. fd-conservative-flux-2).
+//   * chi in Eqs. (fd-conservative-flux-1/2) is the interface path function
+//     chi_{j+1/2} = min(chi^{l,rho}, chi^{r,rho}) of Sec. 3.2.
+//   * GENO constants: variant 0 = Sec. 3.2 text (r=2, eps=1e-12, d=(8,1,1) on
+//     each set's first sub-stencil); variant 1 = App. D (r=3, eps=1e-15,
+//     d=8 on the central sub-stencil); variant 2 = linear (chi = 1).
+//   * Node sub-stencils numbered as in Sec. 3.2 (central first).
+//   * GENO weights chi, omega_k are applied to the derivative as well.
+//   * Component-wise reconstruction of conservative variables.
+//   * tau_0 of Eq. (eq:W-model) = the interface collision time tau.
+//   * W^{l,r}(t) of Eq. (eq:W-model): free transport of the one-sided
+//     Chapman-Enskog distribution over the whole velocity space.
+//   * Node j's averaged gradient uses its own side: (W~^l_{j+1/2} - W~^r_{j-1/2})/h.
+//   * Gradient base of Eq. (eq-interface-update): re-evaluated from the
+//     interface solution at t^n (reading B, default) or the stored gradient
+//     (reading A, grad_base = 1).
+//   * Flux fit uses delta = dt/2 and dt at both S2O4 stages.
+//   * Collision time tau = c1 dt + mu/p0 + c2 dt |pl-pr|/(pl+pr) (interfaces),
+//     tau = c1 dt + mu/p at nodes.
+//   * Node placement: primary nodes at cell centres, dual nodes at cell
+//     corners; n dual nodes per periodic direction, n+1 per bounded one.
+//     Ghost layers by periodic wrap, mirror (symmetry / no-slip wall) or
+//     constant extrapolation (transmissive).  Dual nodes on a no-slip wall
+//     have their velocity set to zero after each stage.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+namespace {
+
+const double PI = 3.14159265358979323846;
+
+// ---------------------------------------------------------------------------
+// Polynomials in the particle velocity (u, v) and xi^2 (App. A1)
+// ---------------------------------------------------------------------------
+struct Mono {
+  int a, b, c;   // u^a v^b (xi^2)^c
+  double coef;
+};
+typedef std::vector<Mono> Poly;
+
+Poly pconst(double s) { return Poly{{0, 0, 0, s}}; }
+Poly pu() { return Poly{{1, 0, 0, 1.0}}; }
+Poly pv() { return Poly{{0, 1, 0, 1.0}}; }
+
+Poly padd(const Poly& p, const Poly& q) {
+  Poly r = p;
+  r.insert(r.end(), q.begin(), q.end());
+  return r;
+}
+Poly pscale(const Poly& p, double s) {
+  Poly r = p;
+  for (auto& m : r) m.coef *= s;
+  return r;
+}
+// sum the coefficients of equal monomials
+Poly pmerge(const Poly& p) {
+  Poly r;
+  for (const auto& x : p) {
+    bool found = false;
+    for (auto& y : r)
+      if (y.a == x.a && y.b == x.b && y.c == x.c) { y.coef += x.coef; found = true; break; }
+    if (!found) r.push_back(x);
+  }
+  return r;
+}
+Poly pmul(const Poly& p, const Poly& q) {
+  Poly r;
+  r.reserve(p.size() * q.size());
+  for (const auto& x : p)
+    for (const auto& y : q) r.push_back({x.a + y.a, x.b + y.b, x.c + y.c, x.coef * y.coef});
+  return pmerge(r);
+}
+
+// collision invariants psi = (1, u, v, (u^2+v^2+xi^2)/2)  (App. A1)
+const Poly& psi(int k) {
+  static const Poly P[4] = {pconst(1.0), pu(), pv(), Poly{{2, 0, 0, 0.5}, {0, 2, 0, 0.5}, {0, 0, 1, 0.5}}};
+  return P[k];
+}
+
+// a slope polynomial a = sum_l a_l psi_l
+Poly slope_poly(const double a[4]) {
+  Poly r;
+  for (int l = 0; l < 4; ++l) r = padd(r, pscale(psi(l), a[l]));
+  return pmerge(r);
+}
+
+// ---------------------------------------------------------------------------
+// Maxwellian g = rho (lam/pi)^((K+2)/2) exp(-lam((u-U)^2+(v-V)^2+xi^2)) and its
+// moments (App. A1).  Half-space moments of the normal component use the
+// erfc / exp seeds; higher ones follow the Gaussian moment recursion.
+// ---------------------------------------------------------------------------
+const int NM = 12;
+struct Maxwellian {
+  double rho, U, V, lam, K;
+  double mu_full[NM], mu_pos[NM], mu_neg[NM];
+  double mv_full[NM], mv_pos[NM], mv_neg[NM];
+  double mxi[NM];
+};
+
+void moments1d(double m, double lam, int sign, double* out) {
+  if (sign == 0) {
+    out[0] = 1.0;
+    out[1] = m;
+  } else {
+    double s = std::sqrt(lam) * m;
+    out[0] = 0.5 * std::erfc(-sign * s);
+    out[1] = m * out[0] + sign * 0.5 * std::exp(-lam * m * m) / std::sqrt(PI * lam);
+  }
+  for (int n = 0; n + 2 < NM; ++n) out[n + 2] = m * out[n + 1] + (n + 1) / (2.0 * lam) * out[n];
+}
+
+Maxwellian make_maxwellian(double rho, double U, double V, double lam, double K) {
+  Maxwellian g;
+  g.rho = rho; g.U = U; g.V = V; g.lam = lam; g.K = K;
+  moments1d(U, lam, 0, g.mu_full);
+  moments1d(U, lam, +1, g.mu_pos);
+  moments1d(U, lam, -1, g.mu_neg);
+  moments1d(V, lam, 0, g.mv_full);
+  moments1d(V, lam, +1, g.mv_pos);
+  moments1d(V, lam, -1, g.mv_neg);
+  g.mxi[0] = 1.0;
+  for (int c = 0; c + 1 < NM; ++c) g.mxi[c + 1] = g.mxi[c] * (K + 2.0 * c) / (2.0 * lam);
+  return g;
+}
+
+// conservative W = (rho, rho U, rho V, rho E) -> Maxwellian, with
+// rho E = rho (U^2 + V^2 + (K+2)/(2 lam)) / 2.
+Maxwellian maxwellian_from_W(const double W[4], double K) {
+  double rho = W[0];
+  double U = W[1] / rho, V = W[2] / rho;
+  double eint = W[3] - 0.5 * rho * (U * U + V * V);   // rho (K+2)/(4 lam)
+  double lam = (K + 2.0) * rho / (4.0 * eint);
+  return make_maxwellian(rho, U, V, lam, K);
+}
+
+// half: axis (-1 none, 0 = u, 1 = v) and sign (+1: component > 0, -1: < 0)
+struct Half { int axis, sign; };
+const Half FULL = {-1, 0};
+
+// integral of p(u, v, xi^2) q(u, v, xi^2) g over the (half) velocity space
+// (q = 1 when omitted)
+double moment2(const Maxwellian& g, Half h, const Poly& p, const Poly& q) {
+  const double* mu = g.mu_full;
+  const double* mv = g.mv_full;
+  if (h.axis == 0) mu = h.sign > 0 ? g.mu_pos : g.mu_neg;
+  if (h.axis == 1) mv = h.sign > 0 ? g.mv_pos : g.mv_neg;
+  double s = 0.0;
+  for (const auto& x : p)
+    for (const auto& y : q) {
+      int a = x.a + y.a, b = x.b + y.b, c = x.c + y.c;
+      if (a >= NM || b >= NM || c >= NM) {
+        std::fprintf(stderr, "oracle: moment order too high\n");
+        std::abort();
+      }
+      s += x.coef * y.coef * mu[a] * mv[b] * g.mxi[c];
+    }
+  return g.rho * s;
+}
+
+double moment(const Maxwellian& g, Half h, const Poly& p) { return moment2(g, h, p, pconst(1.0)); }
+
+// ---------------------------------------------------------------------------
+// Slopes of the Maxwellian: a = sum a_l psi_l solves int a psi_k g = dW_k
+// (the spatial-derivative condition), by plain Gaussian elimination on the
+// 4x4 moment matrix.
+// ---------------------------------------------------------------------------
+void solve4(double M[4][4], double rhs[4], double x[4]) {
+  double A[4][5];
+  for (int i = 0; i < 4; ++i) {
+    for (int j = 0; j < 4; ++j) A[i][j] = M[i][j];
+    A[i][4] = rhs[i];
+  }
+  for (int col = 0; col < 4; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < 4; ++r)
+      if (std::fabs(A[r][col]) > std::fabs(A[piv][col])) piv = r;
+    if (piv != col)
+      for (int j = 0; j < 5; ++j) { double t = A[col][j]; A[col][j] = A[piv][j]; A[piv][j] = t; }
+    for (int r = col + 1; r < 4; ++r) {
+      double f = A[r][col] / A[col][col];
+      for (int j = col; j < 5; ++j) A[r][j] -= f * A[col][j];
+    }
+  }
+  for (int i = 3; i >= 0; --i) {
+    double s = A[i][4];
+    for (int j = i + 1; j < 4; ++j) s -= A[i][j] * x[j];
+    x[i] = s / A[i][i];
+  }
+}
+
+void slope(const Maxwellian& g, const double dW[4], double a[4]) {
+  double M[4][4], rhs[4];
+  for (int k = 0; k < 4; ++k) {
+    for (int l = 0; l < 4; ++l) M[k][l] = moment2(g, FULL, psi(k), psi(l));
+    rhs[k] = dW[k];
+  }
+  solve4(M, rhs, a);
+}
+
+// time slope A from the compatibility condition int (a u + b v + A) psi g = 0
+void time_slope(const Maxwellian& g, const double ax[4], const double ay[4], double A[4]) {
+  Poly transport = padd(pmul(slope_poly(ax), pu()), pmul(slope_poly(ay), pv()));
+  double M[4][4], rhs[4];
+  for (int k = 0; k < 4; ++k) {
+    for (int l = 0; l < 4; ++l) M[k][l] = moment2(g, FULL, psi(k), psi(l));
+    rhs[k] = -moment2(g, FULL, transport, psi(k));
+  }
+  solve4(M, rhs, A);
+}
+
+// ---------------------------------------------------------------------------
+// Time dependence of the interface distribution (App. A1, Eq. eq:integral_f)
+// f(0,t) = c1 g0 + c2 (a0 u + b0 v) g0 + c3 A0 g0
+//        + c4 g^{l,r} + c5 (a^{l,r} u + b^{l,r} v) g^{l,r} + c6 A^{l,r} g^{l,r}
+// (one-sided terms weighted by the Heaviside of the normal velocity), and the
+// time integrals C_k(delta) = int_0^delta c_k(t) dt in closed form.
+// ---------------------------------------------------------------------------
+void fdist_coeffs(double tau, double t, double c[6]) {
+  double E = std::exp(-t / tau);
+  c[0] = 1.0 - E;
+  c[1] = (t + tau) * E - tau;
+  c[2] = t - tau + tau * E;
+  c[3] = E;
+  c[4] = -(t + tau) * E;
+  c[5] = -tau * E;
+}
+
+void time_integrals(double tau, double d, double C[6]) {
+  double E = std::exp(-d / tau);
+  double e1 = -std::expm1(-d / tau);   // 1 - exp(-d/tau)
+  C[0] = d - tau * e1;
+  C[1] = -tau * d * (1.0 + E) + 2.0 * tau * tau * e1;
+  C[2] = 0.5 * d * d - tau * d + tau * tau * e1;
+  C[3] = tau * e1;
+  C[4] = tau * d * E - 2.0 * tau * tau * e1;
+  C[5] = -tau * tau * e1;
+}
+
+// ---------------------------------------------------------------------------
+// Kinetic terms: coef * poly * Maxwellian restricted to a half space
+// ---------------------------------------------------------------------------
+struct Term {
+  const Maxwellian* g;
+  Half half;
+  Poly poly;
+  double coef;
+};
+typedef std::vector<Term> Dist;
+
+double dist_moment(const Dist& f, const Poly& test) {
+  double s = 0.0;
+  for (const auto& t : f) s += t.coef * moment2(*t.g, t.half, t.poly, test);
+  return s;
+}
+
+// W = int psi f, normal flux = int u_n psi f, and the Prandtl-number fix of
+// the energy flux: F_E += (1/Pr - 1) q with q the normal heat flux relative to
+// the velocity (U0, V0) (App. A1).
+void dist_W_and_flux(const Dist& f, int normal, double U0, double V0, double Pr,
+                     double W[4], double F[4]) {
+  Poly un = normal == 0 ? pu() : pv();
+  for (int k = 0; k < 4; ++k) {
+    W[k] = dist_moment(f, psi(k));
+    F[k] = dist_moment(f, pmul(un, psi(k)));
+  }
+  Poly cu = padd(pu(), pconst(-U0));
+  Poly cv = padd(pv(), pconst(-V0));
+  Poly c2 = padd(padd(pmul(cu, cu), pmul(cv, cv)), Poly{{0, 0, 1, 1.0}});
+  Poly qn = pscale(pmul(normal == 0 ? cu : cv, pmerge(c2)), 0.5);
+  double q = dist_moment(f, qn);
+  F[3] += (1.0 / Pr - 1.0) * q;
+}
+
+struct Gas {
+  double gamma, K, mu, Pr, c1, c2;
+};
+
+double pressure_of(const Maxwellian& g) { return g.rho / (2.0 * g.lam); }
+
+// ---------------------------------------------------------------------------
+// Interface solve (App. A1-A2) with normal axis `normal` (0 = x, 1 = y).
+// Inputs: reconstructed left/right states, their normal derivatives, and the
+// (shared) tangential derivative.  Outputs (each 4 values):
+//   Fh, Fht   numerical flux and its time derivative          (App. A2)
+//   Whl, Whr  W^^{l,r}                                        (Eq. eq:W-model)
+//   Whlt, Whrt their time derivatives
+//   also tau.
+// ---------------------------------------------------------------------------
+struct IfaceOut {
+  double Fh[4], Fht[4], Whl[4], Whr[4], Whlt[4], Whrt[4], tau;
+};
+
+IfaceOut iface_solve(const Gas& gas, int normal, double dt, const double Wl[4], const double Wr[4],
+                     const double Wln[4], const double Wrn[4], const double Wt[4]) {
+  const double K = gas.K;
+  Maxwellian gl = maxwellian_from_W(Wl, K);
+  Maxwellian gr = maxwellian_from_W(Wr, K);
+  Half hl = {normal, +1}, hr = {normal, -1};
+
+  // equilibrium state at the interface from the particles crossing it
+  double W0[4];
+  for (int k = 0; k < 4; ++k) W0[k] = moment(gl, hl, psi(k)) + moment(gr, hr, psi(k));
+  Maxwellian g0 = maxwellian_from_W(W0, K);
+
+  // spatial slopes (x-slope multiplies x, y-slope multiplies y)
+  double axl[4], ayl[4], axr[4], ayr[4], ax0[4], ay0[4];
+  double Wn0[4];
+  for (int k = 0; k < 4; ++k) Wn0[k] = 0.5 * (Wln[k] + Wrn[k]);
+  if (normal == 0) {
+    slope(gl, Wln, axl); slope(gl, Wt, ayl);
+    slope(gr, Wrn, axr); slope(gr, Wt, ayr);
+    slope(g0, Wn0, ax0); slope(g0, Wt, ay0);
+  } else {
+    slope(gl, Wln, ayl); slope(gl, Wt, axl);
+    slope(gr, Wrn, ayr); slope(gr, Wt, axr);
+    slope(g0, Wn0, ay0); slope(g0, Wt, ax0);
+  }
+  double Al[4], Ar[4], A0[4];
+  time_slope(gl, axl, ayl, Al);
+  time_slope(gr, axr, ayr, Ar);
+  time_slope(g0, ax0, ay0, A0);
+
+  // collision time
+  double pl = pressure_of(gl), pr = pressure_of(gr), p0 = pressure_of(g0);
+  double tau = gas.c1 * dt + gas.mu / p0 + gas.c2 * dt * std::fabs(pl - pr) / (pl + pr);
+
+  Poly tr0 = padd(pmul(slope_poly(ax0), pu()), pmul(slope_poly(ay0), pv()));
+  Poly trl = padd(pmul(slope_poly(axl), pu()), pmul(slope_poly(ayl), pv()));
+  Poly trr = padd(pmul(slope_poly(axr), pu()), pmul(slope_poly(ayr), pv()));
+
+  // f(0,t) = sum_k c_k(t) phi_k with the basis terms phi_k below; its time
+  // integral over [0, delta] carries the coefficients C_k(delta), and the
+  // linear-in-time fit f = f^n + t f_t^n (App. A1)
+  //   f^n   = (4 fbar(dt/2) - fbar(dt)) / dt
+  //   f_t^n = 4 (fbar(dt) - 2 fbar(dt/2)) / dt^2
+  // is applied to each basis term's coefficient.
+  double Ch[6], Cf[6], cn[6], ct[6];
+  time_integrals(tau, 0.5 * dt, Ch);
+  time_integrals(tau, dt, Cf);
+  for (int k = 0; k < 6; ++k) {
+    cn[k] = (4.0 * Ch[k] - Cf[k]) / dt;
+    ct[k] = 4.0 * (Cf[k] - 2.0 * Ch[k]) / (dt * dt);
+  }
+  struct Basis { const Maxwellian* g; Half half; Poly poly; int k; };
+  std::vector<Basis> basis = {
+      {&g0, FULL, pconst(1.0), 0},       {&g0, FULL, tr0, 1},
+      {&g0, FULL, slope_poly(A0), 2},     {&gl, hl, pconst(1.0), 3},
+      {&gr, hr, pconst(1.0), 3},          {&gl, hl, trl, 4},
+      {&gr, hr, trr, 4},                  {&gl, hl, slope_poly(Al), 5},
+      {&gr, hr, slope_poly(Ar), 5}};
+  Dist fn, ft;
+  for (const auto& b : basis) {
+    fn.push_back({b.g, b.half, b.poly, cn[b.k]});
+    ft.push_back({b.g, b.half, b.poly, ct[b.k]});
+  }
+
+  IfaceOut o;
+  double We[4], Wet[4];
+  dist_W_and_flux(fn, normal, g0.U, g0.V, gas.Pr, We, o.Fh);
+  dist_W_and_flux(ft, normal, g0.U, g0.V, gas.Pr, Wet, o.Fht);
+
+  // one-sided free transport f^{l,r}(t) = g(1 - tau(a u + b v + A) - t(a u + b v))
+  // over the whole velocity space
+  auto one_sided = [&](const Maxwellian& g, const Poly& tr, const double* A, double W[4], double Wt_[4]) {
+    Poly f0 = padd(pconst(1.0), pscale(padd(tr, slope_poly(A)), -tau));
+    Poly f1 = pscale(tr, -1.0);
+    for (int k = 0; k < 4; ++k) {
+      W[k] = moment2(g, FULL, f0, psi(k));
+      Wt_[k] = moment2(g, FULL, f1, psi(k));
+    }
+  };
+  double Wlo[4], Wlot[4], Wro[4], Wrot[4];
+  one_sided(gl, trl, Al, Wlo, Wlot);
+  one_sided(gr, trr, Ar, Wro, Wrot);
+
+  // Eq. (eq:W-model) with tau_0 = tau
+  double E = std::exp(-dt / tau);
+  double e1 = 1.0 - E;
+  for (int k = 0; k < 4; ++k) {
+    o.Whl[k] = e1 * We[k] + E * Wlo[k];
+    o.Whr[k] = e1 * We[k] + E * Wro[k];
+    o.Whlt[k] = e1 * Wet[k] + E * Wlot[k];
+    o.Whrt[k] = e1 * Wet[k] + E * Wrot[k];
+  }
+  o.tau = tau;
+  return o;
+}
+
+// Nodal flux from smooth local data: f = g(1 - tau(a u + b v + A)), f_t = A g
+// (Sec. 2.1: nodal fluxes from the smooth local values).  out = F, G, F_t, G_t.
+void nodal_flux(const Gas& gas, double dt, const double W[4], const double Wx[4], const double Wy[4],
+                double out[16]) {
+  Maxwellian g = maxwellian_from_W(W, gas.K);
+  double ax[4], ay[4], A[4];
+  slope(g, Wx, ax);
+  slope(g, Wy, ay);
+  time_slope(g, ax, ay, A);
+  double tau = gas.c1 * dt + gas.mu / pressure_of(g);
+  Poly tr = padd(pmul(slope_poly(ax), pu()), pmul(slope_poly(ay), pv()));
+  Dist fn = {{&g, FULL, padd(pconst(1.0), pscale(padd(tr, slope_poly(A)), -tau)), 1.0}};
+  Dist ft = {{&g, FULL, slope_poly(A), 1.0}};
+  double Wd[4];
+  dist_W_and_flux(fn, 0, g.U, g.V, gas.Pr, Wd, out + 0);
+  dist_W_and_flux(fn, 1, g.U, g.V, gas.Pr, Wd, out + 4);
+  dist_W_and_flux(ft, 0, g.U, g.V, gas.Pr, Wd, out + 8);
+  dist_W_and_flux(ft, 1, g.U, g.V, gas.Pr, Wd, out + 12);
+}
+
+// ---------------------------------------------------------------------------
+// Compact reconstruction (Sec. 3.1, Eqs. 7th-compact-recons / 6th-compact-recons)
+// and GENO (Sec. 3.2, Eqs. GENO-nonlinear, GENO-IS-linear, IS-highorder-1,
+// GENO-1d-IS-HL; App. C, App. D)
+// ---------------------------------------------------------------------------
+struct GenoConst {
+  int linear;         // 1: chi = 1 (linear scheme)
+  double r, eps_a, eps_w, C;
+  double d_iface[3];  // App. C1/C2 numbering
+  double d_node[3];   // Sec. 3.2 numbering (central first)
+};
+
+GenoConst geno_const(int variant) {
+  GenoConst g;
+  g.linear = variant == 2;
+  g.C = 20.0;
+  g.eps_w = 1e-6;
+  if (variant == 1) {
+    g.r = 3.0; g.eps_a = 1e-15;
+    g.d_iface[0] = 1.0; g.d_iface[1] = 8.0; g.d_iface[2] = 1.0;
+  } else {
+    g.r = 2.0; g.eps_a = 1e-12;
+    g.d_iface[0] = 8.0; g.d_iface[1] = 1.0; g.d_iface[2] = 1.0;
+  }
+  g.d_node[0] = 8.0; g.d_node[1] = 1.0; g.d_node[2] = 1.0;
+  return g;
+}
+
+// generic GENO blend of a high-order value/derivative with the ENO-weighted
+// sub-stencil values/derivatives (Eq. GENO-nonlinear with GENO-IS-linear)
+void geno_blend(const GenoConst& gc, const double IS[3], const double d[3], const double q[3],
+                const double qx[3], double PH, double PHx, double* val, double* der, double* chi_out) {
+  double chi = 1.0;
+  if (!gc.linear) {
+    double ISL = std::fmin(IS[0], std::fmin(IS[1], IS[2]));
+    double ISH = std::fmax(IS[0], std::fmax(IS[1], IS[2]));
+    double IStau = std::fabs(0.5 * (IS[1] + IS[2]) - IS[0]);
+    double aH = 1.0 + std::pow(IStau / (ISH + gc.eps_a), gc.r);
+    double aL = 1.0 + std::pow(IStau / (ISL + gc.eps_a), gc.r);
+    double alpha = 2.0 * aH / (aH + aL);
+    chi = std::tanh(gc.C * alpha) / std::tanh(gc.C);
+  }
+  double wt[3], ws = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    wt[k] = d[k] / ((IS[k] + gc.eps_w) * (IS[k] + gc.eps_w));
+    ws += wt[k];
+  }
+  double PL = 0.0, PLx = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    PL += wt[k] / ws * q[k];
+    PLx += wt[k] / ws * qx[k];
+  }
+  *val = chi * PH + (1.0 - chi) * PL;
+  *der = chi * PHx + (1.0 - chi) * PLx;
+  *chi_out = chi;
+}
+
+// left state at interface j+1/2 from Q_{j-1..j+2} (Q[0..3]) and the averaged
+// gradients Qx_{j-1..j+1} (Qx[0..2]); App. C1
+void recon_left(const GenoConst& gc, const double Q[4], const double Qx[3], double h, double* val,
+                double* der, double* chi) {
+  double PH = ((7 * Q[0] + 35 * Q[1] + 21 * Q[2] + Q[3]) + (Qx[0] + 22 * Qx[1] - 7 * Qx[2]) * h) / 64.0;
+  double PHx = -((Q[0] + 45 * Q[1] - 45 * Q[2] - Q[3]) + 9 * (Qx[1] + Qx[2]) * h) / (30.0 * h);
+  double q[3], qx[3], IS[3];
+  q[0] = (-5 * Q[0] + 9 * Q[1] - 3 * Qx[0] * h) / 4.0;
+  q[1] = (-Q[0] + 6 * Q[1] + 3 * Q[2]) / 8.0;
+  q[2] = (3 * Q[1] + 6 * Q[2] - Q[3]) / 8.0;
+  qx[0] = (-3 * Q[0] + 3 * Q[1] - 2 * Qx[0] * h) / h;
+  qx[1] = (Q[2] - Q[1]) / h;
+  qx[2] = (Q[2] - Q[1]) / h;
+  double t;
+  t = Q[1] - Q[0] - Qx[0] * h;
+  IS[0] = 13.0 / 3.0 * t * t + (2 * (Q[1] - Q[0]) - Qx[0] * h) * (2 * (Q[1] - Q[0]) - Qx[0] * h);
+  t = Q[0] - 2 * Q[1] + Q[2];
+  IS[1] = 13.0 / 12.0 * t * t + 0.25 * (Q[2] - Q[0]) * (Q[2] - Q[0]);
+  t = Q[1] - 2 * Q[2] + Q[3];
+  IS[2] = 13.0 / 12.0 * t * t + 0.25 * (3 * Q[1] - 4 * Q[2] + Q[3]) * (3 * Q[1] - 4 * Q[2] + Q[3]);
+  geno_blend(gc, IS, gc.d_iface, q, qx, PH, PHx, val, der, chi);
+}
+
+// right state at interface j+1/2 from Q_{j-1..j+2} and Qx_{j..j+2} (Qx[0..2]); App. C2
+void recon_right(const GenoConst& gc, const double Q[4], const double Qx[3], double h, double* val,
+                 double* der, double* chi) {
+  // Qx[0] = Q_{x,j}, Qx[1] = Q_{x,j+1}, Qx[2] = Q_{x,j+2}
+  double PH = ((Q[0] + 21 * Q[1] + 35 * Q[2] + 7 * Q[3]) + (7 * Qx[0] - 22 * Qx[1] - Qx[2]) * h) / 64.0;
+  double PHx = -((Q[0] + 45 * Q[1] - 45 * Q[2] - Q[3]) + 9 * (Qx[0] + Qx[1]) * h) / (30.0 * h);
+  double q[3], qx[3], IS[3];
+  q[0] = (-5 * Q[3] + 9 * Q[2] + 3 * Qx[2] * h) / 4.0;
+  q[1] = (-Q[3] + 6 * Q[2] + 3 * Q[1]) / 8.0;
+  q[2] = (-Q[0] + 6 * Q[1] + 3 * Q[2]) / 8.0;
+  qx[0] = (-3 * Q[2] + 3 * Q[3] - 2 * Qx[2] * h) / h;
+  qx[1] = (Q[2] - Q[1]) / h;
+  qx[2] = (Q[2] - Q[1]) / h;
+  double t;
+  t = Q[2] - Q[3] + Qx[2] * h;
+  IS[0] = 13.0 / 3.0 * t * t + (2 * (Q[3] - Q[2]) - Qx[2] * h) * (2 * (Q[3] - Q[2]) - Qx[2] * h);
+  t = Q[1] - 2 * Q[2] + Q[3];
+  IS[1] = 13.0 / 12.0 * t * t + 0.25 * (Q[3] - Q[1]) * (Q[3] - Q[1]);
+  t = Q[0] - 2 * Q[1] + Q[2];
+  IS[2] = 13.0 / 12.0 * t * t + 0.25 * (3 * Q[2] - 4 * Q[1] + Q[0]) * (3 * Q[2] - 4 * Q[1] + Q[0]);
+  geno_blend(gc, IS, gc.d_iface, q, qx, PH, PHx, val, der, chi);
+}
+
+// derivative at node j from Q_{j-1..j+1} and Qx_{j-1..j+1}; Eq. 6th-compact-recons
+// and App. C3, with the sub-stencils numbered as in Sec. 3.2 (central first)
+void recon_node(const GenoConst& gc, const double Q[3], const double Qx[3], double h, double* der,
+                double* chi) {
+  double PHx = (9 * (Q[0] - Q[2]) + h * (Qx[0] + 46 * Qx[1] + Qx[2])) / (30.0 * h);
+  double qx[3], q[3] = {0, 0, 0}, IS[3];
+  // s1 = {Q_{j-1}, Q_j, Q_{j+1}}  (App. C3 q3)
+  qx[0] = (Q[2] - Q[0]) / (2.0 * h);
+  // s2 = {Q_{j-1}, Q_j, Q_{x,j-1}} (App. C3 q1)
+  qx[1] = (-2 * Q[0] + 2 * Q[1] - Qx[0] * h) / h;
+  // s3 = {Q_j, Q_{j+1}, Q_{x,j+1}} (App. C3 q2)
+  qx[2] = (-2 * Q[1] + 2 * Q[2] - Qx[2] * h) / h;
+  double t;
+  t = Q[0] - 2 * Q[1] + Q[2];
+  IS[0] = 13.0 / 12.0 * t * t + 0.25 * (Q[2] - Q[0]) * (Q[2] - Q[0]);
+  t = Q[1] - Q[0] - Qx[0] * h;
+  IS[1] = 13.0 / 3.0 * t * t + (2 * (Q[1] - Q[0]) - Qx[0] * h) * (2 * (Q[1] - Q[0]) - Qx[0] * h);
+  t = Q[2] - Q[1] - Qx[2] * h;
+  IS[2] = 13.0 / 3.0 * t * t + (2 * (Q[2] - Q[1]) - Qx[2] * h) * (2 * (Q[2] - Q[1]) - Qx[2] * h);
+  double val;
+  geno_blend(gc, IS, gc.d_node, q, qx, Q[1], PHx, &val, der, chi);
+}
+
+// ---------------------------------------------------------------------------
+// Compact numerical flux (Eqs. fd-conservative-flux, -flux-1, -flux-2)
+// Fi = {F_{j-1/2}, F_{j+1/2}, F_{j+3/2}} interface fluxes, Fn = {F_j, F_{j+1}}
+// ---------------------------------------------------------------------------
+double compact_flux(int variant, double chi, const double Fi[3], const double Fn[2]) {
+  double Fbar = (Fi[0] + 46.0 * Fi[1] + Fi[2] - 9.0 * (Fn[0] + Fn[1])) / 30.0;
+  double Flow = variant == 62 ? Fi[1] : (8.0 * Fi[1] - Fn[0] - Fn[1]) / 6.0;
+  return (1.0 - chi) * Flow + chi * Fbar;
+}
+
+}  // namespace
+
+// ===========================================================================
+// 2-D dual-grid scheme (Sec. 4) with S2O4 time stepping (Sec. 2.4)
+// ===========================================================================
+extern "C" {
+
+enum { OBC_PERIODIC = 0, OBC_TRANSMISSIVE = 1, OBC_SYMMETRY = 2, OBC_NOSLIP = 3 };
+
+typedef struct {
+  int nx, ny;
+  double x0, x1, y0, y1;
+  double gamma, mu, Pr;
+  int bc[4];            // xlo, xhi, ylo, yhi
+  int flux_variant;     // 64 or 62
+  int geno_variant;     // 0 text, 1 App. D, 2 linear
+  int grad_base;        // 0 reading B (re-evaluated), 1 reading A (stored)
+  double tau_c1, tau_c2;
+} oracle_params;
+
+}  // extern "C"
+
+namespace {
+
+const int G = 3;  // ghost layers
+
+struct Grid {
+  int n[2];        // interior nodes (x, y)
+  int per[2];      // periodic per direction
+  int pitch;       // padded row length
+  int rows;        // padded rows
+  // 12 fields: W[4], Gx[4], Gy[4]
+  std::vector<double> f;
+  int idx(int i, int j) const { return (j + G) * pitch + (i + G); }
+  double& at(int field, int i, int j) { return f[(size_t)field * pitch * rows + idx(i, j)]; }
+  double at(int field, int i, int j) const { return f[(size_t)field * pitch * rows + idx(i, j)]; }
+};
+
+Grid make_grid(int nx, int ny, int perx, int pery) {
+  Grid g;
+  g.n[0] = nx; g.n[1] = ny;
+  g.per[0] = perx; g.per[1] = pery;
+  g.pitch = nx + 2 * G;
+  g.rows = ny + 2 * G;
+  g.f.assign((size_t)12 * g.pitch * g.rows, 0.0);
+  return g;
+}
+
+// ghost fill of one grid; is_dual selects the mirror map (dual nodes lie on
+// bounded boundaries, primary nodes half a spacing inside)
+void fill_ghosts(Grid& g, const int bc[4], bool is_dual) {
+  for (int dir = 0; dir < 2; ++dir) {
+    int n = g.n[dir];
+    int lo = dir == 0 ? -G : -G;
+    int tcount = dir == 0 ? g.n[1] : g.n[0] + 2 * G;   // x pass over interior rows, y pass over all columns
+    int toff = dir == 0 ? 0 : -G;
+    for (int side = 0; side < 2; ++side) {
+      int b = bc[2 * dir + side];
+      for (int t = 0; t < tcount; ++t) {
+        int tt = t + toff;
+        for (int k = 1; k <= G; ++k) {
+          int ghost = side == 0 ? -k : n - 1 + k;
+          int src;
+          if (b == OBC_PERIODIC) src = side == 0 ? n - k : k - 1;
+          else if (b == OBC_TRANSMISSIVE) src = side == 0 ? 0 : n - 1;
+          else if (!is_dual) src = side == 0 ? k - 1 : n - k;
+          else src = side == 0 ? k : n - 1 - k;
+          int gi = dir == 0 ? ghost : tt, gj = dir == 0 ? tt : ghost;
+          int si = dir == 0 ? src : tt, sj = dir == 0 ? tt : src;
+          for (int c = 0; c < 4; ++c) {
+            double sW = 1.0;
+            if (b == OBC_SYMMETRY || b == OBC_NOSLIP) {
+              int normal_mom = 1 + dir, tang_mom = 2 - dir;
+              if (c == normal_mom) sW = -1.0;
+              if (c == tang_mom && b == OBC_NOSLIP) sW = -1.0;
+            }
+            double w = g.at(c, si, sj);
+            double gx = g.at(4 + c, si, sj), gy = g.at(8 + c, si, sj);
+            if (b == OBC_TRANSMISSIVE) {
+              g.at(c, gi, gj) = w;
+              g.at(4 + c, gi, gj) = 0.0;
+              g.at(8 + c, gi, gj) = 0.0;
+            } else if (b == OBC_PERIODIC) {
+              g.at(c, gi, gj) = w;
+              g.at(4 + c, gi, gj) = gx;
+              g.at(8 + c, gi, gj) = gy;
+            } else {
+              g.at(c, gi, gj) = sW * w;
+              // derivative along the mirror normal flips sign once more
+              g.at(4 + c, gi, gj) = (dir == 0 ? -sW : sW) * gx;
+              g.at(8 + c, gi, gj) = (dir == 1 ? -sW : sW) * gy;
+            }
+          }
+        }
+      }
+    }
+    (void)lo;
+  }
+}
+
+struct PointOut {
+  // solve s = 0: the primary-grid solve at this point, s = 1: the dual-grid solve
+  double F[2][4], Ft[2][4], chi[2];
+  double Wl[2][4], Wr[2][4], Wlt[2][4], Wrt[2][4];  // W~ (Eq. eq:W-model-2d)
+};
+
+struct NodeOut { double F[4], G[4], Ft[4], Gt[4]; };
+
+// line reconstruction: 4 values + 4 averaged gradients along the line, at the
+// interface between entries 1 and 2; returns l/r values, derivatives, chi of rho
+void recon_line(const GenoConst& gc, const double Q[4][4], const double Qx[4][4], double h,
+                double Wl[4], double Wr[4], double Wlx[4], double Wrx[4], double* chi) {
+  double chil = 1.0, chir = 1.0;
+  for (int c = 0; c < 4; ++c) {
+    double q[4] = {Q[0][c], Q[1][c], Q[2][c], Q[3][c]};
+    double gl[3] = {Qx[0][c], Qx[1][c], Qx[2][c]};
+    double gr[3] = {Qx[1][c], Qx[2][c], Qx[3][c]};
+    double cl, cr;
+    recon_left(gc, q, gl, h, &Wl[c], &Wlx[c], &cl);
+    recon_right(gc, q, gr, h, &Wr[c], &Wrx[c], &cr);
+    if (c == 0) { chil = cl; chir = cr; }
+  }
+  *chi = std::fmin(chil, chir);
+}
+
+// both solves at one virtual-interface point (Sec. 4 item 1, App. A3).
+// line 0: the grid whose interface normal is `n0`; line 1: the other grid,
+// normal n1 = 1 - n0.
+PointOut point_solve(const Gas& gas, const GenoConst& gc, double dt, int n0, const double Q0[4][4],
+                     const double Q0x[4][4], double h0, const double Q1[4][4], const double Q1x[4][4],
+                     double h1) {
+  double Wl0[4], Wr0[4], Wl0n[4], Wr0n[4], chi0;
+  double Wl1[4], Wr1[4], Wl1n[4], Wr1n[4], chi1;
+  recon_line(gc, Q0, Q0x, h0, Wl0, Wr0, Wl0n, Wr0n, &chi0);
+  recon_line(gc, Q1, Q1x, h1, Wl1, Wr1, Wl1n, Wr1n, &chi1);
+  double t0[4], t1[4];
+  for (int c = 0; c < 4; ++c) {
+    t0[c] = 0.5 * (Wl1n[c] + Wr1n[c]);   // tangential derivative for solve 0
+    t1[c] = 0.5 * (Wl0n[c] + Wr0n[c]);   // tangential derivative for solve 1
+  }
+  IfaceOut s0 = iface_solve(gas, n0, dt, Wl0, Wr0, Wl0n, Wr0n, t0);
+  IfaceOut s1 = iface_solve(gas, 1 - n0, dt, Wl1, Wr1, Wl1n, Wr1n, t1);
+  PointOut o;
+  for (int c = 0; c < 4; ++c) {
+    o.F[0][c] = s0.Fh[c]; o.Ft[0][c] = s0.Fht[c];
+    o.F[1][c] = s1.Fh[c]; o.Ft[1][c] = s1.Fht[c];
+    o.Wl[0][c] = 0.5 * s0.Whl[c] + 0.25 * (s1.Whl[c] + s1.Whr[c]);
+    o.Wr[0][c] = 0.5 * s0.Whr[c] + 0.25 * (s1.Whl[c] + s1.Whr[c]);
+    o.Wlt[0][c] = 0.5 * s0.Whlt[c] + 0.25 * (s1.Whlt[c] + s1.Whrt[c]);
+    o.Wrt[0][c] = 0.5 * s0.Whrt[c] + 0.25 * (s1.Whlt[c] + s1.Whrt[c]);
+    o.Wl[1][c] = 0.5 * s1.Whl[c] + 0.25 * (s0.Whl[c] + s0.Whr[c]);
+    o.Wr[1][c] = 0.5 * s1.Whr[c] + 0.25 * (s0.Whl[c] + s0.Whr[c]);
+    o.Wlt[1][c] = 0.5 * s1.Whlt[c] + 0.25 * (s0.Whlt[c] + s0.Whrt[c]);
+    o.Wrt[1][c] = 0.5 * s1.Whrt[c] + 0.25 * (s0.Whlt[c] + s0.Whrt[c]);
+  }
+  o.chi[0] = chi0;
+  o.chi[1] = chi1;
+  return o;
+}
+
+// 2-D arrays over an index rectangle
+template <class T>
+struct Rect {
+  int i0, i1, j0, j1;   // inclusive
+  std::vector<T> v;
+  void init(int a0, int a1, int b0, int b1) {
+    i0 = a0; i1 = a1; j0 = b0; j1 = b1;
+    v.assign((size_t)(i1 - i0 + 1) * (j1 - j0 + 1), T());
+  }
+  T& at(int i, int j) {
+    if (i < i0 || i > i1 || j < j0 || j > j1) {
+      std::fprintf(stderr, "oracle: rect index (%d,%d) outside [%d,%d]x[%d,%d]\n", i, j, i0, i1, j0, j1);
+      std::abort();
+    }
+    return v[(size_t)(j - j0) * (i1 - i0 + 1) + (i - i0)];
+  }
+};
+
+struct StageOut {
+  // per interior node: L, L_t (4 each), averaged gradient re-evaluated from the
+  // interface solution and its time derivative (x and y, 4 each)
+  std::vector<double> Lp, Ltp, gbp, gtp, Ld, Ltd, gbd, gtd;
+};
+
+struct Scheme {
+  oracle_params p;
+  Gas gas;
+  GenoConst gc;
+  int nxd, nyd;
+  double hx, hy;
+};
+
+void gather_line(const Grid& g, int i, int j, int dir, double Q[4][4], double Qn[4][4]) {
+  // entries at offsets -1..2 along dir from (i, j)
+  for (int m = 0; m < 4; ++m) {
+    int ii = dir == 0 ? i - 1 + m : i, jj = dir == 0 ? j : j - 1 + m;
+    for (int c = 0; c < 4; ++c) {
+      Q[m][c] = g.at(c, ii, jj);
+      Qn[m][c] = g.at((dir == 0 ? 4 : 8) + c, ii, jj);
+    }
+  }
+}
+
+StageOut stage(const Scheme& S, Grid& P, Grid& D, double dt) {
+  const int nx = S.p.nx, ny = S.p.ny, nxd = S.nxd, nyd = S.nyd;
+  fill_ghosts(P, S.p.bc, false);
+  fill_ghosts(D, S.p.bc, true);
+
+  // nodal reconstruction and flux (Sec. 4 item 2, Sec. 2.1)
+  auto nodal = [&](Grid& g, int nxg, int nyg, Rect<NodeOut>& out) {
+    out.init(-1, nxg, -1, nyg);
+    for (int j = -1; j <= nyg; ++j)
+      for (int i = -1; i <= nxg; ++i) {
+        double W[4], Wx[4], Wy[4];
+        for (int c = 0; c < 4; ++c) {
+          W[c] = g.at(c, i, j);
+          double qxl[3] = {g.at(c, i - 1, j), g.at(c, i, j), g.at(c, i + 1, j)};
+          double gxl[3] = {g.at(4 + c, i - 1, j), g.at(4 + c, i, j), g.at(4 + c, i + 1, j)};
+          double qyl[3] = {g.at(c, i, j - 1), g.at(c, i, j), g.at(c, i, j + 1)};
+          double gyl[3] = {g.at(8 + c, i, j - 1), g.at(8 + c, i, j), g.at(8 + c, i, j + 1)};
+          double chi;
+          recon_node(S.gc, qxl, gxl, S.hx, &Wx[c], &chi);
+          recon_node(S.gc, qyl, gyl, S.hy, &Wy[c], &chi);
+        }
+        double o[16];
+        nodal_flux(S.gas, dt, W, Wx, Wy, o);
+        NodeOut& r = out.at(i, j);
+        for (int c = 0; c < 4; ++c) {
+          r.F[c] = o[c]; r.G[c] = o[4 + c]; r.Ft[c] = o[8 + c]; r.Gt[c] = o[12 + c];
+        }
+      }
+  };
+  Rect<NodeOut> NP, ND;
+  nodal(P, nx, ny, NP);
+  nodal(D, nxd, nyd, ND);
+
+  // Type A points (i+1/2, j): primary x-interface and dual y-interface of dual column i+1
+  Rect<PointOut> A, B;
+  A.init(-2, nx, -2, nyd);
+  for (int j = A.j0; j <= A.j1; ++j)
+    for (int i = A.i0; i <= A.i1; ++i) {
+      double Q0[4][4], Q0n[4][4], Q1[4][4], Q1n[4][4];
+      gather_line(P, i, j, 0, Q0, Q0n);          // primary (i-1..i+2, j)
+      gather_line(D, i + 1, j, 1, Q1, Q1n);      // dual (i+1, j-1..j+2)
+      A.at(i, j) = point_solve(S.gas, S.gc, dt, 0, Q0, Q0n, S.hx, Q1, Q1n, S.hy);
+    }
+  // Type B points (i, j+1/2): primary y-interface and dual x-interface of dual row j+1
+  B.init(-2, nxd, -2, ny);
+  for (int j = B.j0; j <= B.j1; ++j)
+    for (int i = B.i0; i <= B.i1; ++i) {
+      double Q0[4][4], Q0n[4][4], Q1[4][4], Q1n[4][4];
+      gather_line(P, i, j, 1, Q0, Q0n);          // primary (i, j-1..j+2)
+      gather_line(D, i, j + 1, 0, Q1, Q1n);      // dual (i-1..i+2, j+1)
+      B.at(i, j) = point_solve(S.gas, S.gc, dt, 1, Q0, Q0n, S.hy, Q1, Q1n, S.hx);
+    }
+
+  StageOut so;
+  so.Lp.assign((size_t)4 * nx * ny, 0.0); so.Ltp = so.Lp;
+  so.gbp.assign((size_t)8 * nx * ny, 0.0); so.gtp = so.gbp;
+  so.Ld.assign((size_t)4 * nxd * nyd, 0.0); so.Ltd = so.Ld;
+  so.gbd.assign((size_t)8 * nxd * nyd, 0.0); so.gtd = so.gbd;
+  const int fv = S.p.flux_variant;
+
+  // primary nodes (Eq. eq-conservation-law-2d; Eq. define-averaged-gradient)
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      size_t n = (size_t)j * nx + i, NN = (size_t)nx * ny;
+      for (int c = 0; c < 4; ++c) {
+        auto fx = [&](int k, bool t) {   // x-interface k+1/2 between primary k, k+1
+          double Fi[3], Fn[2];
+          for (int m = 0; m < 3; ++m) Fi[m] = t ? A.at(k - 1 + m, j).Ft[0][c] : A.at(k - 1 + m, j).F[0][c];
+          Fn[0] = t ? NP.at(k, j).Ft[c] : NP.at(k, j).F[c];
+          Fn[1] = t ? NP.at(k + 1, j).Ft[c] : NP.at(k + 1, j).F[c];
+          return compact_flux(fv, A.at(k, j).chi[0], Fi, Fn);
+        };
+        auto fy = [&](int k, bool t) {   // y-interface k+1/2 between primary k, k+1
+          double Fi[3], Fn[2];
+          for (int m = 0; m < 3; ++m) Fi[m] = t ? B.at(i, k - 1 + m).Ft[0][c] : B.at(i, k - 1 + m).F[0][c];
+          Fn[0] = t ? NP.at(i, k).Gt[c] : NP.at(i, k).G[c];
+          Fn[1] = t ? NP.at(i, k + 1).Gt[c] : NP.at(i, k + 1).G[c];
+          return compact_flux(fv, B.at(i, k).chi[0], Fi, Fn);
+        };
+        so.Lp[c * NN + n] = -(fx(i, false) - fx(i - 1, false)) / S.hx - (fy(j, false) - fy(j - 1, false)) / S.hy;
+        so.Ltp[c * NN + n] = -(fx(i, true) - fx(i - 1, true)) / S.hx - (fy(j, true) - fy(j - 1, true)) / S.hy;
+        so.gbp[c * NN + n] = (A.at(i, j).Wl[0][c] - A.at(i - 1, j).Wr[0][c]) / S.hx;
+        so.gtp[c * NN + n] = (A.at(i, j).Wlt[0][c] - A.at(i - 1, j).Wrt[0][c]) / S.hx;
+        so.gbp[(4 + c) * NN + n] = (B.at(i, j).Wl[0][c] - B.at(i, j - 1).Wr[0][c]) / S.hy;
+        so.gtp[(4 + c) * NN + n] = (B.at(i, j).Wlt[0][c] - B.at(i, j - 1).Wrt[0][c]) / S.hy;
+      }
+    }
+  // dual nodes: x-interfaces of dual row r are B(., r-1); y-interfaces of dual column c are A(c-1, .)
+  for (int r = 0; r < nyd; ++r)
+    for (int cc = 0; cc < nxd; ++cc) {
+      size_t n = (size_t)r * nxd + cc, NN = (size_t)nxd * nyd;
+      for (int c = 0; c < 4; ++c) {
+        auto fx = [&](int k, bool t) {   // dual x-interface k+1/2 between dual k, k+1 in row r
+          double Fi[3], Fn[2];
+          for (int m = 0; m < 3; ++m) Fi[m] = t ? B.at(k - 1 + m, r - 1).Ft[1][c] : B.at(k - 1 + m, r - 1).F[1][c];
+          Fn[0] = t ? ND.at(k, r).Ft[c] : ND.at(k, r).F[c];
+          Fn[1] = t ? ND.at(k + 1, r).Ft[c] : ND.at(k + 1, r).F[c];
+          return compact_flux(fv, B.at(k, r - 1).chi[1], Fi, Fn);
+        };
+        auto fy = [&](int k, bool t) {   // dual y-interface k+1/2 between dual k, k+1 in column cc
+          double Fi[3], Fn[2];
+          for (int m = 0; m < 3; ++m) Fi[m] = t ? A.at(cc - 1, k - 1 + m).Ft[1][c] : A.at(cc - 1, k - 1 + m).F[1][c];
+          Fn[0] = t ? ND.at(cc, k).Gt[c] : ND.at(cc, k).G[c];
+          Fn[1] = t ? ND.at(cc, k + 1).Gt[c] : ND.at(cc, k + 1).G[c];
+          return compact_flux(fv, A.at(cc - 1, k).chi[1], Fi, Fn);
+        };
+        so.Ld[c * NN + n] = -(fx(cc, false) - fx(cc - 1, false)) / S.hx - (fy(r, false) - fy(r - 1, false)) / S.hy;
+        so.Ltd[c * NN + n] = -(fx(cc, true) - fx(cc - 1, true)) / S.hx - (fy(r, true) - fy(r - 1, true)) / S.hy;
+        so.gbd[c * NN + n] = (B.at(cc, r - 1).Wl[1][c] - B.at(cc - 1, r - 1).Wr[1][c]) / S.hx;
+        so.gtd[c * NN + n] = (B.at(cc, r - 1).Wlt[1][c] - B.at(cc - 1, r - 1).Wrt[1][c]) / S.hx;
+        so.gbd[(4 + c) * NN + n] = (A.at(cc - 1, r).Wl[1][c] - A.at(cc - 1, r - 1).Wr[1][c]) / S.hy;
+        so.gtd[(4 + c) * NN + n] = (A.at(cc - 1, r).Wlt[1][c] - A.at(cc - 1, r - 1).Wrt[1][c]) / S.hy;
+      }
+    }
+  return so;
+}
+
+bool make_scheme(const oracle_params* p, Scheme& S) {
+  S.p = *p;
+  if (p->nx < 1 || p->ny < 1) return false;
+  for (int d = 0; d < 2; ++d) {
+    bool a = p->bc[2 * d] == OBC_PERIODIC, b = p->bc[2 * d + 1] == OBC_PERIODIC;
+    if (a != b) return false;
+  }
+  S.nxd = p->nx + (p->bc[0] == OBC_PERIODIC ? 0 : 1);
+  S.nyd = p->ny + (p->bc[2] == OBC_PERIODIC ? 0 : 1);
+  S.hx = (p->x1 - p->x0) / p->nx;
+  S.hy = (p->y1 - p->y0) / p->ny;
+  S.gas.gamma = p->gamma;
+  S.gas.K = (4.0 - 2.0 * p->gamma) / (p->gamma - 1.0);
+  S.gas.mu = p->mu;
+  S.gas.Pr = p->Pr;
+  S.gas.c1 = p->tau_c1;
+  S.gas.c2 = p->tau_c2;
+  S.gc = geno_const(p->geno_variant);
+  return true;
+}
+
+void load_grid(Grid& g, const double* W, const double* Gr) {
+  int nx = g.n[0], ny = g.n[1];
+  size_t NN = (size_t)nx * ny;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i)
+      for (int c = 0; c < 4; ++c) {
+        g.at(c, i, j) = W[c * NN + (size_t)j * nx + i];
+        g.at(4 + c, i, j) = Gr[c * NN + (size_t)j * nx + i];
+        g.at(8 + c, i, j) = Gr[(4 + c) * NN + (size_t)j * nx + i];
+      }
+}
+void store_grid(const Grid& g, double* W, double* Gr) {
+  int nx = g.n[0], ny = g.n[1];
+  size_t NN = (size_t)nx * ny;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i)
+      for (int c = 0; c < 4; ++c) {
+        W[c * NN + (size_t)j * nx + i] = g.at(c, i, j);
+        Gr[c * NN + (size_t)j * nx + i] = g.at(4 + c, i, j);
+        Gr[(4 + c) * NN + (size_t)j * nx + i] = g.at(8 + c, i, j);
+      }
+}
+
+// velocity of dual nodes lying on a no-slip wall is set to zero (kinetic
+// energy removed, internal energy kept)
+void noslip_reset(const Scheme& S, Grid& D) {
+  const int* bc = S.p.bc;
+  for (int j = 0; j < S.nyd; ++j)
+    for (int i = 0; i < S.nxd; ++i) {
+      bool wall = (bc[0] == OBC_NOSLIP && i == 0) || (bc[1] == OBC_NOSLIP && i == S.nxd - 1) ||
+                  (bc[2] == OBC_NOSLIP && j == 0) || (bc[3] == OBC_NOSLIP && j == S.nyd - 1);
+      if (!wall) continue;
+      double rho = D.at(0, i, j);
+      double ke = 0.5 * (D.at(1, i, j) * D.at(1, i, j) + D.at(2, i, j) * D.at(2, i, j)) / rho;
+      D.at(1, i, j) = 0.0;
+      D.at(2, i, j) = 0.0;
+      D.at(3, i, j) -= ke;
+    }
+}
+
+// one S2O4 step (Eqs. eq-nodal-update, eq-interface-update)
+void s2o4_step(const Scheme& S, Grid& P, Grid& D, double dt) {
+  Grid* grids[2] = {&P, &D};
+  const bool readA = S.p.grad_base == 1;
+  Grid P0 = P, D0 = D;   // state at t^n
+  StageOut s1 = stage(S, P, D, dt);
+  // stage 1 -> t^{n+1/2}
+  const std::vector<double>* L1[2] = {&s1.Lp, &s1.Ld};
+  const std::vector<double>* Lt1[2] = {&s1.Ltp, &s1.Ltd};
+  const std::vector<double>* gb1[2] = {&s1.gbp, &s1.gbd};
+  const std::vector<double>* gt1[2] = {&s1.gtp, &s1.gtd};
+  Grid* base[2] = {&P0, &D0};
+  for (int gi = 0; gi < 2; ++gi) {
+    Grid& g = *grids[gi];
+    Grid& g0 = *base[gi];
+    int nx = g.n[0], ny = g.n[1];
+    size_t NN = (size_t)nx * ny;
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t n = (size_t)j * nx + i;
+        for (int c = 0; c < 4; ++c) {
+          double L = (*L1[gi])[c * NN + n], Lt = (*Lt1[gi])[c * NN + n];
+          g.at(c, i, j) = g0.at(c, i, j) + 0.5 * dt * L + 0.125 * dt * dt * Lt;
+          for (int d = 0; d < 2; ++d) {
+            double gbase = readA ? g0.at(4 + 4 * d + c, i, j) : (*gb1[gi])[(4 * d + c) * NN + n];
+            g.at(4 + 4 * d + c, i, j) = gbase + 0.5 * dt * (*gt1[gi])[(4 * d + c) * NN + n];
+          }
+        }
+      }
+  }
+  noslip_reset(S, D);
+  StageOut s2 = stage(S, P, D, dt);
+  const std::vector<double>* Lt2[2] = {&s2.Ltp, &s2.Ltd};
+  const std::vector<double>* gt2[2] = {&s2.gtp, &s2.gtd};
+  for (int gi = 0; gi < 2; ++gi) {
+    Grid& g = *grids[gi];
+    Grid& g0 = *base[gi];
+    int nx = g.n[0], ny = g.n[1];
+    size_t NN = (size_t)nx * ny;
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t n = (size_t)j * nx + i;
+        for (int c = 0; c < 4; ++c) {
+          double L = (*L1[gi])[c * NN + n], Lt = (*Lt1[gi])[c * NN + n], Lts = (*Lt2[gi])[c * NN + n];
+          g.at(c, i, j) = g0.at(c, i, j) + dt * L + 0.5 * dt * dt * Lt + dt * dt / 3.0 * (Lts - Lt);
+          for (int d = 0; d < 2; ++d) {
+            double gbase = readA ? g0.at(4 + 4 * d + c, i, j) : (*gb1[gi])[(4 * d + c) * NN + n];
+            g.at(4 + 4 * d + c, i, j) = gbase + dt * (*gt2[gi])[(4 * d + c) * NN + n];
+          }
+        }
+      }
+  }
+  noslip_reset(S, D);
+}
+
+}  // namespace
+
+// ===========================================================================
+// C entry points (used by tests through ctypes)
+// ===========================================================================
+extern "C" {
+
+int oracle_dims(const oracle_params* p, int* nxd, int* nyd) {
+  Scheme S;
+  if (!make_scheme(p, S)) return 1;
+  *nxd = S.nxd;
+  *nyd = S.nyd;
+  return 0;
+}
+
+// advance nsteps S2O4 steps of size dt in place.  Layouts: W [4][ny][nx],
+// gradients [2][4][ny][nx] (x then y), dual arrays over (nxd, nyd).
+int oracle_steps(const oracle_params* p, double dt, int nsteps, double* Wp, double* Gp, double* Wd,
+                 double* Gd) {
+  Scheme S;
+  if (!make_scheme(p, S)) return 1;
+  Grid P = make_grid(p->nx, p->ny, p->bc[0] == OBC_PERIODIC, p->bc[2] == OBC_PERIODIC);
+  Grid D = make_grid(S.nxd, S.nyd, p->bc[0] == OBC_PERIODIC, p->bc[2] == OBC_PERIODIC);
+  load_grid(P, Wp, Gp);
+  load_grid(D, Wd, Gd);
+  for (int s = 0; s < nsteps; ++s) s2o4_step(S, P, D, dt);
+  store_grid(P, Wp, Gp);
+  store_grid(D, Wd, Gd);
+  return 0;
+}
+
+// one stage's spatial operator: L, L_t, re-evaluated averaged gradients and
+// their time derivatives, for both grids (interior nodes only)
+int oracle_stage(const oracle_params* p, double dt, const double* Wp, const double* Gp, const double* Wd,
+                 const double* Gd, double* Lp, double* Ltp, double* gbp, double* gtp, double* Ld,
+                 double* Ltd, double* gbd, double* gtd) {
+  Scheme S;
+  if (!make_scheme(p, S)) return 1;
+  Grid P = make_grid(p->nx, p->ny, p->bc[0] == OBC_PERIODIC, p->bc[2] == OBC_PERIODIC);
+  Grid D = make_grid(S.nxd, S.nyd, p->bc[0] == OBC_PERIODIC, p->bc[2] == OBC_PERIODIC);
+  load_grid(P, Wp, Gp);
+  load_grid(D, Wd, Gd);
+  StageOut o = stage(S, P, D, dt);
+  std::memcpy(Lp, o.Lp.data(), o.Lp.size() * sizeof(double));
+  std::memcpy(Ltp, o.Ltp.data(), o.Ltp.size() * sizeof(double));
+  std::memcpy(gbp, o.gbp.data(), o.gbp.size() * sizeof(double));
+  std::memcpy(gtp, o.gtp.data(), o.gtp.size() * sizeof(double));
+  std::memcpy(Ld, o.Ld.data(), o.Ld.size() * sizeof(double));
+  std::memcpy(Ltd, o.Ltd.data(), o.Ltd.size() * sizeof(double));
+  std::memcpy(gbd, o.gbd.data(), o.gbd.size() * sizeof(double));
+  std::memcpy(gtd, o.gtd.data(), o.gtd.size() * sizeof(double));
+  return 0;
+}
+
+// CFL time step (Sec. 5): dt = CFL * min over both grids of h/(|U|+c) per
+// direction, and with viscosity also CFL * h^2 / (8 nu_max), nu = mu/rho
+double oracle_cfl_dt(const oracle_params* p, double cfl, const double* Wp, const double* Wd) {
+  Scheme S;
+  if (!make_scheme(p, S)) return -1.0;
+  double best = 1e300;
+  double numax = 0.0;
+  const double* arrs[2] = {Wp, Wd};
+  int nxs[2] = {p->nx, S.nxd}, nys[2] = {p->ny, S.nyd};
+  for (int g = 0; g < 2; ++g) {
+    size_t NN = (size_t)nxs[g] * nys[g];
+    for (size_t n = 0; n < NN; ++n) {
+      double rho = arrs[g][n], U = arrs[g][NN + n] / rho, V = arrs[g][2 * NN + n] / rho;
+      double pr = (p->gamma - 1.0) * (arrs[g][3 * NN + n] - 0.5 * rho * (U * U + V * V));
+      double c = std::sqrt(p->gamma * pr / rho);
+      best = std::fmin(best, std::fmin(S.hx / (std::fabs(U) + c), S.hy / (std::fabs(V) + c)));
+      numax = std::fmax(numax, p->mu / rho);
+    }
+  }
+  double dt = cfl * best;
+  if (numax > 0.0) {
+    double h = std::fmin(S.hx, S.hy);
+    dt = std::fmin(dt, cfl * h * h / (8.0 * numax));
+  }
+  return dt;
+}
+
+// ---- component-level entry points for the pins ----
+
+double oracle_maxwell_moment(double rho, double U, double V, double lam, double K, int a, int b, int c,
+                             int half_axis, int half_sign) {
+  Maxwellian g = make_maxwellian(rho, U, V, lam, K);
+  Half h = {half_axis, half_sign};
+  return moment(g, h, Poly{{a, b, c, 1.0}});
+}
+
+void oracle_slope(const double W[4], const double dW[4], double gamma, double a[4]) {
+  double K = (4.0 - 2.0 * gamma) / (gamma - 1.0);
+  Maxwellian g = maxwellian_from_W(W, K);
+  slope(g, dW, a);
+}
+
+void oracle_time_slope(const double W[4], const double ax[4], const double ay[4], double gamma, double A[4]) {
+  double K = (4.0 - 2.0 * gamma) / (gamma - 1.0);
+  Maxwellian g = maxwellian_from_W(W, K);
+  time_slope(g, ax, ay, A);
+}
+
+void oracle_fdist_coeffs(double tau, double t, double c[6]) { fdist_coeffs(tau, t, c); }
+void oracle_time_integrals(double tau, double delta, double C[6]) { time_integrals(tau, delta, C); }
+
+// GENO reconstructions; out = {value, derivative, chi}
+void oracle_recon_left(int variant, const double Q[4], const double Qx[3], double h, double out[3]) {
+  recon_left(geno_const(variant), Q, Qx, h, &out[0], &out[1], &out[2]);
+}
+void oracle_recon_right(int variant, const double Q[4], const double Qx[3], double h, double out[3]) {
+  recon_right(geno_const(variant), Q, Qx, h, &out[0], &out[1], &out[2]);
+}
+void oracle_recon_node(int variant, const double Q[3], const double Qx[3], double h, double out[2]) {
+  recon_node(geno_const(variant), Q, Qx, h, &out[0], &out[1]);
+}
+void oracle_geno_blend(int variant, int node, const double IS[3], const double q[3], const double qx[3],
+                       double PH, double PHx, double out[3]) {
+  GenoConst gc = geno_const(variant);
+  geno_blend(gc, IS, node ? gc.d_node : gc.d_iface, q, qx, PH, PHx, &out[0], &out[1], &out[2]);
+}
+double oracle_compact_flux(int variant, double chi, const double Fi[3], const double Fn[2]) {
+  return compact_flux(variant, chi, Fi, Fn);
+}
+
+// one interface solve; out = Fh[4], Fht[4], Whl[4], Whr[4], Whlt[4], Whrt[4], tau
+void oracle_iface_solve(const oracle_params* p, int normal, double dt, const double Wl[4], const double Wr[4],
+                        const double Wln[4], const double Wrn[4], const double Wt[4], double out[25]) {
+  Scheme S;
+  make_scheme(p, S);
+  IfaceOut o = iface_solve(S.gas, normal, dt, Wl, Wr, Wln, Wrn, Wt);
+  for (int c = 0; c < 4; ++c) {
+    out[c] = o.Fh[c]; out[4 + c] = o.Fht[c]; out[8 + c] = o.Whl[c];
+    out[12 + c] = o.Whr[c]; out[16 + c] = o.Whlt[c]; out[20 + c] = o.Whrt[c];
+  }
+  out[24] = o.tau;
+}
+
+// nodal flux; out = F[4], G[4], F_t[4], G_t[4]
+void oracle_nodal_flux(const oracle_params* p, double dt, const double W[4], const double Wx[4],
+                       const double Wy[4], double out[16]) {
+  Scheme S;
+  make_scheme(p, S);
+  nodal_flux(S.gas, dt, W, Wx, Wy, out);
+}
+
+}  // extern "C"

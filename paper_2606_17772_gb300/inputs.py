@@ -1,0 +1,223 @@
+"""Seeded synthetic inputs for FD-CGKS runs (initial data only).
+
+This module holds no arithmetic of the scheme.  It evaluates analytic initial
+conditions at the node positions of the primary and dual grids and forms the
+initial averaged gradients as the exact mean derivative over each node's
+interval, (W(x + h/2) - W(x - h/2)) / h (the definition of the averaged
+gradient, Sec. 2.3 of the paper, applied to the exact initial field).  The
+CUDA path and the CPU oracle both take their inputs from here.
+
+Workloads (paper Sec. 5 and the throughput workloads):
+  * density wave (Sec. 5.1): rho = 1 + 0.2 sin(pi (x + y)), U = V = 1, p = 1 on
+    [0, 2]^2 periodic; its 1-D form on a y-periodic strip;
+  * Sod tube (Sec. 5.2) on a y-periodic strip with transmissive x ends;
+  * isentropic vortex on [0, 10]^2 periodic (standard closed form, strength 5);
+  * viscous shock tube (Sec. 5.8) on [0, 1] x [0, 0.5] with walls/symmetry;
+  * a seeded random smooth perturbation used by the parity tests.
+
+Node placement: primary nodes at cell centres x0 + (i + 1/2) h, dual nodes at
+x0 + i h; a bounded direction carries n + 1 dual nodes (on both boundaries).
+"""
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+BC_PERIODIC, BC_TRANSMISSIVE, BC_SYMMETRY, BC_NOSLIP = 0, 1, 2, 3
+
+
+@dataclass
+class Case:
+    """A workload: grid, gas constants, boundary conditions and initial data."""
+    name: str
+    nx: int
+    ny: int
+    x0: float
+    x1: float
+    y0: float
+    y1: float
+    bc: tuple
+    gamma: float = 1.4
+    mu: float = 0.0
+    Pr: float = 1.0
+    tau_c1: float = 0.0
+    tau_c2: float = 0.0
+    flux_variant: int = 64
+    geno_variant: int = 0
+    grad_base: int = 0
+    prim: object = None          # callable (x, y) -> (rho, U, V, p) arrays
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def nxd(self):
+        return self.nx + (0 if self.bc[0] == BC_PERIODIC else 1)
+
+    @property
+    def nyd(self):
+        return self.ny + (0 if self.bc[2] == BC_PERIODIC else 1)
+
+    @property
+    def hx(self):
+        return (self.x1 - self.x0) / self.nx
+
+    @property
+    def hy(self):
+        return (self.y1 - self.y0) / self.ny
+
+    def node_xy(self, dual):
+        """Node coordinates (X, Y) arrays of shape (ny, nx) for one grid."""
+        if dual:
+            i = np.arange(self.nxd, dtype=np.float64)
+            j = np.arange(self.nyd, dtype=np.float64)
+            xs = self.x0 + (self.x1 - self.x0) * i / self.nx
+            ys = self.y0 + (self.y1 - self.y0) * j / self.ny
+        else:
+            i = np.arange(self.nx, dtype=np.float64)
+            j = np.arange(self.ny, dtype=np.float64)
+            xs = self.x0 + (self.x1 - self.x0) * (2 * i + 1) / (2 * self.nx)
+            ys = self.y0 + (self.y1 - self.y0) * (2 * j + 1) / (2 * self.ny)
+        return np.meshgrid(xs, ys)
+
+    def conservative(self, x, y):
+        rho, U, V, p = self.prim(x, y)
+        rho = np.broadcast_to(rho, np.shape(x)).astype(np.float64)
+        U = np.broadcast_to(U, np.shape(x)).astype(np.float64)
+        V = np.broadcast_to(V, np.shape(x)).astype(np.float64)
+        p = np.broadcast_to(p, np.shape(x)).astype(np.float64)
+        return np.stack([rho, rho * U, rho * V, p / (self.gamma - 1.0) + 0.5 * rho * (U * U + V * V)])
+
+    def initial_state(self):
+        """(Wp [4,ny,nx], Gp [2,4,ny,nx], Wd [4,nyd,nxd], Gd [2,4,nyd,nxd]) float64."""
+        out = []
+        for dual in (False, True):
+            X, Y = self.node_xy(dual)
+            W = self.conservative(X, Y)
+            gx = (self.conservative(X + 0.5 * self.hx, Y) - self.conservative(X - 0.5 * self.hx, Y)) / self.hx
+            gy = (self.conservative(X, Y + 0.5 * self.hy) - self.conservative(X, Y - 0.5 * self.hy)) / self.hy
+            out += [np.ascontiguousarray(W), np.ascontiguousarray(np.stack([gx, gy]))]
+        return tuple(out)
+
+    def oracle_kwargs(self):
+        return dict(nx=self.nx, ny=self.ny, x0=self.x0, x1=self.x1, y0=self.y0, y1=self.y1,
+                    gamma=self.gamma, mu=self.mu, Pr=self.Pr, bc=tuple(self.bc),
+                    flux_variant=self.flux_variant, geno_variant=self.geno_variant,
+                    grad_base=self.grad_base, tau_c1=self.tau_c1, tau_c2=self.tau_c2)
+
+
+# ---------------------------------------------------------------------------
+# analytic initial conditions
+# ---------------------------------------------------------------------------
+
+def density_wave_2d(n, t=0.0, **kw):
+    """Sec. 5.1, 2-D: rho = 1 + 0.2 sin(pi(x + y - 2t)), U = V = 1, p = 1 on [0,2]^2."""
+    def prim(x, y):
+        return 1.0 + 0.2 * np.sin(np.pi * (x + y - 2.0 * t)), 1.0, 1.0, 1.0
+    kw.setdefault("flux_variant", 62)
+    return Case("density_wave_2d", n, n, 0.0, 2.0, 0.0, 2.0, (0, 0, 0, 0), prim=prim, **kw)
+
+
+def density_wave_1d(n, ny=1, t=0.0, **kw):
+    """Sec. 5.1, 1-D on a y-periodic strip: rho = 1 + 0.2 sin(pi(x - t)), U = 1, V = 0, p = 1."""
+    h = 2.0 / n
+
+    def prim(x, y):
+        return 1.0 + 0.2 * np.sin(np.pi * (x - t)), 1.0, 0.0, 1.0
+    kw.setdefault("flux_variant", 62)
+    return Case("density_wave_1d", n, ny, 0.0, 2.0, 0.0, ny * h, (0, 0, 0, 0), prim=prim, **kw)
+
+
+def vortex(n, strength=5.0, xc=5.0, yc=5.0, t=0.0, L=10.0, gamma=1.4, **kw):
+    """Isentropic vortex on [0, L]^2 periodic, free stream (1, 1, 1, 1), advected to time t.
+
+    Standard closed form: with (xb, yb) the minimum-image offset from the
+    centre (xc + t, yc + t), r^2 = xb^2 + yb^2,
+      dU = -(eps/2pi) e^{(1-r^2)/2} yb,  dV = (eps/2pi) e^{(1-r^2)/2} xb,
+      T = 1 - (gamma-1) eps^2 / (8 gamma pi^2) e^{1-r^2},  rho = T^{1/(gamma-1)},  p = rho T.
+    """
+    eps = strength
+
+    def prim(x, y):
+        xb = np.mod(x - (xc + t) + 0.5 * L, L) - 0.5 * L
+        yb = np.mod(y - (yc + t) + 0.5 * L, L) - 0.5 * L
+        r2 = xb * xb + yb * yb
+        e = np.exp(0.5 * (1.0 - r2))
+        du = -eps / (2 * math.pi) * e * yb
+        dv = eps / (2 * math.pi) * e * xb
+        T = 1.0 - (gamma - 1.0) * eps * eps / (8.0 * gamma * math.pi ** 2) * np.exp(1.0 - r2)
+        rho = T ** (1.0 / (gamma - 1.0))
+        return rho, 1.0 + du, 1.0 + dv, rho * T
+    kw.setdefault("tau_c2", 1.0)
+    return Case("vortex", n, n, 0.0, L, 0.0, L, (0, 0, 0, 0), gamma=gamma, prim=prim,
+                extra=dict(strength=strength, xc=xc, yc=yc), **kw)
+
+
+def sod_strip(nx=200, ny=4, **kw):
+    """Sec. 5.2 Sod tube on [0,1], y-periodic strip of ny rows, transmissive x ends.
+
+    (rho, U, p) = (1, 0, 1) for x < 0.5 and (0.125, 0, 0.1) for x >= 0.5.
+    """
+    h = 1.0 / nx
+
+    def prim(x, y):
+        right = x >= 0.5
+        return np.where(right, 0.125, 1.0), 0.0, 0.0, np.where(right, 0.1, 1.0)
+    kw.setdefault("tau_c1", 0.05)
+    kw.setdefault("tau_c2", 1.0)
+    return Case("sod_strip", nx, ny, 0.0, 1.0, 0.0, ny * h, (1, 1, 0, 0), prim=prim, **kw)
+
+
+def viscous_shock_tube(nx=1000, ny=500, gamma=1.4, mu=0.005, Pr=0.73, **kw):
+    """Sec. 5.8: [0,1] x [0,0.5], diaphragm x = 0.5, (120,0,0,120/gamma) | (1.2,0,0,1.2/gamma).
+
+    No-slip adiabatic walls left, right and bottom; symmetry at y = 0.5.
+    """
+    def prim(x, y):
+        right = x >= 0.5
+        rho = np.where(right, 1.2, 120.0)
+        return rho, 0.0, 0.0, rho / gamma
+    kw.setdefault("tau_c2", 1.0)
+    return Case("viscous_shock_tube", nx, ny, 0.0, 1.0, 0.0, 0.5,
+                (BC_NOSLIP, BC_NOSLIP, BC_NOSLIP, BC_SYMMETRY), gamma=gamma, mu=mu, Pr=Pr,
+                prim=prim, **kw)
+
+
+def random_smooth(nx, ny, seed, amp=0.05, modes=4, bc=(0, 0, 0, 0), **kw):
+    """Seeded random smooth field: a free stream plus `modes` random Fourier modes per variable.
+
+    Used by the parity tests to exercise every term with non-trivial data.
+    On bounded directions the field is still smooth (the modes need not match
+    the boundaries: the ghost treatment then creates weak discontinuities,
+    which exercise the nonlinear weights too).
+    """
+    rng = np.random.default_rng(seed)
+    Lx, Ly = 1.0, ny / nx
+    k = rng.integers(1, 4, size=(4, modes, 2))
+    ph = rng.uniform(0, 2 * math.pi, size=(4, modes))
+    a = rng.uniform(-amp, amp, size=(4, modes))
+    base = np.array([1.0, 0.6, -0.4, 1.0])
+
+    def prim(x, y):
+        out = []
+        for v in range(4):
+            f = np.full(np.shape(x), base[v])
+            for m in range(modes):
+                f = f + a[v, m] * np.sin(2 * math.pi * (k[v, m, 0] * x / Lx + k[v, m, 1] * y / Ly) + ph[v, m])
+            out.append(f)
+        return tuple(out)
+    return Case("random_smooth", nx, ny, 0.0, Lx, 0.0, Ly, tuple(bc), prim=prim, extra=dict(seed=seed), **kw)
+
+
+def ensemble_members(count=256, seed=0, nmin=32, nmax=512, L=10.0):
+    """Seeded ensemble of periodic isentropic vortices on uneven grids.
+
+    Grid sizes log-uniform in [nmin, nmax] (rounded), strength uniform in
+    [1, 5], centre uniform in the domain.  Returns a list of Case objects.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(round(math.exp(rng.uniform(math.log(nmin), math.log(nmax)))))
+        eps = rng.uniform(1.0, 5.0)
+        xc, yc = rng.uniform(0.0, L, size=2)
+        out.append(vortex(n, strength=eps, xc=xc, yc=yc, L=L))
+    return out
