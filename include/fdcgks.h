@@ -1,0 +1,166 @@
+/*
+ * fdcgks.h -- C ABI of the GB300 FD-CGKS library (libfdcgks.so).
+ *
+ * The library advances the two-dimensional finite-difference compact
+ * gas-kinetic scheme of "Finite Difference Implementation of a High-order
+ * Space-Time Coupled Compact Gas-Kinetic Scheme" (Zhao, Chen, Xu) on one GPU:
+ * the conservative variables W = (rho, rho U, rho V, rho E) and the averaged
+ * spatial gradients of W on a primary grid and on a dual grid offset by half a
+ * spacing in both directions (Sec. 4), evolved by the S2O4 two-stage scheme
+ * (Sec. 2.4) with the space-time coupled BGK interface solution (App. A) and
+ * GENO-blended compact reconstruction (Sec. 3).
+ *
+ * Conventions for every entry point:
+ *   - Status codes; nothing aborts, exits or traps on the device.  A failed
+ *     call leaves a message readable with fdcgks_last_error().
+ *   - Arrays are float64, C order.  Conservative fields W: [4][ny][nx];
+ *     gradients: [2][4][ny][nx] (averaged x-gradient, then y-gradient).
+ *     Dual-grid arrays use (nyd, nxd) from fdcgks_dims().
+ *   - "on_device" selects device pointers (stream-ordered on the context's
+ *     stream) or host pointers (the call returns after the copy completed).
+ *   - The caller owns every pointer it passes; the library never frees or
+ *     retains caller memory.  The context owns its device buffers.
+ *   - All work is issued on params.stream (a cudaStream_t; NULL = legacy
+ *     default stream).
+ *   - Node placement: primary nodes at cell centres x0 + (i + 1/2) hx, dual
+ *     nodes at x0 + i hx.  A bounded direction carries n + 1 dual nodes (the
+ *     outermost lie on the boundaries); a periodic one carries n.
+ */
+#ifndef FDCGKS_H
+#define FDCGKS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fdcgks_ctx* fdcgks_t;
+
+typedef enum {
+  FDCGKS_OK = 0,
+  FDCGKS_ERR_ARG = 1,          /* invalid argument (sizes, variants, dt, pointers) */
+  FDCGKS_ERR_CUDA = 2,         /* a CUDA call failed; see fdcgks_last_error */
+  FDCGKS_ERR_NONPHYSICAL = 3,  /* non-positive or non-finite density or pressure found */
+  FDCGKS_ERR_STATE = 4,        /* step or get_state before set_state */
+  FDCGKS_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
+  FDCGKS_ERR_NOMEM = 6         /* device allocation failed */
+} fdcgks_status;
+
+/* Boundary conditions (Sec. 5 test problems; ghost rules are this library's
+ * reading, the paper does not describe them):
+ *   PERIODIC      wrap (must be set on both sides of a direction)
+ *   TRANSMISSIVE  zero-gradient: ghosts copy the boundary node, zero gradients
+ *   SYMMETRY      mirror; normal momentum odd, all else even
+ *   NOSLIP        adiabatic no-slip wall: mirror with both momenta odd; dual
+ *                 nodes on the wall have their velocity set to zero after each stage */
+typedef enum {
+  FDCGKS_BC_PERIODIC = 0,
+  FDCGKS_BC_TRANSMISSIVE = 1,
+  FDCGKS_BC_SYMMETRY = 2,
+  FDCGKS_BC_NOSLIP = 3
+} fdcgks_bc;
+
+typedef enum { FDCGKS_FP64 = 0, FDCGKS_MIXED = 1 } fdcgks_precision;
+
+typedef struct {
+  int nx, ny;                 /* primary nodes per direction (>= 1) */
+  double x0, x1, y0, y1;      /* domain; hx = (x1 - x0)/nx, hy = (y1 - y0)/ny */
+  double gamma;               /* ratio of specific heats (> 1) */
+  double mu;                  /* dynamic viscosity (>= 0; 0 = inviscid) */
+  double Pr;                  /* Prandtl number (> 0) */
+  int bc[4];                  /* fdcgks_bc for x-low, x-high, y-low, y-high */
+  int flux_variant;           /* 64: FD-CGKS(6-4), Eq. fd-conservative-flux-2 (default);
+                                 62: FD-CGKS(6-2), Eq. fd-conservative-flux-1 */
+  int geno_variant;           /* 0: Sec. 3.2 constants (r=2, eps=1e-12, d=(8,1,1));
+                                 1: App. D constants (r=3, eps=1e-15, d=8 on the central stencil);
+                                 2: linear reconstruction and flux (chi = 1) */
+  int grad_base;              /* Eq. eq-interface-update base: 0 = re-evaluated from the
+                                 interface solution at t^n (default), 1 = stored gradient */
+  int precision;              /* fdcgks_precision: FP64, or MIXED (FP32 reconstruction and
+                                 flux arithmetic, FP64 state, accumulation and time coefficients) */
+  double tau_c1, tau_c2;      /* collision time tau = c1 dt + mu/p + c2 dt |pl - pr|/(pl + pr)
+                                 at interfaces, c1 dt + mu/p at nodes (paper App. A cites the
+                                 GKS literature for tau; these constants are run parameters) */
+  void* stream;               /* cudaStream_t for all work; NULL = legacy default stream */
+} fdcgks_params;
+
+/* Create a context: validates params and allocates the device buffers of the
+ * state (both grids, padded with 3 ghost layers), the S2O4 stage state and
+ * the per-stage interface/nodal intermediates.  *out is NULL on failure. */
+fdcgks_status fdcgks_create(const fdcgks_params* params, fdcgks_t* out);
+
+/* Release a context and its device memory.  NULL is accepted. */
+void fdcgks_destroy(fdcgks_t ctx);
+
+/* Interior node counts of the primary (nx, ny) and dual (nxd, nyd) grids. */
+fdcgks_status fdcgks_dims(fdcgks_t ctx, int* nx, int* ny, int* nxd, int* nyd);
+
+/* Load W and averaged gradients of both grids (layouts above).  Validates
+ * that density and pressure are positive and finite everywhere
+ * (FDCGKS_ERR_NONPHYSICAL otherwise; the state is then not marked loaded). */
+fdcgks_status fdcgks_set_state(fdcgks_t ctx, const double* Wp, const double* Gp, const double* Wd,
+                               const double* Gd, int on_device);
+
+/* Copy W and averaged gradients of both grids out (layouts above). */
+fdcgks_status fdcgks_get_state(fdcgks_t ctx, double* Wp, double* Gp, double* Wd, double* Gd, int on_device);
+
+/* One S2O4 step of size dt (> 0, finite): Eqs. eq-nodal-update and
+ * eq-interface-update, each stage evaluating the compact nonlinear flux
+ * (Eqs. fd-conservative-flux, -flux-1/-2) of GENO-reconstructed (Sec. 3)
+ * kinetic interface and nodal fluxes (App. A) on both grids (Sec. 4).
+ * Asynchronous on the context stream.  A non-physical result sets a device
+ * flag read by fdcgks_check(). */
+fdcgks_status fdcgks_step(fdcgks_t ctx, double dt);
+
+/* nsteps consecutive steps of size dt (same semantics as fdcgks_step). */
+fdcgks_status fdcgks_steps(fdcgks_t ctx, double dt, int nsteps);
+
+/* CFL time step (Sec. 5): cfl * min over all nodes of both grids of
+ * min(hx/(|U|+c), hy/(|V|+c)); with mu > 0 also bounded by
+ * cfl * min(hx,hy)^2 / (8 nu_max), nu = mu/rho.  Synchronizes the stream. */
+fdcgks_status fdcgks_cfl_dt(fdcgks_t ctx, double cfl, double* dt_out);
+
+/* Read and clear the device non-physical flag (synchronizes the stream).
+ * *nonphysical = 1 if a step produced non-positive/non-finite rho or p. */
+fdcgks_status fdcgks_check(fdcgks_t ctx, int* nonphysical);
+
+/* One stage's spatial operator on the current state, without advancing it:
+ * L and dL/dt (Eq. eq-conservation-law-2d applied to the fluxes and their time
+ * derivatives), the averaged gradients re-evaluated from the interface
+ * solution (Eq. define-averaged-gradient) and their time derivatives.  Device
+ * pointers, interior layouts: L* [4][ny][nx], g* [2][4][ny][nx] (dual arrays
+ * over nyd, nxd).  Used to check the kernels stage by stage. */
+fdcgks_status fdcgks_stage_operator(fdcgks_t ctx, double dt, double* Lp, double* Ltp, double* gbp, double* gtp,
+                                    double* Ld, double* Ltd, double* gbd, double* gtd);
+
+/* Batched kinetic interface solve (App. A1-A2, Eq. eq:W-model), normal 0 = x,
+ * 1 = y, on device arrays: in [n][20] = Wl[4], Wr[4], normal derivatives
+ * Wl_n[4], Wr_n[4], tangential derivative Wt[4]; out [n][24] = F[4], F_t[4],
+ * W^l[4], W^r[4], W^l_t[4], W^r_t[4].  Uses params' gas, tau constants and
+ * precision; dt is the step size.  Asynchronous on params->stream. */
+fdcgks_status fdcgks_iface_batch(const fdcgks_params* params, int normal, double dt, int n, const double* in,
+                                 double* out);
+
+/* Batched nodal flux (Sec. 2.1) on device arrays: in [n][12] = W[4], W_x[4],
+ * W_y[4]; out [n][16] = F[4], G[4], F_t[4], G_t[4]. */
+fdcgks_status fdcgks_nodal_batch(const fdcgks_params* params, double dt, int n, const double* in, double* out);
+
+/* Batched GENO reconstruction (Sec. 3) on device arrays.  kind 0: interface
+ * between entries 1 and 2 of a 4-point line, in [n][8] = Q[4], Qx[4];
+ * out [n][6] = value_l, derivative_l, chi_l, value_r, derivative_r, chi_r.
+ * kind 1: node derivative, in [n][6] = Q[3], Qx[3]; out [n][6] = derivative, 0...
+ * h is the spacing. */
+fdcgks_status fdcgks_recon_batch(const fdcgks_params* params, int kind, double h, int n, const double* in,
+                                 double* out);
+
+/* Message of the last failed call on ctx (or of the last failed
+ * context-free call when ctx is NULL). */
+const char* fdcgks_last_error(fdcgks_t ctx);
+
+/* Static name of a status code. */
+const char* fdcgks_status_string(fdcgks_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDCGKS_H */

@@ -39,7 +39,8 @@
 //     corners; n dual nodes per periodic direction, n+1 per bounded one.
 //     Ghost layers by periodic wrap, mirror (symmetry / no-slip wall) or
 //     constant extrapolation (transmissive).  Dual nodes on a no-slip wall
-//     have their velocity set to zero after each stage.
+//     have their velocity, and the averaged momentum gradients along the
+//     wall, set to zero after each stage.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -890,6 +891,7 @@ bool make_scheme(const oracle_params* p, Scheme& S) {
     bool a = p->bc[2 * d] == OBC_PERIODIC, b = p->bc[2 * d + 1] == OBC_PERIODIC;
     if (a != b) return false;
   }
+  if ((p->bc[0] != OBC_PERIODIC && p->nx < 3) || (p->bc[2] != OBC_PERIODIC && p->ny < 3)) return false;
   S.nxd = p->nx + (p->bc[0] == OBC_PERIODIC ? 0 : 1);
   S.nyd = p->ny + (p->bc[2] == OBC_PERIODIC ? 0 : 1);
   S.hx = (p->x1 - p->x0) / p->nx;
@@ -941,6 +943,11 @@ void noslip_reset(const Scheme& S, Grid& D) {
       D.at(1, i, j) = 0.0;
       D.at(2, i, j) = 0.0;
       D.at(3, i, j) -= ke;
+      // U = V = 0 along the whole wall, so the momentum gradients along it vanish too
+      bool xwall = (bc[0] == OBC_NOSLIP && i == 0) || (bc[1] == OBC_NOSLIP && i == S.nxd - 1);
+      bool ywall = (bc[2] == OBC_NOSLIP && j == 0) || (bc[3] == OBC_NOSLIP && j == S.nyd - 1);
+      if (xwall) { D.at(8 + 1, i, j) = 0.0; D.at(8 + 2, i, j) = 0.0; }
+      if (ywall) { D.at(4 + 1, i, j) = 0.0; D.at(4 + 2, i, j) = 0.0; }
     }
 }
 

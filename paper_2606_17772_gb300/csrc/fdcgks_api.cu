@@ -1,0 +1,543 @@
+// Host runtime and C entry points of the FD-CGKS library: context and device
+// buffers, ghost-layer fill, CFL reduction, stage sequencing of the S2O4 step.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/fdcgks.h"
+#include "fdcgks_internal.cuh"
+
+using namespace fdk;
+
+struct fdcgks_ctx {
+  fdcgks_params p;
+  Layout L;
+  double hx, hy;
+  cudaStream_t stream;
+  double* S = nullptr;      // state [2][12][plane]
+  double* S2 = nullptr;     // stage state
+  double* Wacc = nullptr;   // [2][4][plane]
+  double* gB = nullptr;     // [2][8][plane]
+  void* NF = nullptr;       // nodal fluxes [2][16][plane] of the compute type
+  void* PA = nullptr;       // point outputs [50][pplane]
+  void* PB = nullptr;
+  int* flag = nullptr;      // device flags
+  double* red = nullptr;    // reduction scratch
+  int red_blocks = 0;
+  bool has_state = false;
+  char err[512];
+};
+
+static char g_err[512] = "";
+
+static fdcgks_status fail(fdcgks_t c, fdcgks_status s, const char* fmt, ...) {
+  char* dst = c ? c->err : g_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 512, fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define CUDA_TRY(ctx, expr)                                                                              \
+  do {                                                                                                   \
+    cudaError_t e_ = (expr);                                                                             \
+    if (e_ != cudaSuccess) return fail(ctx, FDCGKS_ERR_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), \
+                                       __FILE__, __LINE__);                                              \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// run constants
+// ---------------------------------------------------------------------------
+template <class R>
+static GenoK<R> make_geno(int variant) {
+  GenoK<R> g;
+  g.linear = variant == 2;
+  g.C = (R)20.0;
+  g.tanhC = (R)std::tanh(20.0);
+  g.eps_w = (R)1e-6;
+  if (variant == 1) {
+    g.r = 3;
+    g.eps_a = (R)1e-15;
+    g.d_iface[0] = 1; g.d_iface[1] = 8; g.d_iface[2] = 1;
+  } else {
+    g.r = 2;
+    g.eps_a = (R)1e-12;
+    g.d_iface[0] = 8; g.d_iface[1] = 1; g.d_iface[2] = 1;
+  }
+  g.d_node[0] = 8; g.d_node[1] = 1; g.d_node[2] = 1;
+  return g;
+}
+
+template <class R>
+static GasK<R> make_gas(const fdcgks_params& p, double dt) {
+  GasK<R> g;
+  g.K = (R)((4.0 - 2.0 * p.gamma) / (p.gamma - 1.0));
+  g.prfix = (R)(1.0 / p.Pr - 1.0);
+  g.mu = p.mu;
+  g.c1 = p.tau_c1;
+  g.c2 = p.tau_c2;
+  g.dt = dt;
+  return g;
+}
+
+static const char* check_params(const fdcgks_params* p) {
+  if (!p) return "params is NULL";
+  if (p->nx < 1 || p->ny < 1) return "nx and ny must be >= 1";
+  if (p->nx > (1 << 20) || p->ny > (1 << 20)) return "nx or ny too large";
+  if (!(p->x1 > p->x0) || !(p->y1 > p->y0)) return "domain extents must be positive";
+  if (!(p->gamma > 1.0) || !std::isfinite(p->gamma)) return "gamma must be > 1";
+  if (!(p->mu >= 0.0) || !std::isfinite(p->mu)) return "mu must be >= 0";
+  if (!(p->Pr > 0.0) || !std::isfinite(p->Pr)) return "Pr must be > 0";
+  for (int k = 0; k < 4; ++k)
+    if (p->bc[k] < 0 || p->bc[k] > 3) return "unknown boundary condition";
+  for (int d = 0; d < 2; ++d)
+    if ((p->bc[2 * d] == FDCGKS_BC_PERIODIC) != (p->bc[2 * d + 1] == FDCGKS_BC_PERIODIC))
+      return "periodic boundaries must be paired";
+  if ((p->bc[0] != FDCGKS_BC_PERIODIC && p->nx < 3) || (p->bc[2] != FDCGKS_BC_PERIODIC && p->ny < 3))
+    return "a bounded direction needs at least 3 nodes";
+  if (p->flux_variant != 62 && p->flux_variant != 64) return "flux_variant must be 62 or 64";
+  if (p->geno_variant < 0 || p->geno_variant > 2) return "geno_variant must be 0, 1 or 2";
+  if (p->grad_base != 0 && p->grad_base != 1) return "grad_base must be 0 or 1";
+  if (p->precision != FDCGKS_FP64 && p->precision != FDCGKS_MIXED) return "precision must be 0 or 1";
+  if (!(p->tau_c1 >= 0.0) || !(p->tau_c2 >= 0.0)) return "tau constants must be >= 0";
+  return nullptr;
+}
+
+static size_t rsize(const fdcgks_params& p) { return p.precision == FDCGKS_MIXED ? sizeof(float) : sizeof(double); }
+
+// ---------------------------------------------------------------------------
+// ghost fill: periodic wrap, mirror (symmetry / no-slip) or constant
+// extrapolation (transmissive); x pass over interior rows, then y pass over
+// all columns so that corners are filled consistently
+// ---------------------------------------------------------------------------
+__global__ void ghost_kernel(double* S, Layout L, int bc0, int bc1, int dir) {
+  const int g = blockIdx.z;
+  const int nxg = g == 0 ? L.nx : L.nxd, nyg = g == 0 ? L.ny : L.nyd;
+  const int n = dir == 0 ? nxg : nyg;
+  const int tcount = dir == 0 ? nyg : nxg + 2 * GH;
+  const int toff = dir == 0 ? 0 : -GH;
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;   // over (t, side, k)
+  if (idx >= tcount * 2 * GH) return;
+  const int k = 1 + idx % GH;
+  const int side = (idx / GH) % 2;
+  const int t = idx / (2 * GH) + toff;
+  const int b = side == 0 ? bc0 : bc1;
+  const int ghost = side == 0 ? -k : n - 1 + k;
+  int src;
+  if (b == FDCGKS_BC_PERIODIC) src = ((ghost % n) + n) % n;   // also for n < GH
+  else if (b == FDCGKS_BC_TRANSMISSIVE) src = side == 0 ? 0 : n - 1;
+  else if (g == 0) src = side == 0 ? k - 1 : n - k;
+  else src = side == 0 ? k : n - 1 - k;
+  const long gc = dir == 0 ? cell(L, ghost, t) : cell(L, t, ghost);
+  const long sc = dir == 0 ? cell(L, src, t) : cell(L, t, src);
+  double* Sg = S + (long)g * NFLD * L.plane;
+  for (int c = 0; c < 4; ++c) {
+    double sW = 1.0;
+    if (b == FDCGKS_BC_SYMMETRY || b == FDCGKS_BC_NOSLIP) {
+      if (c == 1 + dir) sW = -1.0;
+      if (c == 2 - dir && b == FDCGKS_BC_NOSLIP) sW = -1.0;
+    }
+    double w = Sg[(long)c * L.plane + sc];
+    double gx = Sg[(long)(4 + c) * L.plane + sc];
+    double gy = Sg[(long)(8 + c) * L.plane + sc];
+    if (b == FDCGKS_BC_TRANSMISSIVE) {
+      gx = 0.0;
+      gy = 0.0;
+    } else if (b != FDCGKS_BC_PERIODIC) {
+      w *= sW;
+      gx *= (dir == 0 ? -sW : sW);
+      gy *= (dir == 1 ? -sW : sW);
+    }
+    Sg[(long)c * L.plane + gc] = w;
+    Sg[(long)(4 + c) * L.plane + gc] = gx;
+    Sg[(long)(8 + c) * L.plane + gc] = gy;
+  }
+}
+
+static cudaError_t fill_ghosts(fdcgks_t c, double* S) {
+  const Layout& L = c->L;
+  int tx = (L.ny > L.nyd ? L.ny : L.nyd) * 2 * GH;
+  ghost_kernel<<<dim3((tx + 127) / 128, 1, 2), 128, 0, c->stream>>>(S, L, c->p.bc[0], c->p.bc[1], 0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int ty = ((L.nx > L.nxd ? L.nx : L.nxd) + 2 * GH) * 2 * GH;
+  ghost_kernel<<<dim3((ty + 127) / 128, 1, 2), 128, 0, c->stream>>>(S, L, c->p.bc[2], c->p.bc[3], 1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// state validation and CFL reduction
+// ---------------------------------------------------------------------------
+__global__ void validate_kernel(const double* S, Layout L, double gamma, int* flag) {
+  const int g = blockIdx.z;
+  const int nxg = g == 0 ? L.nx : L.nxd, nyg = g == 0 ? L.ny : L.nyd;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i >= nxg || j >= nyg) return;
+  const double* Sg = S + (long)g * NFLD * L.plane;
+  const long c0 = cell(L, i, j);
+  double r = Sg[c0], mu_ = Sg[L.plane + c0], mv_ = Sg[2 * L.plane + c0], E = Sg[3 * L.plane + c0];
+  double p = (gamma - 1.0) * (E - 0.5 * (mu_ * mu_ + mv_ * mv_) / r);
+  bool ok = r > 0.0 && p > 0.0 && r < INFINITY && p < INFINITY;
+  for (int f = 4; f < NFLD; ++f) ok = ok && fabs(Sg[(long)f * L.plane + c0]) < INFINITY;
+  if (!ok) atomicOr(flag, 1);
+}
+
+// per-block maxima of (|U|+c)/hx, (|V|+c)/hy (as one rate) and nu = mu/rho
+__global__ void cfl_kernel(const double* S, Layout L, double gamma, double mu, double ihx, double ihy, double* out) {
+  double rate = 0.0, numax = 0.0;
+  const long n0 = (long)L.nx * L.ny, n1 = (long)L.nxd * L.nyd;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n0 + n1; t += (long)gridDim.x * blockDim.x) {
+    int g = t < n0 ? 0 : 1;
+    long q = g == 0 ? t : t - n0;
+    int nxg = g == 0 ? L.nx : L.nxd;
+    int i = (int)(q % nxg), j = (int)(q / nxg);
+    const double* Sg = S + (long)g * NFLD * L.plane;
+    const long c0 = cell(L, i, j);
+    double r = Sg[c0], U = Sg[L.plane + c0] / r, V = Sg[2 * L.plane + c0] / r;
+    double p = (gamma - 1.0) * (Sg[3 * L.plane + c0] - 0.5 * r * (U * U + V * V));
+    double cs = sqrt(gamma * p / r);
+    rate = fmax(rate, fmax((fabs(U) + cs) * ihx, (fabs(V) + cs) * ihy));
+    numax = fmax(numax, mu / r);
+  }
+  // warp-shuffle max, then across warps in shared memory
+  for (int o = 16; o > 0; o >>= 1) {
+    rate = fmax(rate, __shfl_xor_sync(0xffffffffu, rate, o));
+    numax = fmax(numax, __shfl_xor_sync(0xffffffffu, numax, o));
+  }
+  __shared__ double sr[32], sn[32];
+  int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  if (l == 0) { sr[w] = rate; sn[w] = numax; }
+  __syncthreads();
+  if (w == 0) {
+    int nw = blockDim.x / 32;
+    rate = l < nw ? sr[l] : 0.0;
+    numax = l < nw ? sn[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      rate = fmax(rate, __shfl_xor_sync(0xffffffffu, rate, o));
+      numax = fmax(numax, __shfl_xor_sync(0xffffffffu, numax, o));
+    }
+    if (l == 0) { out[2 * blockIdx.x] = rate; out[2 * blockIdx.x + 1] = numax; }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// stage sequencing
+// ---------------------------------------------------------------------------
+template <class R>
+static KArgs<R> make_args(fdcgks_t c, double dt, const double* S, double* Sout, int want_n) {
+  KArgs<R> a;
+  std::memset(&a, 0, sizeof(a));
+  a.L = c->L;
+  a.S = S;
+  a.Sn = c->S;
+  a.Sout = Sout;
+  a.Wacc = c->Wacc;
+  a.gB = c->gB;
+  a.NF = (R*)c->NF;
+  a.PA = (R*)c->PA;
+  a.PB = (R*)c->PB;
+  a.geno = make_geno<R>(c->p.geno_variant);
+  a.gas = make_gas<R>(c->p, dt);
+  a.hd[0] = c->hx; a.hd[1] = c->hy;
+  a.ihd[0] = 1.0 / c->hx; a.ihd[1] = 1.0 / c->hy;
+  a.h[0] = (R)c->hx; a.h[1] = (R)c->hy;
+  a.ih[0] = (R)(1.0 / c->hx); a.ih[1] = (R)(1.0 / c->hy);
+  for (int k = 0; k < 4; ++k) a.bc[k] = c->p.bc[k];
+  a.flux_variant = c->p.flux_variant;
+  a.grad_base = c->p.grad_base;
+  a.want_n = want_n;
+  a.dt = dt;
+  a.flag = c->flag;
+  return a;
+}
+
+template <class R>
+static fdcgks_status run_stage(fdcgks_t c, double dt, int mode, double* const* op) {
+  const double* S = mode == UPD_STAGE2 ? c->S2 : c->S;
+  double* Sout = mode == UPD_STAGE1 ? c->S2 : c->S;
+  CUDA_TRY(c, fill_ghosts(c, const_cast<double*>(S)));
+  KArgs<R> a = make_args<R>(c, dt, S, Sout, mode != UPD_STAGE2);
+  if (op)
+    for (int k = 0; k < 8; ++k) a.op[k] = op[k];
+  CUDA_TRY(c, launch_nodal<R>(a, c->stream));
+  CUDA_TRY(c, launch_points<R>(a, c->stream));
+  CUDA_TRY(c, launch_update<R>(a, mode, c->stream));
+  return FDCGKS_OK;
+}
+
+template <class R>
+static fdcgks_status run_step(fdcgks_t c, double dt) {
+  fdcgks_status s = run_stage<R>(c, dt, UPD_STAGE1, nullptr);
+  if (s != FDCGKS_OK) return s;
+  return run_stage<R>(c, dt, UPD_STAGE2, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// C entry points
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* fdcgks_status_string(fdcgks_status s) {
+  switch (s) {
+    case FDCGKS_OK: return "ok";
+    case FDCGKS_ERR_ARG: return "invalid argument";
+    case FDCGKS_ERR_CUDA: return "CUDA error";
+    case FDCGKS_ERR_NONPHYSICAL: return "non-physical state";
+    case FDCGKS_ERR_STATE: return "no state loaded";
+    case FDCGKS_ERR_TIMEOUT: return "device wait timed out";
+    case FDCGKS_ERR_NOMEM: return "out of device memory";
+  }
+  return "unknown status";
+}
+
+const char* fdcgks_last_error(fdcgks_t ctx) { return ctx ? ctx->err : g_err; }
+
+void fdcgks_destroy(fdcgks_t c) {
+  if (!c) return;
+  void* bufs[] = {c->S, c->S2, c->Wacc, c->gB, c->NF, c->PA, c->PB, c->flag, c->red};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  delete c;
+}
+
+fdcgks_status fdcgks_create(const fdcgks_params* p, fdcgks_t* out) {
+  if (!out) return fail(nullptr, FDCGKS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (const char* m = check_params(p)) return fail(nullptr, FDCGKS_ERR_ARG, "%s", m);
+  fdcgks_t c = new (std::nothrow) fdcgks_ctx();
+  if (!c) return fail(nullptr, FDCGKS_ERR_NOMEM, "host allocation failed");
+  c->p = *p;
+  c->err[0] = 0;
+  c->stream = (cudaStream_t)p->stream;
+  c->hx = (p->x1 - p->x0) / p->nx;
+  c->hy = (p->y1 - p->y0) / p->ny;
+  Layout& L = c->L;
+  L.nx = p->nx;
+  L.ny = p->ny;
+  L.nxd = p->nx + (p->bc[0] == FDCGKS_BC_PERIODIC ? 0 : 1);
+  L.nyd = p->ny + (p->bc[2] == FDCGKS_BC_PERIODIC ? 0 : 1);
+  int mx = L.nx > L.nxd ? L.nx : L.nxd, my = L.ny > L.nyd ? L.ny : L.nyd;
+  L.pitch = ((mx + 2 * GH) + 31) / 32 * 32;
+  L.rows = my + 2 * GH;
+  L.plane = (long)L.pitch * L.rows;
+  L.ppitch = ((mx + 3) + 31) / 32 * 32;
+  L.prows = my + 3;
+  L.pplane = (long)L.ppitch * L.prows;
+  const size_t rs = rsize(*p);
+  struct { void** ptr; size_t bytes; } allocs[] = {
+      {(void**)&c->S, sizeof(double) * 2 * NFLD * L.plane},
+      {(void**)&c->S2, sizeof(double) * 2 * NFLD * L.plane},
+      {(void**)&c->Wacc, sizeof(double) * 2 * 4 * L.plane},
+      {(void**)&c->gB, sizeof(double) * 2 * 8 * L.plane},
+      {&c->NF, rs * 2 * NNF * L.plane},
+      {&c->PA, rs * NPT * L.pplane},
+      {&c->PB, rs * NPT * L.pplane},
+      {(void**)&c->flag, sizeof(int) * 4},
+  };
+  for (auto& a : allocs) {
+    cudaError_t e = cudaMalloc(a.ptr, a.bytes);
+    if (e != cudaSuccess) {
+      fail(nullptr, e == cudaErrorMemoryAllocation ? FDCGKS_ERR_NOMEM : FDCGKS_ERR_CUDA, "cudaMalloc(%zu): %s",
+           a.bytes, cudaGetErrorString(e));
+      fdcgks_destroy(c);
+      return e == cudaErrorMemoryAllocation ? FDCGKS_ERR_NOMEM : FDCGKS_ERR_CUDA;
+    }
+  }
+  c->red_blocks = 1024;
+  if (cudaMalloc((void**)&c->red, sizeof(double) * 2 * c->red_blocks) != cudaSuccess) {
+    fdcgks_destroy(c);
+    return fail(nullptr, FDCGKS_ERR_NOMEM, "cudaMalloc of the reduction scratch failed");
+  }
+  // zero everything once so that ghost corners and unused entries are defined
+  cudaError_t e = cudaSuccess;
+  e = e == cudaSuccess ? cudaMemsetAsync(c->S, 0, sizeof(double) * 2 * NFLD * L.plane, c->stream) : e;
+  e = e == cudaSuccess ? cudaMemsetAsync(c->S2, 0, sizeof(double) * 2 * NFLD * L.plane, c->stream) : e;
+  e = e == cudaSuccess ? cudaMemsetAsync(c->flag, 0, sizeof(int) * 4, c->stream) : e;
+  e = e == cudaSuccess ? cudaStreamSynchronize(c->stream) : e;
+  if (e != cudaSuccess) {
+    fdcgks_destroy(c);
+    return fail(nullptr, FDCGKS_ERR_CUDA, "initialisation: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  return FDCGKS_OK;
+}
+
+fdcgks_status fdcgks_dims(fdcgks_t c, int* nx, int* ny, int* nxd, int* nyd) {
+  if (!c) return fail(nullptr, FDCGKS_ERR_ARG, "ctx is NULL");
+  if (nx) *nx = c->L.nx;
+  if (ny) *ny = c->L.ny;
+  if (nxd) *nxd = c->L.nxd;
+  if (nyd) *nyd = c->L.nyd;
+  return FDCGKS_OK;
+}
+
+// copy one interior field plane between a dense [ny][nx] array and the padded layout
+static cudaError_t copy_field(fdcgks_t c, double* dev_plane, const double* src, double* dst, int nxg, int nyg,
+                              bool to_dev, int on_device) {
+  const Layout& L = c->L;
+  double* d0 = dev_plane + cell(L, 0, 0);
+  cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : (to_dev ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost);
+  if (to_dev)
+    return cudaMemcpy2DAsync(d0, sizeof(double) * L.pitch, src, sizeof(double) * nxg, sizeof(double) * nxg, nyg, k,
+                             c->stream);
+  return cudaMemcpy2DAsync(dst, sizeof(double) * nxg, d0, sizeof(double) * L.pitch, sizeof(double) * nxg, nyg, k,
+                           c->stream);
+}
+
+fdcgks_status fdcgks_set_state(fdcgks_t c, const double* Wp, const double* Gp, const double* Wd, const double* Gd,
+                               int on_device) {
+  if (!c) return fail(nullptr, FDCGKS_ERR_ARG, "ctx is NULL");
+  if (!Wp || !Gp || !Wd || !Gd) return fail(c, FDCGKS_ERR_ARG, "NULL state pointer");
+  const Layout& L = c->L;
+  const double* srcW[2] = {Wp, Wd};
+  const double* srcG[2] = {Gp, Gd};
+  for (int g = 0; g < 2; ++g) {
+    int nxg = g == 0 ? L.nx : L.nxd, nyg = g == 0 ? L.ny : L.nyd;
+    long NN = (long)nxg * nyg;
+    double* Sg = c->S + (long)g * NFLD * L.plane;
+    for (int f = 0; f < NFLD; ++f) {
+      const double* src = f < 4 ? srcW[g] + f * NN : srcG[g] + (f - 4) * NN;
+      CUDA_TRY(c, copy_field(c, Sg + (long)f * L.plane, src, nullptr, nxg, nyg, true, on_device));
+    }
+  }
+  CUDA_TRY(c, cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+  int mx = L.nx > L.nxd ? L.nx : L.nxd, my = L.ny > L.nyd ? L.ny : L.nyd;
+  validate_kernel<<<dim3((mx + 127) / 128, my, 2), 128, 0, c->stream>>>(c->S, L, c->p.gamma, c->flag);
+  CUDA_TRY(c, cudaGetLastError());
+  int h = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&h, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (h) {
+    c->has_state = false;
+    CUDA_TRY(c, cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+    return fail(c, FDCGKS_ERR_NONPHYSICAL, "state has non-positive or non-finite density/pressure");
+  }
+  c->has_state = true;
+  return FDCGKS_OK;
+}
+
+fdcgks_status fdcgks_get_state(fdcgks_t c, double* Wp, double* Gp, double* Wd, double* Gd, int on_device) {
+  if (!c) return fail(nullptr, FDCGKS_ERR_ARG, "ctx is NULL");
+  if (!c->has_state) return fail(c, FDCGKS_ERR_STATE, "no state loaded");
+  if (!Wp || !Gp || !Wd || !Gd) return fail(c, FDCGKS_ERR_ARG, "NULL state pointer");
+  const Layout& L = c->L;
+  double* dstW[2] = {Wp, Wd};
+  double* dstG[2] = {Gp, Gd};
+  for (int g = 0; g < 2; ++g) {
+    int nxg = g == 0 ? L.nx : L.nxd, nyg = g == 0 ? L.ny : L.nyd;
+    long NN = (long)nxg * nyg;
+    double* Sg = c->S + (long)g * NFLD * L.plane;
+    for (int f = 0; f < NFLD; ++f) {
+      double* dst = f < 4 ? dstW[g] + f * NN : dstG[g] + (f - 4) * NN;
+      CUDA_TRY(c, copy_field(c, Sg + (long)f * L.plane, nullptr, dst, nxg, nyg, false, on_device));
+    }
+  }
+  if (!on_device) CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return FDCGKS_OK;
+}
+
+fdcgks_status fdcgks_steps(fdcgks_t c, double dt, int nsteps) {
+  if (!c) return fail(nullptr, FDCGKS_ERR_ARG, "ctx is NULL");
+  if (!c->has_state) return fail(c, FDCGKS_ERR_STATE, "no state loaded");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, FDCGKS_ERR_ARG, "dt must be positive and finite");
+  if (nsteps < 0) return fail(c, FDCGKS_ERR_ARG, "nsteps must be >= 0");
+  for (int s = 0; s < nsteps; ++s) {
+    fdcgks_status st = c->p.precision == FDCGKS_MIXED ? run_step<float>(c, dt) : run_step<double>(c, dt);
+    if (st != FDCGKS_OK) return st;
+  }
+  return FDCGKS_OK;
+}
+
+fdcgks_status fdcgks_step(fdcgks_t c, double dt) { return fdcgks_steps(c, dt, 1); }
+
+fdcgks_status fdcgks_check(fdcgks_t c, int* nonphysical) {
+  if (!c || !nonphysical) return fail(c, FDCGKS_ERR_ARG, "NULL argument");
+  int h = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&h, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+  *nonphysical = h & 1;
+  return FDCGKS_OK;
+}
+
+fdcgks_status fdcgks_cfl_dt(fdcgks_t c, double cfl, double* dt_out) {
+  if (!c || !dt_out) return fail(c, FDCGKS_ERR_ARG, "NULL argument");
+  if (!c->has_state) return fail(c, FDCGKS_ERR_STATE, "no state loaded");
+  if (!(cfl > 0.0) || !std::isfinite(cfl)) return fail(c, FDCGKS_ERR_ARG, "cfl must be positive and finite");
+  cfl_kernel<<<c->red_blocks, 256, 0, c->stream>>>(c->S, c->L, c->p.gamma, c->p.mu, 1.0 / c->hx, 1.0 / c->hy, c->red);
+  CUDA_TRY(c, cudaGetLastError());
+  double* h = new double[2 * c->red_blocks];
+  cudaError_t e = cudaMemcpyAsync(h, c->red, sizeof(double) * 2 * c->red_blocks, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    delete[] h;
+    return fail(c, FDCGKS_ERR_CUDA, "cfl reduction: %s", cudaGetErrorString(e));
+  }
+  double rate = 0.0, numax = 0.0;
+  for (int b = 0; b < c->red_blocks; ++b) {
+    rate = std::fmax(rate, h[2 * b]);
+    numax = std::fmax(numax, h[2 * b + 1]);
+  }
+  delete[] h;
+  if (!(rate > 0.0) || !std::isfinite(rate)) return fail(c, FDCGKS_ERR_NONPHYSICAL, "no finite wave speed");
+  double dt = cfl / rate;
+  if (numax > 0.0) {
+    double hm = std::fmin(c->hx, c->hy);
+    dt = std::fmin(dt, cfl * hm * hm / (8.0 * numax));
+  }
+  *dt_out = dt;
+  return FDCGKS_OK;
+}
+
+fdcgks_status fdcgks_stage_operator(fdcgks_t c, double dt, double* Lp, double* Ltp, double* gbp, double* gtp,
+                                    double* Ld, double* Ltd, double* gbd, double* gtd) {
+  if (!c) return fail(nullptr, FDCGKS_ERR_ARG, "ctx is NULL");
+  if (!c->has_state) return fail(c, FDCGKS_ERR_STATE, "no state loaded");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, FDCGKS_ERR_ARG, "dt must be positive and finite");
+  double* op[8] = {Lp, Ltp, gbp, gtp, Ld, Ltd, gbd, gtd};
+  for (double* q : op)
+    if (!q) return fail(c, FDCGKS_ERR_ARG, "NULL output pointer");
+  return c->p.precision == FDCGKS_MIXED ? run_stage<float>(c, dt, UPD_OPERATOR, op)
+                                        : run_stage<double>(c, dt, UPD_OPERATOR, op);
+}
+
+fdcgks_status fdcgks_iface_batch(const fdcgks_params* p, int normal, double dt, int n, const double* in, double* out) {
+  if (const char* m = check_params(p)) return fail(nullptr, FDCGKS_ERR_ARG, "%s", m);
+  if (normal != 0 && normal != 1) return fail(nullptr, FDCGKS_ERR_ARG, "normal must be 0 or 1");
+  if (n < 0 || (n > 0 && (!in || !out))) return fail(nullptr, FDCGKS_ERR_ARG, "bad batch arguments");
+  if (!(dt > 0.0)) return fail(nullptr, FDCGKS_ERR_ARG, "dt must be positive");
+  cudaError_t e = p->precision == FDCGKS_MIXED
+                      ? launch_iface_batch<float>(make_gas<float>(*p, dt), normal, n, in, out, (cudaStream_t)p->stream)
+                      : launch_iface_batch<double>(make_gas<double>(*p, dt), normal, n, in, out, (cudaStream_t)p->stream);
+  if (e != cudaSuccess) return fail(nullptr, FDCGKS_ERR_CUDA, "iface batch: %s", cudaGetErrorString(e));
+  return FDCGKS_OK;
+}
+
+fdcgks_status fdcgks_nodal_batch(const fdcgks_params* p, double dt, int n, const double* in, double* out) {
+  if (const char* m = check_params(p)) return fail(nullptr, FDCGKS_ERR_ARG, "%s", m);
+  if (n < 0 || (n > 0 && (!in || !out))) return fail(nullptr, FDCGKS_ERR_ARG, "bad batch arguments");
+  if (!(dt > 0.0)) return fail(nullptr, FDCGKS_ERR_ARG, "dt must be positive");
+  cudaError_t e = p->precision == FDCGKS_MIXED
+                      ? launch_nodal_batch<float>(make_gas<float>(*p, dt), n, in, out, (cudaStream_t)p->stream)
+                      : launch_nodal_batch<double>(make_gas<double>(*p, dt), n, in, out, (cudaStream_t)p->stream);
+  if (e != cudaSuccess) return fail(nullptr, FDCGKS_ERR_CUDA, "nodal batch: %s", cudaGetErrorString(e));
+  return FDCGKS_OK;
+}
+
+fdcgks_status fdcgks_recon_batch(const fdcgks_params* p, int kind, double h, int n, const double* in, double* out) {
+  if (const char* m = check_params(p)) return fail(nullptr, FDCGKS_ERR_ARG, "%s", m);
+  if (kind != 0 && kind != 1) return fail(nullptr, FDCGKS_ERR_ARG, "kind must be 0 or 1");
+  if (!(h > 0.0) || n < 0 || (n > 0 && (!in || !out))) return fail(nullptr, FDCGKS_ERR_ARG, "bad batch arguments");
+  cudaError_t e = p->precision == FDCGKS_MIXED
+                      ? launch_recon_batch<float>(make_geno<float>(p->geno_variant), kind, h, n, in, out,
+                                                  (cudaStream_t)p->stream)
+                      : launch_recon_batch<double>(make_geno<double>(p->geno_variant), kind, h, n, in, out,
+                                                   (cudaStream_t)p->stream);
+  if (e != cudaSuccess) return fail(nullptr, FDCGKS_ERR_CUDA, "recon batch: %s", cudaGetErrorString(e));
+  return FDCGKS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,369 @@
+// Templated CUDA kernels of the FD-CGKS stage (Sec. 4 of the paper): nodal
+// reconstruction + flux, virtual-interface points (two line reconstructions
+// shared by the primary-grid and dual-grid solves), and the fused compact
+// finite-difference + S2O4 update.  Included by one translation unit per
+// compute precision.
+#pragma once
+
+#include "fdcgks_internal.cuh"
+
+namespace fdk {
+
+// ---------------------------------------------------------------------------
+// nodal reconstruction and flux (Sec. 4 item 2; Sec. 2.1 nodal fluxes)
+// one thread per node, nodes i in [-1, n_x], j in [-1, n_y] of grid blockIdx.z
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void __launch_bounds__(128) nodal_kernel(KArgs<R> a) {
+  const int g = blockIdx.z;
+  const Layout& L = a.L;
+  const int nxg = g == 0 ? L.nx : L.nxd, nyg = g == 0 ? L.ny : L.nyd;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x - 1;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y - 1;
+  if (i > nxg || j > nyg) return;
+  const double* S = a.S + (long)g * NFLD * L.plane;
+  const long c0 = cell(L, i, j);
+  R W[4], Wx[4], Wy[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const double* f = S + (long)c * L.plane;
+    const double* gx = S + (long)(4 + c) * L.plane;
+    const double* gy = S + (long)(8 + c) * L.plane;
+    W[c] = (R)f[c0];
+    R qx[3] = {(R)f[c0 - 1], W[c], (R)f[c0 + 1]};
+    R gxv[3] = {(R)gx[c0 - 1], (R)gx[c0], (R)gx[c0 + 1]};
+    Wx[c] = recon_node(a.geno, qx, gxv, a.h[0], a.ih[0]);
+    R qy[3] = {(R)f[c0 - L.pitch], W[c], (R)f[c0 + L.pitch]};
+    R gyv[3] = {(R)gy[c0 - L.pitch], (R)gy[c0], (R)gy[c0 + L.pitch]};
+    Wy[c] = recon_node(a.geno, qy, gyv, a.h[1], a.ih[1]);
+  }
+  R F[4], G[4], Ft[4], Gt[4];
+  nodal_flux(a.gas, W, Wx, Wy, F, G, Ft, Gt);
+  R* NF = a.NF + (long)g * NNF * L.plane + c0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    NF[(long)c * L.plane] = F[c];
+    NF[(long)(4 + c) * L.plane] = G[c];
+    NF[(long)(8 + c) * L.plane] = Ft[c];
+    NF[(long)(12 + c) * L.plane] = Gt[c];
+  }
+}
+
+// reconstruct one 4-point line of one grid at its virtual interface
+// (between entries 1 and 2): starting cell c0 (entry 0), stride between
+// entries, gradient field offset gfield (4: x-gradient, 8: y-gradient)
+template <class R>
+FD_HD void recon_line(const GenoK<R>& geno, const double* S, long plane, long c0, long stride, int gfield, R h,
+                      R ih, R vl[4], R dl[4], R vr[4], R dr[4], R& chi) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const double* f = S + (long)c * plane + c0;
+    const double* gr = S + (long)(gfield + c) * plane + c0;
+    R Q[4] = {(R)f[0], (R)f[stride], (R)f[2 * stride], (R)f[3 * stride]};
+    R Qx[4] = {(R)gr[0], (R)gr[stride], (R)gr[2 * stride], (R)gr[3 * stride]};
+    R cl, cr;
+    recon_interface(geno, Q, Qx, h, ih, vl[c], dl[c], cl, vr[c], dr[c], cr);
+    if (c == 0) chi = s_min(cl, cr);   // chi_{j+1/2} = min(chi^{l,rho}, chi^{r,rho})
+  }
+}
+
+// ---------------------------------------------------------------------------
+// virtual-interface points (Sec. 4 item 1; App. A3).
+// TYPE 0 = point A (i+1/2, j): primary x-interface, dual y-interface of dual column i+1
+// TYPE 1 = point B (i, j+1/2): primary y-interface, dual x-interface of dual row j+1
+// ---------------------------------------------------------------------------
+template <class R, int TYPE>
+__global__ void __launch_bounds__(128) point_kernel(KArgs<R> a) {
+  const Layout& L = a.L;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x - 2;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y - 2;
+  const int imax = TYPE == 0 ? L.nx : L.nxd;
+  const int jmax = TYPE == 0 ? L.nyd : L.ny;
+  if (i > imax || j > jmax) return;
+  const double* SP = a.S;
+  const double* SD = a.S + (long)NFLD * L.plane;
+  const int n0 = TYPE;        // normal of the primary-grid solve
+  R l0v[4], l0d[4], r0v[4], r0d[4], chi0;
+  R l1v[4], l1d[4], r1v[4], r1d[4], chi1;
+  if (TYPE == 0) {
+    // primary nodes (i-1..i+2, j) along x; dual nodes (i+1, j-1..j+2) along y
+    recon_line(a.geno, SP, L.plane, cell(L, i - 1, j), 1, 4, a.h[0], a.ih[0], l0v, l0d, r0v, r0d, chi0);
+    recon_line(a.geno, SD, L.plane, cell(L, i + 1, j - 1), L.pitch, 8, a.h[1], a.ih[1], l1v, l1d, r1v, r1d, chi1);
+  } else {
+    // primary nodes (i, j-1..j+2) along y; dual nodes (i-1..i+2, j+1) along x
+    recon_line(a.geno, SP, L.plane, cell(L, i, j - 1), L.pitch, 8, a.h[1], a.ih[1], l0v, l0d, r0v, r0d, chi0);
+    recon_line(a.geno, SD, L.plane, cell(L, i - 1, j + 1), 1, 4, a.h[0], a.ih[0], l1v, l1d, r1v, r1d, chi1);
+  }
+  // tangential derivative of each solve: mean of the other line's l/r derivatives
+  R t0[4], t1[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    t0[c] = R(0.5) * (l1d[c] + r1d[c]);
+    t1[c] = R(0.5) * (l0d[c] + r0d[c]);
+  }
+  const bool wn = a.want_n != 0;
+  IfaceOut<R> o0, o1;
+  iface_solve(a.gas, n0, l0v, r0v, l0d, r0d, t0, wn, o0);
+  iface_solve(a.gas, 1 - n0, l1v, r1v, l1d, r1d, t1, wn, o1);
+
+  R* P = (TYPE == 0 ? a.PA : a.PB) + pcell(L, i, j);
+  const long pp = L.pplane;
+  // W~ of Eq. (eq:W-model-2d): half of the own solve plus a quarter of each side of the other
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    R m1t = R(0.25) * (o1.Wlt[c] + o1.Wrt[c]), m0t = R(0.25) * (o0.Wlt[c] + o0.Wrt[c]);
+    P[(PO_FT + c) * pp] = o0.Ft[c];
+    P[(PO_WLT + c) * pp] = R(0.5) * o0.Wlt[c] + m1t;
+    P[(PO_WRT + c) * pp] = R(0.5) * o0.Wrt[c] + m1t;
+    P[(NPS + PO_FT + c) * pp] = o1.Ft[c];
+    P[(NPS + PO_WLT + c) * pp] = R(0.5) * o1.Wlt[c] + m0t;
+    P[(NPS + PO_WRT + c) * pp] = R(0.5) * o1.Wrt[c] + m0t;
+    if (wn) {
+      R m1 = R(0.25) * (o1.Wl[c] + o1.Wr[c]), m0 = R(0.25) * (o0.Wl[c] + o0.Wr[c]);
+      P[(PO_F + c) * pp] = o0.F[c];
+      P[(PO_WL + c) * pp] = R(0.5) * o0.Wl[c] + m1;
+      P[(PO_WR + c) * pp] = R(0.5) * o0.Wr[c] + m1;
+      P[(NPS + PO_F + c) * pp] = o1.F[c];
+      P[(NPS + PO_WL + c) * pp] = R(0.5) * o1.Wl[c] + m0;
+      P[(NPS + PO_WR + c) * pp] = R(0.5) * o1.Wr[c] + m0;
+    }
+  }
+  P[PO_CHI * pp] = chi0;
+  P[(NPS + PO_CHI) * pp] = chi1;
+}
+
+// ---------------------------------------------------------------------------
+// compact FD + S2O4 update (Eqs. eq-conservation-law-2d, fd-conservative-flux*,
+// define-averaged-gradient, eq-nodal-update, eq-interface-update).
+// One thread per interior node of grid blockIdx.z.
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void __launch_bounds__(128) update_kernel(KArgs<R> a, int mode) {
+  const int g = blockIdx.z;
+  const Layout& L = a.L;
+  const int nxg = g == 0 ? L.nx : L.nxd, nyg = g == 0 ? L.ny : L.nyd;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= nxg || j >= nyg) return;
+  const long pp = L.pplane;
+  // x-interface k+1/2 of this grid's row and y-interface k+1/2 of its column
+  const R* PX = g == 0 ? a.PA : a.PB + NPS * pp;   // primary: A points solve 0; dual: B points solve 1
+  const R* PY = g == 0 ? a.PB : a.PA + NPS * pp;   // primary: B points solve 0; dual: A points solve 1
+  auto xi = [&](int k) { return g == 0 ? pcell(L, k, j) : pcell(L, k, j - 1); };
+  auto yi = [&](int k) { return g == 0 ? pcell(L, i, k) : pcell(L, i - 1, k); };
+  const R* NF = a.NF + (long)g * NNF * L.plane;
+  const long c0 = cell(L, i, j);
+  const long cN = cell(L, i, j);
+  const int fv = a.flux_variant;
+  const R ihx = a.ih[0], ihy = a.ih[1];
+
+  const long xm2 = xi(i - 2), xm1 = xi(i - 1), x0 = xi(i), xp1 = xi(i + 1);
+  const long ym2 = yi(j - 2), ym1 = yi(j - 1), y0 = yi(j), yp1 = yi(j + 1);
+  const R chixm = PX[PO_CHI * pp + xm1], chix0 = PX[PO_CHI * pp + x0];
+  const R chiym = PY[PO_CHI * pp + ym1], chiy0 = PY[PO_CHI * pp + y0];
+
+  double Wnew[4];
+  const double* Sg = a.S + (long)g * NFLD * L.plane;
+  const double* Sng = a.Sn + (long)g * NFLD * L.plane;
+  const long NN = (long)nxg * nyg;
+  const long oi = (long)j * nxg + i;
+  const double dt = a.dt;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const R* nF = NF + (long)c * L.plane;
+    const R* nG = NF + (long)(4 + c) * L.plane;
+    const R* nFt = NF + (long)(8 + c) * L.plane;
+    const R* nGt = NF + (long)(12 + c) * L.plane;
+    const R* pF = PX + (long)(PO_F + c) * pp;
+    const R* pFt = PX + (long)(PO_FT + c) * pp;
+    const R* qF = PY + (long)(PO_F + c) * pp;
+    const R* qFt = PY + (long)(PO_FT + c) * pp;
+    R Lt, L0 = R(0);
+    {
+      R fp = compact_flux(fv, chix0, pFt[xm1], pFt[x0], pFt[xp1], nFt[cN], nFt[cN + 1]);
+      R fm = compact_flux(fv, chixm, pFt[xm2], pFt[xm1], pFt[x0], nFt[cN - 1], nFt[cN]);
+      R gp = compact_flux(fv, chiy0, qFt[ym1], qFt[y0], qFt[yp1], nGt[cN], nGt[cN + L.pitch]);
+      R gm = compact_flux(fv, chiym, qFt[ym2], qFt[ym1], qFt[y0], nGt[cN - L.pitch], nGt[cN]);
+      Lt = -(fp - fm) * ihx - (gp - gm) * ihy;
+    }
+    if (mode != UPD_STAGE2) {
+      R fp = compact_flux(fv, chix0, pF[xm1], pF[x0], pF[xp1], nF[cN], nF[cN + 1]);
+      R fm = compact_flux(fv, chixm, pF[xm2], pF[xm1], pF[x0], nF[cN - 1], nF[cN]);
+      R gp = compact_flux(fv, chiy0, qF[ym1], qF[y0], qF[yp1], nG[cN], nG[cN + L.pitch]);
+      R gm = compact_flux(fv, chiym, qF[ym2], qF[ym1], qF[y0], nG[cN - L.pitch], nG[cN]);
+      L0 = -(fp - fm) * ihx - (gp - gm) * ihy;
+    }
+    // averaged gradients from the interface solution, node's own side
+    R gtx = (PX[(PO_WLT + c) * pp + x0] - PX[(PO_WRT + c) * pp + xm1]) * ihx;
+    R gty = (PY[(PO_WLT + c) * pp + y0] - PY[(PO_WRT + c) * pp + ym1]) * ihy;
+    R gbx = R(0), gby = R(0);
+    if (mode != UPD_STAGE2) {
+      gbx = (PX[(PO_WL + c) * pp + x0] - PX[(PO_WR + c) * pp + xm1]) * ihx;
+      gby = (PY[(PO_WL + c) * pp + y0] - PY[(PO_WR + c) * pp + ym1]) * ihy;
+    }
+    if (mode == UPD_OPERATOR) {
+      double** op = a.op + 4 * g;
+      op[0][c * NN + oi] = (double)L0;
+      op[1][c * NN + oi] = (double)Lt;
+      op[2][c * NN + oi] = (double)gbx;
+      op[2][(4 + c) * NN + oi] = (double)gby;
+      op[3][c * NN + oi] = (double)gtx;
+      op[3][(4 + c) * NN + oi] = (double)gty;
+      continue;
+    }
+    double* Og = a.Sout + (long)g * NFLD * L.plane;
+    double* Ag = a.Wacc + (long)g * 4 * L.plane;
+    double* Bg = a.gB + (long)g * 8 * L.plane;
+    if (mode == UPD_STAGE1) {
+      double Wn = Sng[(long)c * L.plane + c0];
+      double dL = (double)L0, dLt = (double)Lt;
+      Wnew[c] = Wn + 0.5 * dt * dL + 0.125 * dt * dt * dLt;
+      Ag[(long)c * L.plane + c0] = Wn + dt * dL + dt * dt / 6.0 * dLt;
+      double bx = a.grad_base ? Sng[(long)(4 + c) * L.plane + c0] : (double)gbx;
+      double by = a.grad_base ? Sng[(long)(8 + c) * L.plane + c0] : (double)gby;
+      Bg[(long)c * L.plane + c0] = bx;
+      Bg[(long)(4 + c) * L.plane + c0] = by;
+      Og[(long)(4 + c) * L.plane + c0] = bx + 0.5 * dt * (double)gtx;
+      Og[(long)(8 + c) * L.plane + c0] = by + 0.5 * dt * (double)gty;
+    } else {
+      Wnew[c] = Ag[(long)c * L.plane + c0] + dt * dt / 3.0 * (double)Lt;
+      Og[(long)(4 + c) * L.plane + c0] = Bg[(long)c * L.plane + c0] + dt * (double)gtx;
+      Og[(long)(8 + c) * L.plane + c0] = Bg[(long)(4 + c) * L.plane + c0] + dt * (double)gty;
+    }
+  }
+  (void)Sg;
+  if (mode == UPD_OPERATOR) return;
+  double* Og = a.Sout + (long)g * NFLD * L.plane;
+  // dual nodes on a no-slip wall: velocity set to zero (internal energy kept),
+  // and, as U = V = 0 along the whole wall, the momentum gradients along it too
+  if (g == 1) {
+    bool xwall = (a.bc[0] == 3 && i == 0) || (a.bc[1] == 3 && i == nxg - 1);
+    bool ywall = (a.bc[2] == 3 && j == 0) || (a.bc[3] == 3 && j == nyg - 1);
+    if (xwall || ywall) {
+      double ke = 0.5 * (Wnew[1] * Wnew[1] + Wnew[2] * Wnew[2]) / Wnew[0];
+      Wnew[1] = 0.0;
+      Wnew[2] = 0.0;
+      Wnew[3] -= ke;
+    }
+    if (xwall) { Og[(long)(8 + 1) * L.plane + c0] = 0.0; Og[(long)(8 + 2) * L.plane + c0] = 0.0; }
+    if (ywall) { Og[(long)(4 + 1) * L.plane + c0] = 0.0; Og[(long)(4 + 2) * L.plane + c0] = 0.0; }
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) Og[(long)c * L.plane + c0] = Wnew[c];
+  // positivity of density and pressure (no trap: a flag the host reads)
+  double p = Wnew[3] - 0.5 * (Wnew[1] * Wnew[1] + Wnew[2] * Wnew[2]) / Wnew[0];
+  if (!(Wnew[0] > 0.0) || !(p > 0.0)) atomicOr(a.flag, 1);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+inline dim3 grid2(int nxp, int nyp, dim3 b, int z) {
+  return dim3((unsigned)((nxp + b.x - 1) / b.x), (unsigned)((nyp + b.y - 1) / b.y), (unsigned)z);
+}
+
+template <class R>
+cudaError_t launch_nodal(const KArgs<R>& a, cudaStream_t s) {
+  dim3 b(32, 4);
+  int mx = (a.L.nx > a.L.nxd ? a.L.nx : a.L.nxd) + 2, my = (a.L.ny > a.L.nyd ? a.L.ny : a.L.nyd) + 2;
+  nodal_kernel<R><<<grid2(mx, my, b, 2), b, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_points(const KArgs<R>& a, cudaStream_t s) {
+  dim3 b(32, 4);
+  point_kernel<R, 0><<<grid2(a.L.nx + 3, a.L.nyd + 3, b, 1), b, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  point_kernel<R, 1><<<grid2(a.L.nxd + 3, a.L.ny + 3, b, 1), b, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_update(const KArgs<R>& a, int mode, cudaStream_t s) {
+  dim3 b(32, 4);
+  int mx = a.L.nx > a.L.nxd ? a.L.nx : a.L.nxd, my = a.L.ny > a.L.nyd ? a.L.ny : a.L.nyd;
+  update_kernel<R><<<grid2(mx, my, b, 2), b, 0, s>>>(a, mode);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// component batches
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void iface_batch_kernel(GasK<R> gas, int normal, int n, const double* in, double* out) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  R v[20];
+  for (int k = 0; k < 20; ++k) v[k] = (R)in[(long)t * 20 + k];
+  IfaceOut<R> o;
+  iface_solve(gas, normal, v, v + 4, v + 8, v + 12, v + 16, true, o);
+  double* q = out + (long)t * 24;
+  for (int k = 0; k < 4; ++k) {
+    q[k] = o.F[k]; q[4 + k] = o.Ft[k]; q[8 + k] = o.Wl[k];
+    q[12 + k] = o.Wr[k]; q[16 + k] = o.Wlt[k]; q[20 + k] = o.Wrt[k];
+  }
+}
+
+template <class R>
+__global__ void nodal_batch_kernel(GasK<R> gas, int n, const double* in, double* out) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  R v[12];
+  for (int k = 0; k < 12; ++k) v[k] = (R)in[(long)t * 12 + k];
+  R F[4], G[4], Ft[4], Gt[4];
+  nodal_flux(gas, v, v + 4, v + 8, F, G, Ft, Gt);
+  double* q = out + (long)t * 16;
+  for (int k = 0; k < 4; ++k) { q[k] = F[k]; q[4 + k] = G[k]; q[8 + k] = Ft[k]; q[12 + k] = Gt[k]; }
+}
+
+template <class R>
+__global__ void recon_batch_kernel(GenoK<R> g, int kind, R h, R ih, int n, const double* in, double* out) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  if (kind == 0) {
+    R Q[4], Qx[4];
+    for (int k = 0; k < 4; ++k) { Q[k] = (R)in[(long)t * 8 + k]; Qx[k] = (R)in[(long)t * 8 + 4 + k]; }
+    R vl, dl, cl, vr, dr, cr;
+    recon_interface(g, Q, Qx, h, ih, vl, dl, cl, vr, dr, cr);
+    double* q = out + (long)t * 6;
+    q[0] = vl; q[1] = dl; q[2] = cl; q[3] = vr; q[4] = dr; q[5] = cr;
+  } else {
+    R Q[3], Qx[3];
+    for (int k = 0; k < 3; ++k) { Q[k] = (R)in[(long)t * 6 + k]; Qx[k] = (R)in[(long)t * 6 + 3 + k]; }
+    out[(long)t * 6] = recon_node(g, Q, Qx, h, ih);
+    for (int k = 1; k < 6; ++k) out[(long)t * 6 + k] = 0.0;
+  }
+}
+
+template <class R>
+cudaError_t launch_iface_batch(const GasK<R>& gas, int normal, int n, const double* in, double* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  iface_batch_kernel<R><<<(n + 63) / 64, 64, 0, s>>>(gas, normal, n, in, out);
+  return cudaGetLastError();
+}
+template <class R>
+cudaError_t launch_nodal_batch(const GasK<R>& gas, int n, const double* in, double* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  nodal_batch_kernel<R><<<(n + 63) / 64, 64, 0, s>>>(gas, n, in, out);
+  return cudaGetLastError();
+}
+template <class R>
+cudaError_t launch_recon_batch(const GenoK<R>& g, int kind, double h, int n, const double* in, double* out,
+                               cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  recon_batch_kernel<R><<<(n + 127) / 128, 128, 0, s>>>(g, kind, (R)h, (R)(1.0 / h), n, in, out);
+  return cudaGetLastError();
+}
+
+#define FDK_INSTANTIATE(R)                                                                                  \
+  template cudaError_t launch_nodal<R>(const KArgs<R>&, cudaStream_t);                                     \
+  template cudaError_t launch_points<R>(const KArgs<R>&, cudaStream_t);                                    \
+  template cudaError_t launch_update<R>(const KArgs<R>&, int, cudaStream_t);                               \
+  template cudaError_t launch_iface_batch<R>(const GasK<R>&, int, int, const double*, double*, cudaStream_t); \
+  template cudaError_t launch_nodal_batch<R>(const GasK<R>&, int, const double*, double*, cudaStream_t);   \
+  template cudaError_t launch_recon_batch<R>(const GenoK<R>&, int, double, int, const double*, double*,     \
+                                             cudaStream_t);
+
+}  // namespace fdk

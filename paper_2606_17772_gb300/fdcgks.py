@@ -1,0 +1,276 @@
+"""Python binding of libfdcgks.so (ctypes; argument marshalling only).
+
+Every step of the FD-CGKS path runs in the library's CUDA kernels; this module
+only passes pointers, sizes and the current torch CUDA stream across the C
+ABI declared in include/fdcgks.h.  There is no fallback: if the library is
+missing or the GPU is unavailable, the calls raise.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+BC_PERIODIC, BC_TRANSMISSIVE, BC_SYMMETRY, BC_NOSLIP = 0, 1, 2, 3
+FP64, MIXED = 0, 1
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "non-physical state", 4: "no state loaded",
+          5: "device wait timed out", 6: "out of device memory"}
+
+EXPORTS = ["fdcgks_create", "fdcgks_destroy", "fdcgks_dims", "fdcgks_set_state", "fdcgks_get_state",
+           "fdcgks_step", "fdcgks_steps", "fdcgks_cfl_dt", "fdcgks_check", "fdcgks_stage_operator",
+           "fdcgks_iface_batch", "fdcgks_nodal_batch", "fdcgks_recon_batch", "fdcgks_last_error",
+           "fdcgks_status_string"]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+        ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("mu", ctypes.c_double), ("Pr", ctypes.c_double),
+        ("bc", ctypes.c_int * 4),
+        ("flux_variant", ctypes.c_int),
+        ("geno_variant", ctypes.c_int),
+        ("grad_base", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("tau_c1", ctypes.c_double), ("tau_c2", ctypes.c_double),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class FdcgksError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s (%d): %s" % (STATUS.get(status, "?"), status, message))
+        self.status = status
+
+
+_lib = None
+_VP = ctypes.c_void_p
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(path=None):
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise FileNotFoundError("libfdcgks.so not found at %s: build it with "
+                                "paper_2606_17772_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    lib.fdcgks_create.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(_VP)]
+    lib.fdcgks_destroy.argtypes = [_VP]
+    lib.fdcgks_destroy.restype = None
+    lib.fdcgks_dims.argtypes = [_VP] + [ctypes.POINTER(ctypes.c_int)] * 4
+    lib.fdcgks_set_state.argtypes = [_VP, _VP, _VP, _VP, _VP, ctypes.c_int]
+    lib.fdcgks_get_state.argtypes = [_VP, _VP, _VP, _VP, _VP, ctypes.c_int]
+    lib.fdcgks_step.argtypes = [_VP, ctypes.c_double]
+    lib.fdcgks_steps.argtypes = [_VP, ctypes.c_double, ctypes.c_int]
+    lib.fdcgks_cfl_dt.argtypes = [_VP, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    lib.fdcgks_check.argtypes = [_VP, ctypes.POINTER(ctypes.c_int)]
+    lib.fdcgks_stage_operator.argtypes = [_VP, ctypes.c_double] + [_VP] * 8
+    lib.fdcgks_iface_batch.argtypes = [ctypes.POINTER(Params), ctypes.c_int, ctypes.c_double, ctypes.c_int, _VP, _VP]
+    lib.fdcgks_nodal_batch.argtypes = [ctypes.POINTER(Params), ctypes.c_double, ctypes.c_int, _VP, _VP]
+    lib.fdcgks_recon_batch.argtypes = [ctypes.POINTER(Params), ctypes.c_int, ctypes.c_double, ctypes.c_int, _VP, _VP]
+    lib.fdcgks_last_error.argtypes = [_VP]
+    lib.fdcgks_last_error.restype = ctypes.c_char_p
+    lib.fdcgks_status_string.argtypes = [ctypes.c_int]
+    lib.fdcgks_status_string.restype = ctypes.c_char_p
+    for name in ("fdcgks_create", "fdcgks_dims", "fdcgks_set_state", "fdcgks_get_state", "fdcgks_step",
+                 "fdcgks_steps", "fdcgks_cfl_dt", "fdcgks_check", "fdcgks_stage_operator", "fdcgks_iface_batch",
+                 "fdcgks_nodal_batch", "fdcgks_recon_batch"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status, ctx=None):
+    if status != 0:
+        msg = load().fdcgks_last_error(ctx).decode()
+        raise FdcgksError(status, msg)
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def make_params(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, mu=0.0, Pr=1.0, bc=(0, 0, 0, 0),
+                flux_variant=64, geno_variant=0, grad_base=0, precision=FP64, tau_c1=0.0, tau_c2=0.0,
+                stream=None):
+    p = Params()
+    p.nx, p.ny = nx, ny
+    p.x0, p.x1, p.y0, p.y1 = x0, x1, y0, y1
+    p.gamma, p.mu, p.Pr = gamma, mu, Pr
+    for k in range(4):
+        p.bc[k] = bc[k]
+    p.flux_variant, p.geno_variant, p.grad_base = flux_variant, geno_variant, grad_base
+    p.precision = precision
+    p.tau_c1, p.tau_c2 = tau_c1, tau_c2
+    p.stream = stream
+    return p
+
+
+def params_for_case(case, precision=FP64, stream=None):
+    """Params from a paper_2606_17772_gb300.inputs.Case."""
+    return make_params(precision=precision, stream=stream, **case.oracle_kwargs())
+
+
+def _dptr(t, numel=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError("tensor has %d elements, expected %d" % (t.numel(), numel))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a, numel=None):
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("expected a C-contiguous float64 array")
+        if numel is not None and a.size != numel:
+            raise ValueError("array has %d elements, expected %d" % (a.size, numel))
+        return ctypes.c_void_p(a.ctypes.data)
+    import torch
+    if isinstance(a, torch.Tensor) and not a.is_cuda:
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("expected a contiguous float64 tensor")
+        if numel is not None and a.numel() != numel:
+            raise ValueError("tensor has %d elements, expected %d" % (a.numel(), numel))
+        return ctypes.c_void_p(a.data_ptr())
+    raise TypeError("expected a host array")
+
+
+class Solver:
+    """One FD-CGKS context (fdcgks_create ... fdcgks_destroy)."""
+
+    def __init__(self, params):
+        lib = load()
+        self._p = params
+        if params.stream is None:
+            params.stream = _stream().value
+        h = _VP()
+        _check(lib.fdcgks_create(ctypes.byref(params), ctypes.byref(h)))
+        self._h = h
+        d = [ctypes.c_int() for _ in range(4)]
+        _check(lib.fdcgks_dims(h, *[ctypes.byref(x) for x in d]), h)
+        self.nx, self.ny, self.nxd, self.nyd = (x.value for x in d)
+
+    @classmethod
+    def from_case(cls, case, precision=FP64):
+        return cls(params_for_case(case, precision))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().fdcgks_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # --- sizes of the state arrays
+    def shapes(self):
+        return ((4, self.ny, self.nx), (2, 4, self.ny, self.nx), (4, self.nyd, self.nxd), (2, 4, self.nyd, self.nxd))
+
+    def _ptrs(self, arrs, on_device):
+        sizes = [int(np.prod(s)) for s in self.shapes()]
+        conv = _dptr if on_device else _hptr
+        return [conv(a, n) for a, n in zip(arrs, sizes)]
+
+    def set_state(self, Wp, Gp, Wd, Gd):
+        """Device (CUDA float64 tensors) or host (numpy / CPU tensors) arrays."""
+        import torch
+        on_device = isinstance(Wp, torch.Tensor) and Wp.is_cuda
+        _check(load().fdcgks_set_state(self._h, *self._ptrs((Wp, Gp, Wd, Gd), on_device), int(on_device)), self._h)
+
+    def get_state(self, out=None, device=True):
+        import torch
+        if out is None:
+            if device:
+                out = [torch.empty(s, dtype=torch.float64, device="cuda") for s in self.shapes()]
+            else:
+                out = [np.empty(s) for s in self.shapes()]
+        on_device = isinstance(out[0], torch.Tensor) and out[0].is_cuda
+        _check(load().fdcgks_get_state(self._h, *self._ptrs(out, on_device), int(on_device)), self._h)
+        return tuple(out)
+
+    def step(self, dt):
+        _check(load().fdcgks_step(self._h, ctypes.c_double(dt)), self._h)
+
+    def steps(self, dt, n):
+        _check(load().fdcgks_steps(self._h, ctypes.c_double(dt), int(n)), self._h)
+
+    def cfl_dt(self, cfl):
+        out = ctypes.c_double()
+        _check(load().fdcgks_cfl_dt(self._h, ctypes.c_double(cfl), ctypes.byref(out)), self._h)
+        return out.value
+
+    def check(self):
+        out = ctypes.c_int()
+        _check(load().fdcgks_check(self._h, ctypes.byref(out)), self._h)
+        return bool(out.value)
+
+    def stage_operator(self, dt):
+        import torch
+        sp, sg, sdp, sdg = self.shapes()
+        out = {k: torch.empty(s, dtype=torch.float64, device="cuda") for k, s in
+               [("Lp", sp), ("Ltp", sp), ("gbp", sg), ("gtp", sg), ("Ld", sdp), ("Ltd", sdp), ("gbd", sdg),
+                ("gtd", sdg)]}
+        ptrs = [_dptr(out[k]) for k in ("Lp", "Ltp", "gbp", "gtp", "Ld", "Ltd", "gbd", "gtd")]
+        _check(load().fdcgks_stage_operator(self._h, ctypes.c_double(dt), *ptrs), self._h)
+        return out
+
+
+def iface_batch(params, normal, dt, inp, out=None):
+    """Batched interface solves: inp [n, 20] CUDA float64 -> out [n, 24]."""
+    import torch
+    n = inp.shape[0]
+    if out is None:
+        out = torch.empty((n, 24), dtype=torch.float64, device=inp.device)
+    if params.stream is None:
+        params.stream = _stream().value
+    _check(load().fdcgks_iface_batch(ctypes.byref(params), int(normal), ctypes.c_double(dt), n,
+                                     _dptr(inp, 20 * n), _dptr(out, 24 * n)))
+    return out
+
+
+def nodal_batch(params, dt, inp, out=None):
+    """Batched nodal fluxes: inp [n, 12] -> out [n, 16] (CUDA float64)."""
+    import torch
+    n = inp.shape[0]
+    if out is None:
+        out = torch.empty((n, 16), dtype=torch.float64, device=inp.device)
+    if params.stream is None:
+        params.stream = _stream().value
+    _check(load().fdcgks_nodal_batch(ctypes.byref(params), ctypes.c_double(dt), n, _dptr(inp, 12 * n),
+                                     _dptr(out, 16 * n)))
+    return out
+
+
+def recon_batch(params, kind, h, inp, out=None):
+    """Batched GENO reconstructions: kind 0 inp [n, 8], kind 1 inp [n, 6] -> out [n, 6]."""
+    import torch
+    n = inp.shape[0]
+    if out is None:
+        out = torch.empty((n, 6), dtype=torch.float64, device=inp.device)
+    if params.stream is None:
+        params.stream = _stream().value
+    _check(load().fdcgks_recon_batch(ctypes.byref(params), int(kind), ctypes.c_double(h), n,
+                                     _dptr(inp, (8 if kind == 0 else 6) * n), _dptr(out, 6 * n)))
+    return out
