@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the FD-CGKS step on GB300.
+
+Workload: the 2-D isentropic vortex on a periodic [0,10]^2 domain at 1024^2
+primary nodes (plus 1024^2 dual nodes), strength 5 at (5,5), free stream
+(1,1,1,1), gamma = 1.4, FD-CGKS(6-4), GENO (Sec. 3.2 constants), CFL 0.4.
+A step is one full S2O4 step (two stages) of both grids; a node update is
+one step of one primary or dual node (2 * 1024^2 per step).
+
+Prints one JSON line.  `value` is the FP64 path's node-updates/s with the
+state resident in HBM (all N ranks together); the mixed FP32/FP64 path is
+reported beside it with its L1 error against the FP64 path.  `e2e` is the
+same metric through the C ABI with host state: every step copies the state
+in from pinned host memory, steps, and copies it back out.
+
+--impl reference times the CPU oracle (the plain FP64 C++ implementation
+the tests compare against) on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "2D node-updates/s, FP64 vs mixed-FP32 at stated L1 error; % of roofline"
+UNIT = "node-updates/s"
+# FP64 peak derived from unit counts and clocks: 152 SMs x 4 FP64 flop/clk/SM
+# (2 DFMA per clock per SM on GB300) x 2.07 GHz maximum SM clock
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+# FP32: 152 SMs x 128 lanes x 2 flop/FMA x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1024, help="primary nodes per direction")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def oracle_rate(n_sample, nsteps):
+    """Node-updates/s of the CPU oracle on an n_sample^2 vortex (same constants)."""
+    import oracle
+    from paper_2606_17772_gb300 import inputs
+    case = inputs.vortex(n_sample)
+    p = oracle.make_params(**case.oracle_kwargs())
+    S = case.initial_state()
+    dt = 0.4 * case.hx / (math.sqrt(2.0) + math.sqrt(1.4)) * 0.9
+    warm = inputs.vortex(16)            # load the library outside the timing
+    oracle.steps(oracle.make_params(**warm.oracle_kwargs()), dt, 1, *warm.initial_state())
+    t0 = time.perf_counter()
+    oracle.steps(p, dt, nsteps, *S)
+    el = time.perf_counter() - t0
+    return 2 * n_sample * n_sample * nsteps / el, el
+
+
+def run_reference(args):
+    """CPU oracle as the reference arm: K timed steps of a bounded sample."""
+    world, rank = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2606_17772_gb300 import inputs
+    ns = 48
+    case = inputs.vortex(ns)
+    p = oracle.make_params(**case.oracle_kwargs())
+    S = case.initial_state()
+    dt = 0.4 * case.hx / (math.sqrt(2.0) + math.sqrt(1.4)) * 0.9
+    for _ in range(args.warmup):
+        S = oracle.steps(p, dt, 1, *S)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        S = oracle.steps(p, dt, 1, *S)
+    el = time.perf_counter() - t0
+    value = 2 * ns * ns * args.steps / el
+    sample = "isentropic vortex %d^2 (+%d^2 dual), periodic [0,10]^2, strength 5, FD-CGKS(6-4)" % (ns, ns)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "isentropic vortex 1024^2 (oracle on a %d^2 sample)" % ns},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def timed_steps(solver, dt, steps, warmup, world, device_index, sample_clocks):
+    import torch
+    solver.steps(dt, warmup)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    solver.set_profiling(True)
+    solver.get_profile()                         # clear, read launch counter
+    launches0 = solver.get_profile()[2]
+    sampler = ClockSampler(device_index) if sample_clocks else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.steps(dt, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1)
+    prof_ms, prof_n, launches1 = solver.get_profile()
+    solver.set_profiling(False)
+    return ms, prof_ms, prof_n, launches1 - launches0, clocks
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    from paper_2606_17772_gb300 import build as fbuild
+    from paper_2606_17772_gb300 import fdcgks, flops, inputs
+
+    fbuild.build()
+    world, rank, local = dist_setup(args)
+    n = args.n
+    case = inputs.vortex(n)
+    S_host = case.initial_state()
+    S_dev = [torch.from_numpy(a).cuda() for a in S_host]
+    nodes = 2 * n * n
+
+    results = {}
+    for name, prec in (("fp64", fdcgks.FP64), ("mixed", fdcgks.MIXED)):
+        if name == "mixed" and args.no_mixed:
+            continue
+        with fdcgks.Solver.from_case(case, prec) as s:
+            s.set_state(*S_dev)
+            dt = s.cfl_dt(0.4)
+            ms, pms, pn, launches, clocks = timed_steps(s, dt, args.steps, args.warmup, world, local,
+                                                        sample_clocks=(name == "fp64" and rank == 0))
+            out = s.get_state()
+            assert not s.check(), "non-physical state during the benchmark"
+        ms_max = max_over_ranks(ms, world)
+        results[name] = dict(ms=ms_max, prof_ms=pms, prof_n=pn, launches=launches, clocks=clocks, dt=dt,
+                             state=[t.cpu().numpy() for t in out] if rank == 0 else None)
+
+    fp = results["fp64"]
+    value = nodes * args.steps * world / (fp["ms"] / 1e3)
+
+    # roofline of the dominant kernel class (the interface-point kernels), FP64 pipe
+    cnt = flops.step_counts(case, S_host, fp["dt"], precision=0)
+    pt_flops = 2 * n * n * (cnt["point_stage1"]["fp64"] + cnt["point_stage2"]["fp64"]) / 2   # per launch group
+    pt_ms = fp["prof_ms"]["points"] / max(fp["prof_n"]["points"], 1)
+    achieved = pt_flops / (pt_ms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "kernel": "point_kernel (Type A + Type B interface points, FP64)",
+            "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
+            "step_share": fp["prof_ms"]["points"] / max(sum(fp["prof_ms"].values()), 1e-9),
+            "flops_per_node_update": cnt["per_node_update_total"]["fp64"],
+            "step_achieved_tflops": cnt["per_node_update_total"]["fp64"] * nodes * args.steps / (fp["ms"] / 1e3) / 1e12}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": fp["ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "isentropic vortex %d^2 primary + %d^2 dual, periodic [0,10]^2, strength 5, "
+                                   "FD-CGKS(6-4), GENO, CFL 0.4" % (n, n),
+                       "grid": [n, n], "node_updates_per_step": nodes, "parallelism": "replicas",
+                       "l2": "working set %.2f GB > 129 MB L2 (no flush needed)" %
+                             (nodes * 8 * (24 + 24 + 12) / 1e9 + nodes * 8 * 66 / 1e9)},
+            "roofline": roof, "clocks": fp["clocks"], "gpu_launches": fp["launches"] * world}
+
+    if "mixed" in results:
+        mx = results["mixed"]
+        mval = nodes * args.steps * world / (mx["ms"] / 1e3)
+        mcnt = flops.step_counts(case, S_host, mx["dt"], precision=1)
+        mpt = 2 * n * n * (mcnt["point_stage1"]["fp32"] + mcnt["point_stage2"]["fp32"]) / 2
+        mpt_ms = mx["prof_ms"]["points"] / max(mx["prof_n"]["points"], 1)
+        mach = mpt / (mpt_ms / 1e3) / 1e12
+        err = None
+        if rank == 0:
+            a, b = mx["state"][0], fp["state"][0]
+            err = {"L1_rel_rho_vs_fp64": float(np.abs(a[0] - b[0]).mean() / np.abs(b[0]).mean()),
+                   "Linf_rel_rho_vs_fp64": float(np.abs(a[0] - b[0]).max() / np.abs(b[0]).max()),
+                   "after_steps": args.warmup + args.steps}
+        line["mixed"] = {"value": mval, "unit": UNIT, "dtype": "f32+f64", "ms_per_step": mx["ms"] / args.steps,
+                         "error": err,
+                         "roofline": {"bound": "alu", "achieved": mach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                      "frac": mach / FP32_PEAK_TFLOPS,
+                                      "kernel": "point_kernel (FP32 arithmetic, FP64 time coefficients)",
+                                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                                      "fp64_flops_per_node_update": mcnt["per_node_update_total"]["fp64"],
+                                      "fp32_flops_per_node_update": mcnt["per_node_update_total"]["fp32"]},
+                         "gpu_launches": mx["launches"] * world}
+
+    if not args.no_e2e:
+        # end to end through the C ABI with host state in pinned memory
+        pin = [torch.from_numpy(a).pin_memory() for a in S_host]
+        outp = [torch.empty_like(t).pin_memory() for t in pin]
+        with fdcgks.Solver.from_case(case, fdcgks.FP64) as s:
+            s.set_state(*pin)
+            dt = s.cfl_dt(0.4)
+            for _ in range(max(1, args.warmup)):
+                s.set_state(*pin)
+                s.step(dt)
+                s.get_state(out=outp)
+            barrier(world)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                s.set_state(*pin)
+                s.step(dt)
+                s.get_state(out=outp)
+            torch.cuda.synchronize()
+            el = max_over_ranks(time.perf_counter() - t0, world)
+        nbytes = sum(t.numel() * 8 for t in pin)
+        line["e2e"] = {"value": nodes * args.steps * world / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                       "d2h_bytes_per_step": nbytes, "ms_per_step": 1e3 * el / args.steps,
+                       "path": "fdcgks_set_state(host pinned) + fdcgks_step + fdcgks_get_state(host pinned)"}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ns, nst = 128, 2
+        rate, el = oracle_rate(ns, nst)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "isentropic vortex %d^2 (+dual), %d steps, %.1f s, single thread" %
+                                          (ns, nst, el)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -132,6 +132,17 @@ fdcgks_status fdcgks_check(fdcgks_t ctx, int* nonphysical);
 fdcgks_status fdcgks_stage_operator(fdcgks_t ctx, double dt, double* Lp, double* Ltp, double* gbp, double* gtp,
                                     double* Ld, double* Ltd, double* gbd, double* gtd);
 
+/* Kernel-class timing: with profiling enabled, every stage records CUDA
+ * events on the context stream around its ghost fill, nodal kernel, point
+ * kernels (Type A and B) and update kernel.  fdcgks_get_profile waits for
+ * the recorded events, returns the summed milliseconds and the number of
+ * launch groups per class in ms[4] / count[4] (order: ghost, nodal, points,
+ * update; either may be NULL), clears the record, and returns in *launches
+ * (may be NULL) the total number of kernels the stepping path has launched
+ * on this context. */
+fdcgks_status fdcgks_set_profiling(fdcgks_t ctx, int enable);
+fdcgks_status fdcgks_get_profile(fdcgks_t ctx, double* ms, int* count, long long* launches);
+
 /* Batched kinetic interface solve (App. A1-A2, Eq. eq:W-model), normal 0 = x,
  * 1 = y, on device arrays: in [n][20] = Wl[4], Wr[4], normal derivatives
  * Wl_n[4], Wr_n[4], tangential derivative Wt[4]; out [n][24] = F[4], F_t[4],

@@ -27,6 +27,12 @@ struct fdcgks_ctx {
   double* red = nullptr;    // reduction scratch
   int red_blocks = 0;
   bool has_state = false;
+  // kernel-class timing with CUDA events on the context stream (optional)
+  int profiling = 0;
+  cudaEvent_t* ev = nullptr;  // event pool
+  int ev_cap = 0, ev_used = 0;
+  int* ev_class = nullptr;    // class of the interval that ends at event 2k+1
+  long long launches = 0;     // kernels launched by the stepping path
   char err[512];
 };
 
@@ -224,6 +230,33 @@ __global__ void cfl_kernel(const double* S, Layout L, double gamma, double mu, d
 }
 
 // ---------------------------------------------------------------------------
+// optional timing of kernel classes (events recorded around each launch group)
+// ---------------------------------------------------------------------------
+enum { KC_GHOST = 0, KC_NODAL = 1, KC_POINTS = 2, KC_UPDATE = 3, KC_N = 4 };
+
+static cudaError_t prof_mark(fdcgks_t c, int cls, bool begin) {
+  if (!c->profiling) return cudaSuccess;
+  if (c->ev_used + 1 > c->ev_cap) {
+    int cap = c->ev_cap ? 2 * c->ev_cap : 256;
+    cudaEvent_t* ev = new cudaEvent_t[cap];
+    int* cl = new int[cap / 2];
+    for (int k = 0; k < c->ev_cap; ++k) ev[k] = c->ev[k];
+    for (int k = 0; k < c->ev_cap / 2; ++k) cl[k] = c->ev_class[k];
+    for (int k = c->ev_cap; k < cap; ++k) {
+      cudaError_t e = cudaEventCreate(&ev[k]);
+      if (e != cudaSuccess) { delete[] ev; delete[] cl; return e; }
+    }
+    delete[] c->ev;
+    delete[] c->ev_class;
+    c->ev = ev;
+    c->ev_class = cl;
+    c->ev_cap = cap;
+  }
+  if (!begin) c->ev_class[c->ev_used / 2] = cls;
+  return cudaEventRecord(c->ev[c->ev_used++], c->stream);
+}
+
+// ---------------------------------------------------------------------------
 // stage sequencing
 // ---------------------------------------------------------------------------
 template <class R>
@@ -258,13 +291,22 @@ template <class R>
 static fdcgks_status run_stage(fdcgks_t c, double dt, int mode, double* const* op) {
   const double* S = mode == UPD_STAGE2 ? c->S2 : c->S;
   double* Sout = mode == UPD_STAGE1 ? c->S2 : c->S;
+  CUDA_TRY(c, prof_mark(c, KC_GHOST, true));
   CUDA_TRY(c, fill_ghosts(c, const_cast<double*>(S)));
+  CUDA_TRY(c, prof_mark(c, KC_GHOST, false));
   KArgs<R> a = make_args<R>(c, dt, S, Sout, mode != UPD_STAGE2);
   if (op)
     for (int k = 0; k < 8; ++k) a.op[k] = op[k];
+  CUDA_TRY(c, prof_mark(c, KC_NODAL, true));
   CUDA_TRY(c, launch_nodal<R>(a, c->stream));
+  CUDA_TRY(c, prof_mark(c, KC_NODAL, false));
+  CUDA_TRY(c, prof_mark(c, KC_POINTS, true));
   CUDA_TRY(c, launch_points<R>(a, c->stream));
+  CUDA_TRY(c, prof_mark(c, KC_POINTS, false));
+  CUDA_TRY(c, prof_mark(c, KC_UPDATE, true));
   CUDA_TRY(c, launch_update<R>(a, mode, c->stream));
+  CUDA_TRY(c, prof_mark(c, KC_UPDATE, false));
+  c->launches += 6;   // 2 ghost passes, nodal, 2 point types, update
   return FDCGKS_OK;
 }
 
@@ -297,6 +339,9 @@ const char* fdcgks_last_error(fdcgks_t ctx) { return ctx ? ctx->err : g_err; }
 
 void fdcgks_destroy(fdcgks_t c) {
   if (!c) return;
+  for (int k = 0; k < c->ev_cap; ++k) cudaEventDestroy(c->ev[k]);
+  delete[] c->ev;
+  delete[] c->ev_class;
   void* bufs[] = {c->S, c->S2, c->Wacc, c->gB, c->NF, c->PA, c->PB, c->flag, c->red};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -502,6 +547,32 @@ fdcgks_status fdcgks_stage_operator(fdcgks_t c, double dt, double* Lp, double* L
     if (!q) return fail(c, FDCGKS_ERR_ARG, "NULL output pointer");
   return c->p.precision == FDCGKS_MIXED ? run_stage<float>(c, dt, UPD_OPERATOR, op)
                                         : run_stage<double>(c, dt, UPD_OPERATOR, op);
+}
+
+fdcgks_status fdcgks_set_profiling(fdcgks_t c, int enable) {
+  if (!c) return fail(nullptr, FDCGKS_ERR_ARG, "ctx is NULL");
+  c->profiling = enable ? 1 : 0;
+  c->ev_used = 0;
+  return FDCGKS_OK;
+}
+
+fdcgks_status fdcgks_get_profile(fdcgks_t c, double* ms, int* count, long long* launches) {
+  if (!c) return fail(nullptr, FDCGKS_ERR_ARG, "ctx is NULL");
+  if (ms)
+    for (int k = 0; k < KC_N; ++k) ms[k] = 0.0;
+  if (count)
+    for (int k = 0; k < KC_N; ++k) count[k] = 0;
+  if (c->ev_used) CUDA_TRY(c, cudaEventSynchronize(c->ev[c->ev_used - 1]));
+  for (int k = 0; k + 1 < c->ev_used; k += 2) {
+    float t = 0.f;
+    CUDA_TRY(c, cudaEventElapsedTime(&t, c->ev[k], c->ev[k + 1]));
+    int cls = c->ev_class[k / 2];
+    if (ms) ms[cls] += t;
+    if (count) count[cls] += 1;
+  }
+  c->ev_used = 0;
+  if (launches) *launches = c->launches;
+  return FDCGKS_OK;
 }
 
 fdcgks_status fdcgks_iface_batch(const fdcgks_params* p, int normal, double dt, int n, const double* in, double* out) {

@@ -34,8 +34,14 @@ FD_HD double s_min(double a, double b) { return fmin(a, b); }
 FD_HD float s_min(float a, float b) { return fminf(a, b); }
 FD_HD double s_max(double a, double b) { return fmax(a, b); }
 FD_HD float s_max(float a, float b) { return fmaxf(a, b); }
-template <class R> FD_HD R to_R(double x) { return (R)x; }
-template <class R> FD_HD double to_d(R x) { return (double)x; }
+FD_HD double s_expm1(double x) { return expm1(x); }
+
+// The FP64 part of the arithmetic (collision time and time coefficients) runs
+// in Wide<R>::T: double for both compute types; an instrumented scalar type
+// maps to its own wide counterpart.
+template <class R> struct Wide { typedef double T; };
+template <class R> FD_HD typename Wide<R>::T to_w(R x) { return (typename Wide<R>::T)x; }
+template <class R> FD_HD R from_w(typename Wide<R>::T x) { return (R)x; }
 
 // value at which tanh(z) rounds to exactly 1 in the compute type
 template <class R> struct TanhSat;
@@ -312,35 +318,38 @@ FD_HD R heat_flux_y(const R G[4], const R W[4], R U0, R V0) {
 // [0, delta] for delta = dt/2 and dt and fitted to f^n + t f_t^n (App. A1).
 // Always FP64: the coefficients cancel when dt/tau is small.
 // ---------------------------------------------------------------------------
+template <class TW>
 struct TimeCoef {
-  double cn[6], ct[6];
-  double E, e1;   // exp(-dt/tau), 1 - exp(-dt/tau)
+  TW cn[6], ct[6];
+  TW E, e1;   // exp(-dt/tau), 1 - exp(-dt/tau)
 };
 
-FD_HD void time_integrals_d(double tau, double d, double E, double e1, double C[6]) {
+template <class TW>
+FD_HD void time_integrals_d(TW tau, TW d, TW E, TW e1, TW C[6]) {
   C[0] = d - tau * e1;
-  C[1] = -tau * d * (1.0 + E) + 2.0 * tau * tau * e1;
-  C[2] = 0.5 * d * d - tau * d + tau * tau * e1;
+  C[1] = -tau * d * (TW(1) + E) + TW(2) * tau * tau * e1;
+  C[2] = TW(0.5) * d * d - tau * d + tau * tau * e1;
   C[3] = tau * e1;
-  C[4] = tau * d * E - 2.0 * tau * tau * e1;
+  C[4] = tau * d * E - TW(2) * tau * tau * e1;
   C[5] = -tau * tau * e1;
 }
 
-FD_HD TimeCoef time_coef(double tau, double dt) {
-  TimeCoef t;
+template <class TW>
+FD_HD TimeCoef<TW> time_coef(TW tau, TW dt) {
+  TimeCoef<TW> t;
   // one transcendental: em = exp(-dt/(2 tau)) - 1, then
   // exp(-dt/tau) - 1 = em (em + 2) without cancellation
-  double em = expm1(-0.5 * dt / tau);
-  double Eh = 1.0 + em, e1h = -em;
+  TW em = s_expm1(-TW(0.5) * dt / tau);
+  TW Eh = TW(1) + em, e1h = -em;
   t.E = Eh * Eh;
-  t.e1 = -em * (em + 2.0);
-  double Ch[6], Cf[6];
-  time_integrals_d(tau, 0.5 * dt, Eh, e1h, Ch);
+  t.e1 = -em * (em + TW(2));
+  TW Ch[6], Cf[6];
+  time_integrals_d(tau, TW(0.5) * dt, Eh, e1h, Ch);
   time_integrals_d(tau, dt, t.E, t.e1, Cf);
-  double idt = 1.0 / dt;
+  TW idt = TW(1) / dt;
   for (int k = 0; k < 6; ++k) {
-    t.cn[k] = (4.0 * Ch[k] - Cf[k]) * idt;
-    t.ct[k] = 4.0 * (Cf[k] - 2.0 * Ch[k]) * idt * idt;
+    t.cn[k] = (TW(4) * Ch[k] - Cf[k]) * idt;
+    t.ct[k] = TW(4) * (Cf[k] - TW(2) * Ch[k]) * idt * idt;
   }
   return t;
 }
@@ -418,13 +427,15 @@ FD_HD void iface_solve_x(const GasK<R>& gas, const R Wl[4], const R Wr[4], const
   slope_solve(g0, K, r0, A0);
 
   // collision time and time coefficients (FP64)
-  double pl = to_d(gl.rho / (R(2) * gl.lam)), pr = to_d(gr.rho / (R(2) * gr.lam));
-  double p0 = to_d(g0.rho / (R(2) * g0.lam));
-  double tau = gas.c1 * gas.dt + gas.mu / p0 + gas.c2 * gas.dt * fabs(pl - pr) / (pl + pr);
-  TimeCoef tc = time_coef(tau, gas.dt);
+  typedef typename Wide<R>::T TW;
+  TW pl = to_w(gl.rho / (R(2) * gl.lam)), pr = to_w(gr.rho / (R(2) * gr.lam));
+  TW p0 = to_w(g0.rho / (R(2) * g0.lam));
+  TW dtw = TW(gas.dt);
+  TW tau = TW(gas.c1) * dtw + TW(gas.mu) / p0 + TW(gas.c2) * dtw * s_abs(pl - pr) / (pl + pr);
+  TimeCoef<TW> tc = time_coef(tau, dtw);
   R cn[6], ct[6];
 #pragma unroll
-  for (int k = 0; k < 6; ++k) { cn[k] = to_R<R>(tc.cn[k]); ct[k] = to_R<R>(tc.ct[k]); }
+  for (int k = 0; k < 6; ++k) { cn[k] = from_w<R>(tc.cn[k]); ct[k] = from_w<R>(tc.ct[k]); }
 
   // moment vectors of the six basis terms, flux (u psi) and W (psi)
   R F[4], Ftt[4], We[4], Wet[4];
@@ -493,7 +504,7 @@ FD_HD void iface_solve_x(const GasK<R>& gas, const R Wl[4], const R Wr[4], const
 
   // interface flow variables, Eq. (eq:W-model) with tau_0 = tau; the one-sided
   // time derivatives are W_t = -rho <(a u + b v) psi> = rho * (compatibility rhs)
-  R E = to_R<R>(tc.E), e1 = to_R<R>(tc.e1);
+  R E = from_w<R>(tc.E), e1 = from_w<R>(tc.e1);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     o.Ft[k] = Ftt[k];
@@ -552,7 +563,8 @@ FD_HD void nodal_flux(const GasK<R>& gas, const R W[4], const R Wx[4], const R W
   slope_solve(g, K, r, A);
 #pragma unroll
   for (int k = 0; k < 4; ++k) Wt[k] = g.rho * r[k];   // int psi A g
-  R tau = to_R<R>(gas.c1 * gas.dt + gas.mu / to_d(g.rho / (R(2) * g.lam)));
+  typedef typename Wide<R>::T TW;
+  R tau = from_w<R>(TW(gas.c1) * TW(gas.dt) + TW(gas.mu) / to_w(g.rho / (R(2) * g.lam)));
 
   R e0[4], ea[4], eb[4], eA[4];
   // x-flux

@@ -21,7 +21,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "non-physical stat
 EXPORTS = ["fdcgks_create", "fdcgks_destroy", "fdcgks_dims", "fdcgks_set_state", "fdcgks_get_state",
            "fdcgks_step", "fdcgks_steps", "fdcgks_cfl_dt", "fdcgks_check", "fdcgks_stage_operator",
            "fdcgks_iface_batch", "fdcgks_nodal_batch", "fdcgks_recon_batch", "fdcgks_last_error",
-           "fdcgks_status_string"]
+           "fdcgks_status_string", "fdcgks_set_profiling", "fdcgks_get_profile"]
 
 
 class Params(ctypes.Structure):
@@ -78,13 +78,16 @@ def load(path=None):
     lib.fdcgks_iface_batch.argtypes = [ctypes.POINTER(Params), ctypes.c_int, ctypes.c_double, ctypes.c_int, _VP, _VP]
     lib.fdcgks_nodal_batch.argtypes = [ctypes.POINTER(Params), ctypes.c_double, ctypes.c_int, _VP, _VP]
     lib.fdcgks_recon_batch.argtypes = [ctypes.POINTER(Params), ctypes.c_int, ctypes.c_double, ctypes.c_int, _VP, _VP]
+    lib.fdcgks_set_profiling.argtypes = [_VP, ctypes.c_int]
+    lib.fdcgks_get_profile.argtypes = [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_longlong)]
     lib.fdcgks_last_error.argtypes = [_VP]
     lib.fdcgks_last_error.restype = ctypes.c_char_p
     lib.fdcgks_status_string.argtypes = [ctypes.c_int]
     lib.fdcgks_status_string.restype = ctypes.c_char_p
     for name in ("fdcgks_create", "fdcgks_dims", "fdcgks_set_state", "fdcgks_get_state", "fdcgks_step",
                  "fdcgks_steps", "fdcgks_cfl_dt", "fdcgks_check", "fdcgks_stage_operator", "fdcgks_iface_batch",
-                 "fdcgks_nodal_batch", "fdcgks_recon_batch"):
+                 "fdcgks_nodal_batch", "fdcgks_recon_batch", "fdcgks_set_profiling", "fdcgks_get_profile"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -225,6 +228,21 @@ class Solver:
         out = ctypes.c_int()
         _check(load().fdcgks_check(self._h, ctypes.byref(out)), self._h)
         return bool(out.value)
+
+    def set_profiling(self, enable=True):
+        _check(load().fdcgks_set_profiling(self._h, int(bool(enable))), self._h)
+
+    def get_profile(self):
+        """(ms per class, launch groups per class, total launches); classes: ghost, nodal, points, update."""
+        ms = (ctypes.c_double * 4)()
+        cn = (ctypes.c_int * 4)()
+        n = ctypes.c_longlong()
+        _check(load().fdcgks_get_profile(self._h, ms, cn, ctypes.byref(n)), self._h)
+        names = ("ghost", "nodal", "points", "update")
+        return dict(zip(names, list(ms))), dict(zip(names, list(cn))), n.value
+
+    def launches(self):
+        return self.get_profile()[2]
 
     def stage_operator(self, dt):
         import torch
