@@ -163,6 +163,34 @@ fdcgks_status fdcgks_nodal_batch(const fdcgks_params* params, double dt, int n, 
 fdcgks_status fdcgks_recon_batch(const fdcgks_params* params, int kind, double h, int n, const double* in,
                                  double* out);
 
+/* Allocation-free CFL time step.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory when they need
+ * a time step, e.g. code running while a stream is captured into a CUDA graph
+ * (allocation calls are not allowed there), hosts that give the library a
+ * fixed memory budget, or loops that must not risk an allocation failure or
+ * the synchronisation cudaMalloc/cudaFree can imply.  It computes the same
+ * time step as fdcgks_cfl_dt, from the caller's device arrays Wp [4][ny][nx]
+ * and Wd [4][nyd][nxd] (float64, read only), without a context and without
+ * allocating: its partial maxima live in a fixed device array of the library
+ * (FDCGKS_NOALLOC_MAX_TILES tiles of FDCGKS_NOALLOC_TILE_NODES nodes, 64 KB),
+ * which every GPU that loads the library holds until the process exits.
+ *   - Uses params' nx, ny, bc (for nxd, nyd), domain, gamma, mu and stream;
+ *     runs on params->stream and synchronizes it to read the result.
+ *   - Grids with more than FDCGKS_NOALLOC_MAX_TILES * FDCGKS_NOALLOC_TILE_NODES
+ *     primary plus dual nodes are rejected with FDCGKS_ERR_ARG.
+ *   - The first call on each device looks up the device address of the
+ *     library's array (once per device, with that device current); make that
+ *     first call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents;
+ *     each call writes every entry it reads, so nothing needs clearing, but
+ *     calls that overlap on the GPU (other streams, other host threads) race
+ *     on it and must be serialized by the caller.
+ *   - Errors are reported through fdcgks_last_error(NULL). */
+#define FDCGKS_NOALLOC_TILE_NODES 4096
+#define FDCGKS_NOALLOC_MAX_TILES 4096
+fdcgks_status fdcgks_cfl_dt_noalloc(const fdcgks_params* params, const double* Wp, const double* Wd, double cfl,
+                                    double* dt_out);
+
 /* Message of the last failed call on ctx (or of the last failed
  * context-free call when ctx is NULL). */
 const char* fdcgks_last_error(fdcgks_t ctx);

@@ -38,6 +38,8 @@ struct fdcgks_ctx {
 
 static char g_err[512] = "";
 
+void fdk::set_global_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
 static fdcgks_status fail(fdcgks_t c, fdcgks_status s, const char* fmt, ...) {
   char* dst = c ? c->err : g_err;
   va_list ap;

@@ -57,6 +57,9 @@ struct KArgs {
 
 enum { UPD_STAGE1 = 0, UPD_STAGE2 = 1, UPD_OPERATOR = 2 };
 
+// message returned by fdcgks_last_error(NULL)
+void set_global_error(const char* msg);
+
 template <class R> cudaError_t launch_nodal(const KArgs<R>& a, cudaStream_t s);
 template <class R> cudaError_t launch_points(const KArgs<R>& a, cudaStream_t s);
 template <class R> cudaError_t launch_update(const KArgs<R>& a, int mode, cudaStream_t s);

@@ -21,7 +21,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "non-physical stat
 EXPORTS = ["fdcgks_create", "fdcgks_destroy", "fdcgks_dims", "fdcgks_set_state", "fdcgks_get_state",
            "fdcgks_step", "fdcgks_steps", "fdcgks_cfl_dt", "fdcgks_check", "fdcgks_stage_operator",
            "fdcgks_iface_batch", "fdcgks_nodal_batch", "fdcgks_recon_batch", "fdcgks_last_error",
-           "fdcgks_status_string", "fdcgks_set_profiling", "fdcgks_get_profile"]
+           "fdcgks_status_string", "fdcgks_set_profiling", "fdcgks_get_profile", "fdcgks_cfl_dt_noalloc"]
 
 
 class Params(ctypes.Structure):
@@ -81,13 +81,16 @@ def load(path=None):
     lib.fdcgks_set_profiling.argtypes = [_VP, ctypes.c_int]
     lib.fdcgks_get_profile.argtypes = [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_longlong)]
+    lib.fdcgks_cfl_dt_noalloc.argtypes = [ctypes.POINTER(Params), _VP, _VP, ctypes.c_double,
+                                          ctypes.POINTER(ctypes.c_double)]
     lib.fdcgks_last_error.argtypes = [_VP]
     lib.fdcgks_last_error.restype = ctypes.c_char_p
     lib.fdcgks_status_string.argtypes = [ctypes.c_int]
     lib.fdcgks_status_string.restype = ctypes.c_char_p
     for name in ("fdcgks_create", "fdcgks_dims", "fdcgks_set_state", "fdcgks_get_state", "fdcgks_step",
                  "fdcgks_steps", "fdcgks_cfl_dt", "fdcgks_check", "fdcgks_stage_operator", "fdcgks_iface_batch",
-                 "fdcgks_nodal_batch", "fdcgks_recon_batch", "fdcgks_set_profiling", "fdcgks_get_profile"):
+                 "fdcgks_nodal_batch", "fdcgks_recon_batch", "fdcgks_set_profiling", "fdcgks_get_profile",
+                 "fdcgks_cfl_dt_noalloc"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -292,3 +295,24 @@ def recon_batch(params, kind, h, inp, out=None):
     _check(load().fdcgks_recon_batch(ctypes.byref(params), int(kind), ctypes.c_double(h), n,
                                      _dptr(inp, (8 if kind == 0 else 6) * n), _dptr(out, 6 * n)))
     return out
+
+
+def cfl_dt_noalloc(params, Wp, Wd, cfl):
+    """CFL time step from caller-owned device arrays without any allocation.
+
+    For callers that cannot allocate device memory when they need a time step
+    (stream capture in progress, a fixed memory budget, no allocation allowed in
+    the loop).  Wp: [4, ny, nx], Wd: [4, nyd, nxd] contiguous float64 CUDA
+    tensors.  The library keeps the partial maxima in a fixed device array
+    shared by all calls; calls that overlap on the GPU race on it.  The first
+    call on a device looks up that array's address, so make it before any
+    stream capture.
+    """
+    if params.stream is None:
+        params.stream = _stream().value
+    nxd = params.nx + (0 if params.bc[0] == BC_PERIODIC else 1)
+    nyd = params.ny + (0 if params.bc[2] == BC_PERIODIC else 1)
+    out = ctypes.c_double()
+    _check(load().fdcgks_cfl_dt_noalloc(ctypes.byref(params), _dptr(Wp, 4 * params.nx * params.ny),
+                                        _dptr(Wd, 4 * nxd * nyd), ctypes.c_double(cfl), ctypes.byref(out)))
+    return out.value
