@@ -38,6 +38,31 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
+def kernel_hash():
+    """Hash of the kernel sources; profiles/ summaries record the hash they were taken on."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("fdcgks_math.cuh", "fdcgks_kernels.cuh", "fdcgks_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2606_17772_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(name, n):
+    """DRAM bytes per launch from a committed ncu summary, if it matches this
+    kernel source and grid (otherwise None)."""
+    path = os.path.join(ROOT, "profiles", name)
+    if n != 1024 or not os.path.exists(path):
+        return None
+    text = open(path).read()
+    if "kernel_hash: " + kernel_hash() not in text:
+        return None
+    for line in text.splitlines():
+        if line.startswith("traffic_bytes_per_launch:"):
+            return int(line.split(":")[1])
+    return None
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -248,7 +273,9 @@ def main():
     pt_ms = fp["prof_ms"]["points"] / max(fp["prof_n"]["points"], 1)
     achieved = pt_flops / (pt_ms / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "frac": achieved / FP64_PEAK_TFLOPS,
+            "traffic": profiled_traffic("point_kernel_fp64_vortex1024.md", n),
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch (profiles/)",
             "kernel": "point_kernel (Type A + Type B interface points, FP64)",
             "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
             "step_share": fp["prof_ms"]["points"] / max(sum(fp["prof_ms"].values()), 1e-9),

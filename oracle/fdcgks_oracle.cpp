@@ -38,7 +38,12 @@
 //   * Node placement: primary nodes at cell centres, dual nodes at cell
 //     corners; n dual nodes per periodic direction, n+1 per bounded one.
 //     Ghost layers by periodic wrap, mirror (symmetry / no-slip wall) or
-//     constant extrapolation (transmissive).  Dual nodes on a no-slip wall
+//     constant extrapolation (transmissive).
+//
+// Parity unpinned: the form and constants of the collision time tau and the
+// choice tau_0 = tau are exercised by no number the paper prints (its
+// accuracy tables use tau = 0); the no-slip wall treatment is pinned only by
+// symmetry, free-stream and conservation-bound tests.  Dual nodes on a no-slip wall
 //     have their velocity, and the averaged momentum gradients along the
 //     wall, set to zero after each stage.
 #include <cmath>
