@@ -16,8 +16,18 @@ struct fdcgks_ctx {
   Layout L;
   double hx, hy;
   cudaStream_t stream;
-  double* S = nullptr;      // state [2][12][plane]
-  double* S2 = nullptr;     // stage state
+  double* S = nullptr;      // state [2][12][plane] (FP64 path; staging of set/get_state in the mixed path)
+  double* S2 = nullptr;     // stage state (FP64 path)
+  // mixed path: the state as float-float pairs (high parts with ghost layers,
+  // read by the nodal/point kernels), the stage state (high parts) and the
+  // S2O4 accumulators as pairs
+  float* Sf = nullptr;
+  float* Slo = nullptr;
+  float* S2f = nullptr;
+  float* Acc_hi = nullptr;
+  float* Acc_lo = nullptr;
+  float* Gb_hi = nullptr;
+  float* Gb_lo = nullptr;
   double* Wacc = nullptr;   // [2][4][plane]
   double* gB = nullptr;     // [2][8][plane]
   void* NF = nullptr;       // nodal fluxes [2][16][plane] of the compute type
@@ -65,6 +75,7 @@ static GenoK<R> make_geno(int variant) {
   g.linear = variant == 2;
   g.C = (R)20.0;
   g.tanhC = (R)std::tanh(20.0);
+  g.inv_tanhC = (R)(1.0 / std::tanh(20.0));
   g.eps_w = (R)1e-6;
   if (variant == 1) {
     g.r = 3;
@@ -82,12 +93,21 @@ static GenoK<R> make_geno(int variant) {
 template <class R>
 static GasK<R> make_gas(const fdcgks_params& p, double dt) {
   GasK<R> g;
-  g.K = (R)((4.0 - 2.0 * p.gamma) / (p.gamma - 1.0));
+  const double K = (4.0 - 2.0 * p.gamma) / (p.gamma - 1.0);
+  g.K = (R)K;
+  g.gm1 = (R)(p.gamma - 1.0);
+  g.c4K = (R)(4.0 / (K + 2.0));
   g.prfix = (R)(1.0 / p.Pr - 1.0);
   g.mu = p.mu;
   g.c1 = p.tau_c1;
   g.c2 = p.tau_c2;
   g.dt = dt;
+  g.inv_dt = 1.0 / dt;
+  g.mu_r = (R)p.mu;
+  g.c1_r = (R)p.tau_c1;
+  g.c2_r = (R)p.tau_c2;
+  g.dt_r = (R)dt;
+  g.inv_dt_r = (R)(1.0 / dt);
   return g;
 }
 
@@ -121,7 +141,8 @@ static size_t rsize(const fdcgks_params& p) { return p.precision == FDCGKS_MIXED
 // extrapolation (transmissive); x pass over interior rows, then y pass over
 // all columns so that corners are filled consistently
 // ---------------------------------------------------------------------------
-__global__ void ghost_kernel(double* S, Layout L, int bc0, int bc1, int dir) {
+template <class T>
+__global__ void ghost_kernel(T* S, Layout L, int bc0, int bc1, int dir) {
   const int g = blockIdx.z;
   const int nxg = g == 0 ? L.nx : L.nxd, nyg = g == 0 ? L.ny : L.nyd;
   const int n = dir == 0 ? nxg : nyg;
@@ -141,19 +162,19 @@ __global__ void ghost_kernel(double* S, Layout L, int bc0, int bc1, int dir) {
   else src = side == 0 ? k : n - 1 - k;
   const long gc = dir == 0 ? cell(L, ghost, t) : cell(L, t, ghost);
   const long sc = dir == 0 ? cell(L, src, t) : cell(L, t, src);
-  double* Sg = S + (long)g * NFLD * L.plane;
+  T* Sg = S + (long)g * NFLD * L.plane;
   for (int c = 0; c < 4; ++c) {
-    double sW = 1.0;
+    T sW = 1;
     if (b == FDCGKS_BC_SYMMETRY || b == FDCGKS_BC_NOSLIP) {
       if (c == 1 + dir) sW = -1.0;
       if (c == 2 - dir && b == FDCGKS_BC_NOSLIP) sW = -1.0;
     }
-    double w = Sg[(long)c * L.plane + sc];
-    double gx = Sg[(long)(4 + c) * L.plane + sc];
-    double gy = Sg[(long)(8 + c) * L.plane + sc];
+    T w = Sg[(long)c * L.plane + sc];
+    T gx = Sg[(long)(4 + c) * L.plane + sc];
+    T gy = Sg[(long)(8 + c) * L.plane + sc];
     if (b == FDCGKS_BC_TRANSMISSIVE) {
-      gx = 0.0;
-      gy = 0.0;
+      gx = 0;
+      gy = 0;
     } else if (b != FDCGKS_BC_PERIODIC) {
       w *= sW;
       gx *= (dir == 0 ? -sW : sW);
@@ -165,14 +186,34 @@ __global__ void ghost_kernel(double* S, Layout L, int bc0, int bc1, int dir) {
   }
 }
 
-static cudaError_t fill_ghosts(fdcgks_t c, double* S) {
+template <class T>
+static cudaError_t fill_ghosts(fdcgks_t c, T* S) {
   const Layout& L = c->L;
   int tx = (L.ny > L.nyd ? L.ny : L.nyd) * 2 * GH;
-  ghost_kernel<<<dim3((tx + 127) / 128, 1, 2), 128, 0, c->stream>>>(S, L, c->p.bc[0], c->p.bc[1], 0);
+  ghost_kernel<T><<<dim3((tx + 127) / 128, 1, 2), 128, 0, c->stream>>>(S, L, c->p.bc[0], c->p.bc[1], 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int ty = ((L.nx > L.nxd ? L.nx : L.nxd) + 2 * GH) * 2 * GH;
-  ghost_kernel<<<dim3((ty + 127) / 128, 1, 2), 128, 0, c->stream>>>(S, L, c->p.bc[2], c->p.bc[3], 1);
+  ghost_kernel<T><<<dim3((ty + 127) / 128, 1, 2), 128, 0, c->stream>>>(S, L, c->p.bc[2], c->p.bc[3], 1);
+  return cudaGetLastError();
+}
+
+// mixed path: FP64 state <-> float-float pairs (whole padded planes)
+__global__ void split_ff_kernel(const double* S, float* hi, float* lo, long n) {
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+    float h = (float)S[t];
+    hi[t] = h;
+    lo[t] = (float)(S[t] - (double)h);
+  }
+}
+__global__ void join_ff_kernel(const float* hi, const float* lo, double* S, long n) {
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+    S[t] = (double)hi[t] + (double)lo[t];
+}
+
+static cudaError_t join_state(fdcgks_t c) {
+  if (!c->Sf) return cudaSuccess;
+  join_ff_kernel<<<1024, 256, 0, c->stream>>>(c->Sf, c->Slo, c->S, 2L * NFLD * c->L.plane);
   return cudaGetLastError();
 }
 
@@ -289,14 +330,31 @@ static KArgs<R> make_args(fdcgks_t c, double dt, const double* S, double* Sout, 
   return a;
 }
 
+// precision-specific state pointers of one stage
+static void stage_state(fdcgks_t c, int mode, KArgs<double>& a) {
+  a.S = mode == UPD_STAGE2 ? c->S2 : c->S;
+  a.Sout = mode == UPD_STAGE1 ? c->S2 : c->S;
+  a.Sr = a.S;
+}
+static void stage_state(fdcgks_t c, int mode, KArgs<float>& a) {
+  a.Sr = mode == UPD_STAGE2 ? c->S2f : c->Sf;
+  a.Sn_hi = c->Sf;
+  a.Sn_lo = c->Slo;
+  a.Out_hi = mode == UPD_STAGE1 ? c->S2f : c->Sf;
+  a.Out_lo = mode == UPD_STAGE1 ? nullptr : c->Slo;
+  a.Acc_hi = c->Acc_hi;
+  a.Acc_lo = c->Acc_lo;
+  a.Gb_hi = c->Gb_hi;
+  a.Gb_lo = c->Gb_lo;
+}
+
 template <class R>
 static fdcgks_status run_stage(fdcgks_t c, double dt, int mode, double* const* op) {
-  const double* S = mode == UPD_STAGE2 ? c->S2 : c->S;
-  double* Sout = mode == UPD_STAGE1 ? c->S2 : c->S;
+  KArgs<R> a = make_args<R>(c, dt, nullptr, nullptr, mode != UPD_STAGE2);
+  stage_state(c, mode, a);
   CUDA_TRY(c, prof_mark(c, KC_GHOST, true));
-  CUDA_TRY(c, fill_ghosts(c, const_cast<double*>(S)));
+  CUDA_TRY(c, fill_ghosts(c, const_cast<R*>(a.Sr)));
   CUDA_TRY(c, prof_mark(c, KC_GHOST, false));
-  KArgs<R> a = make_args<R>(c, dt, S, Sout, mode != UPD_STAGE2);
   if (op)
     for (int k = 0; k < 8; ++k) a.op[k] = op[k];
   CUDA_TRY(c, prof_mark(c, KC_NODAL, true));
@@ -344,7 +402,8 @@ void fdcgks_destroy(fdcgks_t c) {
   for (int k = 0; k < c->ev_cap; ++k) cudaEventDestroy(c->ev[k]);
   delete[] c->ev;
   delete[] c->ev_class;
-  void* bufs[] = {c->S, c->S2, c->Wacc, c->gB, c->NF, c->PA, c->PB, c->flag, c->red};
+  void* bufs[] = {c->S, c->S2, c->Sf, c->Slo, c->S2f, c->Acc_hi, c->Acc_lo, c->Gb_hi, c->Gb_lo,
+                  c->Wacc, c->gB, c->NF, c->PA, c->PB, c->flag, c->red};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete c;
@@ -374,17 +433,27 @@ fdcgks_status fdcgks_create(const fdcgks_params* p, fdcgks_t* out) {
   L.prows = my + 3;
   L.pplane = (long)L.ppitch * L.prows;
   const size_t rs = rsize(*p);
+  const bool mixed = p->precision == FDCGKS_MIXED;
+  const size_t fp = sizeof(float) * L.plane;
   struct { void** ptr; size_t bytes; } allocs[] = {
       {(void**)&c->S, sizeof(double) * 2 * NFLD * L.plane},
-      {(void**)&c->S2, sizeof(double) * 2 * NFLD * L.plane},
-      {(void**)&c->Wacc, sizeof(double) * 2 * 4 * L.plane},
-      {(void**)&c->gB, sizeof(double) * 2 * 8 * L.plane},
+      {(void**)&c->S2, mixed ? 0 : sizeof(double) * 2 * NFLD * L.plane},
+      {(void**)&c->Wacc, mixed ? 0 : sizeof(double) * 2 * 4 * L.plane},
+      {(void**)&c->gB, mixed ? 0 : sizeof(double) * 2 * 8 * L.plane},
+      {(void**)&c->Sf, mixed ? fp * 2 * NFLD : 0},
+      {(void**)&c->Slo, mixed ? fp * 2 * NFLD : 0},
+      {(void**)&c->S2f, mixed ? fp * 2 * NFLD : 0},
+      {(void**)&c->Acc_hi, mixed ? fp * 2 * 4 : 0},
+      {(void**)&c->Acc_lo, mixed ? fp * 2 * 4 : 0},
+      {(void**)&c->Gb_hi, mixed ? fp * 2 * 8 : 0},
+      {(void**)&c->Gb_lo, mixed ? fp * 2 * 8 : 0},
       {&c->NF, rs * 2 * NNF * L.plane},
       {&c->PA, rs * NPT * L.pplane},
       {&c->PB, rs * NPT * L.pplane},
       {(void**)&c->flag, sizeof(int) * 4},
   };
   for (auto& a : allocs) {
+    if (a.bytes == 0) continue;
     cudaError_t e = cudaMalloc(a.ptr, a.bytes);
     if (e != cudaSuccess) {
       fail(nullptr, e == cudaErrorMemoryAllocation ? FDCGKS_ERR_NOMEM : FDCGKS_ERR_CUDA, "cudaMalloc(%zu): %s",
@@ -401,7 +470,9 @@ fdcgks_status fdcgks_create(const fdcgks_params* p, fdcgks_t* out) {
   // zero everything once so that ghost corners and unused entries are defined
   cudaError_t e = cudaSuccess;
   e = e == cudaSuccess ? cudaMemsetAsync(c->S, 0, sizeof(double) * 2 * NFLD * L.plane, c->stream) : e;
-  e = e == cudaSuccess ? cudaMemsetAsync(c->S2, 0, sizeof(double) * 2 * NFLD * L.plane, c->stream) : e;
+  if (c->S2) e = e == cudaSuccess ? cudaMemsetAsync(c->S2, 0, sizeof(double) * 2 * NFLD * L.plane, c->stream) : e;
+  if (c->Sf) e = e == cudaSuccess ? cudaMemsetAsync(c->Sf, 0, sizeof(float) * 2 * NFLD * L.plane, c->stream) : e;
+  if (c->S2f) e = e == cudaSuccess ? cudaMemsetAsync(c->S2f, 0, sizeof(float) * 2 * NFLD * L.plane, c->stream) : e;
   e = e == cudaSuccess ? cudaMemsetAsync(c->flag, 0, sizeof(int) * 4, c->stream) : e;
   e = e == cudaSuccess ? cudaStreamSynchronize(c->stream) : e;
   if (e != cudaSuccess) {
@@ -450,6 +521,10 @@ fdcgks_status fdcgks_set_state(fdcgks_t c, const double* Wp, const double* Gp, c
       CUDA_TRY(c, copy_field(c, Sg + (long)f * L.plane, src, nullptr, nxg, nyg, true, on_device));
     }
   }
+  if (c->Sf) {
+    split_ff_kernel<<<1024, 256, 0, c->stream>>>(c->S, c->Sf, c->Slo, 2L * NFLD * L.plane);
+    CUDA_TRY(c, cudaGetLastError());
+  }
   CUDA_TRY(c, cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
   int mx = L.nx > L.nxd ? L.nx : L.nxd, my = L.ny > L.nyd ? L.ny : L.nyd;
   validate_kernel<<<dim3((mx + 127) / 128, my, 2), 128, 0, c->stream>>>(c->S, L, c->p.gamma, c->flag);
@@ -471,6 +546,7 @@ fdcgks_status fdcgks_get_state(fdcgks_t c, double* Wp, double* Gp, double* Wd, d
   if (!c->has_state) return fail(c, FDCGKS_ERR_STATE, "no state loaded");
   if (!Wp || !Gp || !Wd || !Gd) return fail(c, FDCGKS_ERR_ARG, "NULL state pointer");
   const Layout& L = c->L;
+  CUDA_TRY(c, join_state(c));
   double* dstW[2] = {Wp, Wd};
   double* dstG[2] = {Gp, Gd};
   for (int g = 0; g < 2; ++g) {
@@ -514,6 +590,7 @@ fdcgks_status fdcgks_cfl_dt(fdcgks_t c, double cfl, double* dt_out) {
   if (!c || !dt_out) return fail(c, FDCGKS_ERR_ARG, "NULL argument");
   if (!c->has_state) return fail(c, FDCGKS_ERR_STATE, "no state loaded");
   if (!(cfl > 0.0) || !std::isfinite(cfl)) return fail(c, FDCGKS_ERR_ARG, "cfl must be positive and finite");
+  CUDA_TRY(c, join_state(c));
   cfl_kernel<<<c->red_blocks, 256, 0, c->stream>>>(c->S, c->L, c->p.gamma, c->p.mu, 1.0 / c->hx, 1.0 / c->hy, c->red);
   CUDA_TRY(c, cudaGetLastError());
   double* h = new double[2 * c->red_blocks];

@@ -36,7 +36,18 @@ FD_HD long pcell(const Layout& L, int i, int j) { return (long)(j + 2) * L.ppitc
 template <class R>
 struct KArgs {
   Layout L;
-  const double* S;       // state read by this stage [2][12][plane]
+  const R* Sr;           // state read by the nodal and point kernels, in the compute type
+                         // (the FP64 state itself, or the high parts in the mixed path)
+  // mixed path: the state and the S2O4 accumulators are float-float pairs
+  const R* Sn_hi;        // state at t^n [2][12][plane], high and low parts
+  const R* Sn_lo;
+  R* Out_hi;             // stage 1: W*, grad* (high parts only); stage 2: the new state
+  R* Out_lo;             // stage 2: low parts of the new state (null at stage 1)
+  R* Acc_hi;             // W_acc pairs [2][4][plane]
+  R* Acc_lo;
+  R* Gb_hi;              // gradient-base pairs [2][8][plane]
+  R* Gb_lo;
+  const double* S;       // state read by this stage [2][12][plane] (FP64 path)
   const double* Sn;      // state at t^n (stage 1 base, reading-A gradient base)
   double* Sout;          // stage 1: W*, grad*;  stage 2: W^{n+1}, grad^{n+1}
   double* Wacc;          // [2][4][plane]  W^n + dt L + dt^2/6 L_t

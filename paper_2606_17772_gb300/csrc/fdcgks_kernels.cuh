@@ -21,14 +21,14 @@ __global__ void __launch_bounds__(128) nodal_kernel(KArgs<R> a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x - 1;
   const int j = blockIdx.y * blockDim.y + threadIdx.y - 1;
   if (i > nxg || j > nyg) return;
-  const double* S = a.S + (long)g * NFLD * L.plane;
+  const R* S = a.Sr + (long)g * NFLD * L.plane;
   const long c0 = cell(L, i, j);
   R W[4], Wx[4], Wy[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    const double* f = S + (long)c * L.plane;
-    const double* gx = S + (long)(4 + c) * L.plane;
-    const double* gy = S + (long)(8 + c) * L.plane;
+    const R* f = S + (long)c * L.plane;
+    const R* gx = S + (long)(4 + c) * L.plane;
+    const R* gy = S + (long)(8 + c) * L.plane;
     W[c] = (R)f[c0];
     R qx[3] = {(R)f[c0 - 1], W[c], (R)f[c0 + 1]};
     R gxv[3] = {(R)gx[c0 - 1], (R)gx[c0], (R)gx[c0 + 1]};
@@ -53,12 +53,12 @@ __global__ void __launch_bounds__(128) nodal_kernel(KArgs<R> a) {
 // (between entries 1 and 2): starting cell c0 (entry 0), stride between
 // entries, gradient field offset gfield (4: x-gradient, 8: y-gradient)
 template <class R>
-FD_HD void recon_line(const GenoK<R>& geno, const double* S, long plane, long c0, long stride, int gfield, R h,
+FD_HD void recon_line(const GenoK<R>& geno, const R* S, long plane, long c0, long stride, int gfield, R h,
                       R ih, R vl[4], R dl[4], R vr[4], R dr[4], R& chi) {
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    const double* f = S + (long)c * plane + c0;
-    const double* gr = S + (long)(gfield + c) * plane + c0;
+    const R* f = S + (long)c * plane + c0;
+    const R* gr = S + (long)(gfield + c) * plane + c0;
     R Q[4] = {(R)f[0], (R)f[stride], (R)f[2 * stride], (R)f[3 * stride]};
     R Qx[4] = {(R)gr[0], (R)gr[stride], (R)gr[2 * stride], (R)gr[3 * stride]};
     R cl, cr;
@@ -80,8 +80,8 @@ __global__ void __launch_bounds__(128) point_kernel(KArgs<R> a) {
   const int imax = TYPE == 0 ? L.nx : L.nxd;
   const int jmax = TYPE == 0 ? L.nyd : L.ny;
   if (i > imax || j > jmax) return;
-  const double* SP = a.S;
-  const double* SD = a.S + (long)NFLD * L.plane;
+  const R* SP = a.Sr;
+  const R* SD = a.Sr + (long)NFLD * L.plane;
   const int n0 = TYPE;        // normal of the primary-grid solve
   R l0v[4], l0d[4], r0v[4], r0d[4], chi0;
   R l1v[4], l1d[4], r1v[4], r1d[4], chi1;
@@ -137,14 +137,18 @@ __global__ void __launch_bounds__(128) point_kernel(KArgs<R> a) {
 // define-averaged-gradient, eq-nodal-update, eq-interface-update).
 // One thread per interior node of grid blockIdx.z.
 // ---------------------------------------------------------------------------
+
+// one node's stage operator: L, dL/dt (per component), the averaged gradients
+// re-evaluated from the interface solution (node's own side) and their time
+// derivatives
 template <class R>
-__global__ void __launch_bounds__(128) update_kernel(KArgs<R> a, int mode) {
-  const int g = blockIdx.z;
+struct NodeOp {
+  R L[4], Lt[4], gbx[4], gby[4], gtx[4], gty[4];
+};
+
+template <class R>
+__device__ __forceinline__ void node_operator(const KArgs<R>& a, int g, int i, int j, bool want_n, NodeOp<R>& o) {
   const Layout& L = a.L;
-  const int nxg = g == 0 ? L.nx : L.nxd, nyg = g == 0 ? L.ny : L.nyd;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= nxg || j >= nyg) return;
   const long pp = L.pplane;
   // x-interface k+1/2 of this grid's row and y-interface k+1/2 of its column
   const R* PX = g == 0 ? a.PA : a.PB + NPS * pp;   // primary: A points solve 0; dual: B points solve 1
@@ -152,22 +156,13 @@ __global__ void __launch_bounds__(128) update_kernel(KArgs<R> a, int mode) {
   auto xi = [&](int k) { return g == 0 ? pcell(L, k, j) : pcell(L, k, j - 1); };
   auto yi = [&](int k) { return g == 0 ? pcell(L, i, k) : pcell(L, i - 1, k); };
   const R* NF = a.NF + (long)g * NNF * L.plane;
-  const long c0 = cell(L, i, j);
   const long cN = cell(L, i, j);
   const int fv = a.flux_variant;
   const R ihx = a.ih[0], ihy = a.ih[1];
-
   const long xm2 = xi(i - 2), xm1 = xi(i - 1), x0 = xi(i), xp1 = xi(i + 1);
   const long ym2 = yi(j - 2), ym1 = yi(j - 1), y0 = yi(j), yp1 = yi(j + 1);
   const R chixm = PX[PO_CHI * pp + xm1], chix0 = PX[PO_CHI * pp + x0];
   const R chiym = PY[PO_CHI * pp + ym1], chiy0 = PY[PO_CHI * pp + y0];
-
-  double Wnew[4];
-  const double* Sg = a.S + (long)g * NFLD * L.plane;
-  const double* Sng = a.Sn + (long)g * NFLD * L.plane;
-  const long NN = (long)nxg * nyg;
-  const long oi = (long)j * nxg + i;
-  const double dt = a.dt;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     const R* nF = NF + (long)c * L.plane;
@@ -178,81 +173,184 @@ __global__ void __launch_bounds__(128) update_kernel(KArgs<R> a, int mode) {
     const R* pFt = PX + (long)(PO_FT + c) * pp;
     const R* qF = PY + (long)(PO_F + c) * pp;
     const R* qFt = PY + (long)(PO_FT + c) * pp;
-    R Lt, L0 = R(0);
     {
       R fp = compact_flux(fv, chix0, pFt[xm1], pFt[x0], pFt[xp1], nFt[cN], nFt[cN + 1]);
       R fm = compact_flux(fv, chixm, pFt[xm2], pFt[xm1], pFt[x0], nFt[cN - 1], nFt[cN]);
       R gp = compact_flux(fv, chiy0, qFt[ym1], qFt[y0], qFt[yp1], nGt[cN], nGt[cN + L.pitch]);
       R gm = compact_flux(fv, chiym, qFt[ym2], qFt[ym1], qFt[y0], nGt[cN - L.pitch], nGt[cN]);
-      Lt = -(fp - fm) * ihx - (gp - gm) * ihy;
+      o.Lt[c] = -(fp - fm) * ihx - (gp - gm) * ihy;
     }
-    if (mode != UPD_STAGE2) {
+    o.L[c] = R(0);
+    o.gbx[c] = R(0);
+    o.gby[c] = R(0);
+    if (want_n) {
       R fp = compact_flux(fv, chix0, pF[xm1], pF[x0], pF[xp1], nF[cN], nF[cN + 1]);
       R fm = compact_flux(fv, chixm, pF[xm2], pF[xm1], pF[x0], nF[cN - 1], nF[cN]);
       R gp = compact_flux(fv, chiy0, qF[ym1], qF[y0], qF[yp1], nG[cN], nG[cN + L.pitch]);
       R gm = compact_flux(fv, chiym, qF[ym2], qF[ym1], qF[y0], nG[cN - L.pitch], nG[cN]);
-      L0 = -(fp - fm) * ihx - (gp - gm) * ihy;
+      o.L[c] = -(fp - fm) * ihx - (gp - gm) * ihy;
+      o.gbx[c] = (PX[(PO_WL + c) * pp + x0] - PX[(PO_WR + c) * pp + xm1]) * ihx;
+      o.gby[c] = (PY[(PO_WL + c) * pp + y0] - PY[(PO_WR + c) * pp + ym1]) * ihy;
     }
-    // averaged gradients from the interface solution, node's own side
-    R gtx = (PX[(PO_WLT + c) * pp + x0] - PX[(PO_WRT + c) * pp + xm1]) * ihx;
-    R gty = (PY[(PO_WLT + c) * pp + y0] - PY[(PO_WRT + c) * pp + ym1]) * ihy;
-    R gbx = R(0), gby = R(0);
-    if (mode != UPD_STAGE2) {
-      gbx = (PX[(PO_WL + c) * pp + x0] - PX[(PO_WR + c) * pp + xm1]) * ihx;
-      gby = (PY[(PO_WL + c) * pp + y0] - PY[(PO_WR + c) * pp + ym1]) * ihy;
-    }
-    if (mode == UPD_OPERATOR) {
-      double** op = a.op + 4 * g;
-      op[0][c * NN + oi] = (double)L0;
-      op[1][c * NN + oi] = (double)Lt;
-      op[2][c * NN + oi] = (double)gbx;
-      op[2][(4 + c) * NN + oi] = (double)gby;
-      op[3][c * NN + oi] = (double)gtx;
-      op[3][(4 + c) * NN + oi] = (double)gty;
-      continue;
-    }
-    double* Og = a.Sout + (long)g * NFLD * L.plane;
-    double* Ag = a.Wacc + (long)g * 4 * L.plane;
-    double* Bg = a.gB + (long)g * 8 * L.plane;
-    if (mode == UPD_STAGE1) {
-      double Wn = Sng[(long)c * L.plane + c0];
-      double dL = (double)L0, dLt = (double)Lt;
-      Wnew[c] = Wn + 0.5 * dt * dL + 0.125 * dt * dt * dLt;
-      Ag[(long)c * L.plane + c0] = Wn + dt * dL + dt * dt / 6.0 * dLt;
-      double bx = a.grad_base ? Sng[(long)(4 + c) * L.plane + c0] : (double)gbx;
-      double by = a.grad_base ? Sng[(long)(8 + c) * L.plane + c0] : (double)gby;
-      Bg[(long)c * L.plane + c0] = bx;
-      Bg[(long)(4 + c) * L.plane + c0] = by;
-      Og[(long)(4 + c) * L.plane + c0] = bx + 0.5 * dt * (double)gtx;
-      Og[(long)(8 + c) * L.plane + c0] = by + 0.5 * dt * (double)gty;
-    } else {
-      Wnew[c] = Ag[(long)c * L.plane + c0] + dt * dt / 3.0 * (double)Lt;
-      Og[(long)(4 + c) * L.plane + c0] = Bg[(long)c * L.plane + c0] + dt * (double)gtx;
-      Og[(long)(8 + c) * L.plane + c0] = Bg[(long)(4 + c) * L.plane + c0] + dt * (double)gty;
-    }
+    o.gtx[c] = (PX[(PO_WLT + c) * pp + x0] - PX[(PO_WRT + c) * pp + xm1]) * ihx;
+    o.gty[c] = (PY[(PO_WLT + c) * pp + y0] - PY[(PO_WRT + c) * pp + ym1]) * ihy;
   }
-  (void)Sg;
-  if (mode == UPD_OPERATOR) return;
-  double* Og = a.Sout + (long)g * NFLD * L.plane;
+}
+
+// float-float (double-word) accumulation for the mixed path: Knuth's TwoSum
+// gives s + e = a + b exactly; Dekker's FastTwoSum renormalises hi + lo
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float v = s - a;
+  e = (a - (s - v)) + (b - v);
+}
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float b) {
+  float s, e;
+  two_sum(hi, b, s, e);
+  e += lo;
+  hi = s + e;
+  lo = e - (hi - s);
+}
+
+template <class R>
+__global__ void __launch_bounds__(128) update_kernel(KArgs<R> a, int mode) {
+  const int g = blockIdx.z;
+  const Layout& L = a.L;
+  const int nxg = g == 0 ? L.nx : L.nxd, nyg = g == 0 ? L.ny : L.nyd;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= nxg || j >= nyg) return;
+  NodeOp<R> o;
+  node_operator(a, g, i, j, mode != UPD_STAGE2, o);
+  const long c0 = cell(L, i, j);
+  if (mode == UPD_OPERATOR) {
+    const long NN = (long)nxg * nyg, oi = (long)j * nxg + i;
+    double* const* op = a.op + 4 * g;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      op[0][c * NN + oi] = (double)o.L[c];
+      op[1][c * NN + oi] = (double)o.Lt[c];
+      op[2][c * NN + oi] = (double)o.gbx[c];
+      op[2][(4 + c) * NN + oi] = (double)o.gby[c];
+      op[3][c * NN + oi] = (double)o.gtx[c];
+      op[3][(4 + c) * NN + oi] = (double)o.gty[c];
+    }
+    return;
+  }
   // dual nodes on a no-slip wall: velocity set to zero (internal energy kept),
   // and, as U = V = 0 along the whole wall, the momentum gradients along it too
-  if (g == 1) {
-    bool xwall = (a.bc[0] == 3 && i == 0) || (a.bc[1] == 3 && i == nxg - 1);
-    bool ywall = (a.bc[2] == 3 && j == 0) || (a.bc[3] == 3 && j == nyg - 1);
+  const bool xwall = g == 1 && ((a.bc[0] == 3 && i == 0) || (a.bc[1] == 3 && i == nxg - 1));
+  const bool ywall = g == 1 && ((a.bc[2] == 3 && j == 0) || (a.bc[3] == 3 && j == nyg - 1));
+  const long P = L.plane;
+
+  if constexpr (IsF32<R>::v) {
+    // mixed path: state and accumulators are float-float pairs; increments are
+    // formed in FP32 and added exactly (two_sum) to the pairs
+    const float dtr = a.gas.dt_r;
+    float Wh[4], Wl[4], Gh[8], Gl[8];
+    const float* Snh = a.Sn_hi + (long)g * NFLD * P;
+    const float* Snl = a.Sn_lo + (long)g * NFLD * P;
+    float* Ah = a.Acc_hi + (long)g * 4 * P;
+    float* Al = a.Acc_lo + (long)g * 4 * P;
+    float* Bh = a.Gb_hi + (long)g * 8 * P;
+    float* Bl = a.Gb_lo + (long)g * 8 * P;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if (mode == UPD_STAGE1) {
+        float wh = Snh[(long)c * P + c0], wl = Snl[(long)c * P + c0];
+        float sh = wh, sl = wl;
+        ff_add(sh, sl, 0.5f * dtr * o.L[c] + 0.125f * dtr * dtr * o.Lt[c]);
+        Wh[c] = sh;
+        Wl[c] = sl;
+        float ah = wh, al = wl;
+        ff_add(ah, al, dtr * o.L[c] + dtr * dtr * (1.0f / 6.0f) * o.Lt[c]);
+        Ah[(long)c * P + c0] = ah;
+        Al[(long)c * P + c0] = al;
+        for (int d = 0; d < 2; ++d) {
+          const int f = 4 + 4 * d + c;
+          float bh = a.grad_base ? Snh[(long)f * P + c0] : (d == 0 ? o.gbx[c] : o.gby[c]);
+          float bl = a.grad_base ? Snl[(long)f * P + c0] : 0.0f;
+          Bh[(long)(4 * d + c) * P + c0] = bh;
+          Bl[(long)(4 * d + c) * P + c0] = bl;
+          ff_add(bh, bl, 0.5f * dtr * (d == 0 ? o.gtx[c] : o.gty[c]));
+          Gh[4 * d + c] = bh;
+          Gl[4 * d + c] = bl;
+        }
+      } else {
+        float wh = Ah[(long)c * P + c0], wl = Al[(long)c * P + c0];
+        ff_add(wh, wl, dtr * dtr * (1.0f / 3.0f) * o.Lt[c]);
+        Wh[c] = wh;
+        Wl[c] = wl;
+        for (int d = 0; d < 2; ++d) {
+          float bh = Bh[(long)(4 * d + c) * P + c0], bl = Bl[(long)(4 * d + c) * P + c0];
+          ff_add(bh, bl, dtr * (d == 0 ? o.gtx[c] : o.gty[c]));
+          Gh[4 * d + c] = bh;
+          Gl[4 * d + c] = bl;
+        }
+      }
+    }
+    if (xwall || ywall) {
+      float ke = 0.5f * (Wh[1] * Wh[1] + Wh[2] * Wh[2]) / Wh[0];
+      Wh[1] = Wl[1] = Wh[2] = Wl[2] = 0.0f;
+      ff_add(Wh[3], Wl[3], -ke);
+    }
+    if (xwall) { Gh[5] = Gl[5] = Gh[6] = Gl[6] = 0.0f; }   // y-gradients of rho U, rho V
+    if (ywall) { Gh[1] = Gl[1] = Gh[2] = Gl[2] = 0.0f; }   // x-gradients of rho U, rho V
+    float* Oh = a.Out_hi + (long)g * NFLD * P;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) Oh[(long)c * P + c0] = Wh[c];
+#pragma unroll
+    for (int f = 0; f < 8; ++f) Oh[(long)(4 + f) * P + c0] = Gh[f];
+    if (a.Out_lo) {
+      float* Ol = a.Out_lo + (long)g * NFLD * P;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) Ol[(long)c * P + c0] = Wl[c];
+#pragma unroll
+      for (int f = 0; f < 8; ++f) Ol[(long)(4 + f) * P + c0] = Gl[f];
+    }
+    float pr = Wh[3] - 0.5f * (Wh[1] * Wh[1] + Wh[2] * Wh[2]) / Wh[0];
+    if (!(Wh[0] > 0.0f) || !(pr > 0.0f)) atomicOr(a.flag, 1);
+  } else {
+    // FP64 path
+    const double dt = a.dt;
+    const double* Sng = a.Sn + (long)g * NFLD * P;
+    double* Og = a.Sout + (long)g * NFLD * P;
+    double* Ag = a.Wacc + (long)g * 4 * P;
+    double* Bg = a.gB + (long)g * 8 * P;
+    double Wnew[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if (mode == UPD_STAGE1) {
+        double Wn = Sng[(long)c * P + c0];
+        double dL = (double)o.L[c], dLt = (double)o.Lt[c];
+        Wnew[c] = Wn + 0.5 * dt * dL + 0.125 * dt * dt * dLt;
+        Ag[(long)c * P + c0] = Wn + dt * dL + dt * dt / 6.0 * dLt;
+        double bx = a.grad_base ? Sng[(long)(4 + c) * P + c0] : (double)o.gbx[c];
+        double by = a.grad_base ? Sng[(long)(8 + c) * P + c0] : (double)o.gby[c];
+        Bg[(long)c * P + c0] = bx;
+        Bg[(long)(4 + c) * P + c0] = by;
+        Og[(long)(4 + c) * P + c0] = bx + 0.5 * dt * (double)o.gtx[c];
+        Og[(long)(8 + c) * P + c0] = by + 0.5 * dt * (double)o.gty[c];
+      } else {
+        Wnew[c] = Ag[(long)c * P + c0] + dt * dt / 3.0 * (double)o.Lt[c];
+        Og[(long)(4 + c) * P + c0] = Bg[(long)c * P + c0] + dt * (double)o.gtx[c];
+        Og[(long)(8 + c) * P + c0] = Bg[(long)(4 + c) * P + c0] + dt * (double)o.gty[c];
+      }
+    }
     if (xwall || ywall) {
       double ke = 0.5 * (Wnew[1] * Wnew[1] + Wnew[2] * Wnew[2]) / Wnew[0];
       Wnew[1] = 0.0;
       Wnew[2] = 0.0;
       Wnew[3] -= ke;
     }
-    if (xwall) { Og[(long)(8 + 1) * L.plane + c0] = 0.0; Og[(long)(8 + 2) * L.plane + c0] = 0.0; }
-    if (ywall) { Og[(long)(4 + 1) * L.plane + c0] = 0.0; Og[(long)(4 + 2) * L.plane + c0] = 0.0; }
-  }
+    if (xwall) { Og[(long)(8 + 1) * P + c0] = 0.0; Og[(long)(8 + 2) * P + c0] = 0.0; }
+    if (ywall) { Og[(long)(4 + 1) * P + c0] = 0.0; Og[(long)(4 + 2) * P + c0] = 0.0; }
 #pragma unroll
-  for (int c = 0; c < 4; ++c) Og[(long)c * L.plane + c0] = Wnew[c];
-  // positivity of density and pressure (no trap: a flag the host reads)
-  double p = Wnew[3] - 0.5 * (Wnew[1] * Wnew[1] + Wnew[2] * Wnew[2]) / Wnew[0];
-  if (!(Wnew[0] > 0.0) || !(p > 0.0)) atomicOr(a.flag, 1);
+    for (int c = 0; c < 4; ++c) Og[(long)c * P + c0] = Wnew[c];
+    // positivity of density and pressure (no trap: a flag the host reads)
+    double p = Wnew[3] - 0.5 * (Wnew[1] * Wnew[1] + Wnew[2] * Wnew[2]) / Wnew[0];
+    if (!(Wnew[0] > 0.0) || !(p > 0.0)) atomicOr(a.flag, 1);
+  }
 }
 
 // ---------------------------------------------------------------------------

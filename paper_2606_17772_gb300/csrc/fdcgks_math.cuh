@@ -35,6 +35,7 @@ FD_HD float s_min(float a, float b) { return fminf(a, b); }
 FD_HD double s_max(double a, double b) { return fmax(a, b); }
 FD_HD float s_max(float a, float b) { return fmaxf(a, b); }
 FD_HD double s_expm1(double x) { return expm1(x); }
+FD_HD float s_expm1(float x) { return expm1f(x); }
 
 // The FP64 part of the arithmetic (collision time and time coefficients) runs
 // in Wide<R>::T: double for both compute types; an instrumented scalar type
@@ -42,6 +43,33 @@ FD_HD double s_expm1(double x) { return expm1(x); }
 template <class R> struct Wide { typedef double T; };
 template <class R> FD_HD typename Wide<R>::T to_w(R x) { return (typename Wide<R>::T)x; }
 template <class R> FD_HD R from_w(typename Wide<R>::T x) { return (R)x; }
+
+// Division in the compute type: IEEE in FP64; in FP32 on the device the
+// fast division x * (1/y) with an approximate reciprocal (2 ulp), which is
+// below the FP32 path's own error.  Denominators here are bounded away from
+// 0 and from 2^126.
+FD_HD double s_div(double a, double b) { return a / b; }
+FD_HD float s_div(float a, float b) {
+#if defined(__CUDA_ARCH__)
+  return __fdividef(a, b);
+#else
+  return a / b;
+#endif
+}
+
+// erfc(x) given ex2 = exp(-x^2), which the caller has already computed.
+// FP64: the library function.  FP32: Abramowitz & Stegun, Handbook of
+// Mathematical Functions, Eq. 7.1.26 (Hastings' rational approximation of
+// erf, absolute error <= 1.5e-7), erfc(|x|) = t (a1 + t(a2 + ...)) exp(-x^2)
+// with t = 1/(1 + p |x|), and erfc(x) = 2 - erfc(-x) for x < 0.
+FD_HD double s_erfc_e(double x, double ex2) { (void)ex2; return erfc(x); }
+FD_HD float s_erfc_e(float x, float ex2) {
+  float ax = fabsf(x);
+  float t = s_div(1.0f, 1.0f + 0.3275911f * ax);
+  float poly = t * (0.254829592f + t * (-0.284496736f + t * (1.421413741f + t * (-1.453152027f + t * 1.061405429f))));
+  float r = poly * ex2;
+  return x >= 0.0f ? r : 2.0f - r;
+}
 
 // value at which tanh(z) rounds to exactly 1 in the compute type
 template <class R> struct TanhSat;
@@ -55,7 +83,7 @@ template <class R>
 struct GenoK {
   int linear;        // 1: chi = 1 everywhere (linear scheme)
   int r;             // exponent of GENO-IS-linear
-  R eps_a, eps_w, C, tanhC;
+  R eps_a, eps_w, C, tanhC, inv_tanhC;
   R d_iface[3];      // ideal weights of the interface sub-stencils (App. C1/C2 order)
   R d_node[3];       // ideal weights of the node sub-stencils (Sec. 3.2 order, central first)
 };
@@ -63,9 +91,17 @@ struct GenoK {
 template <class R>
 struct GasK {
   R K;               // internal degrees of freedom, (4 - 2 gamma)/(gamma - 1)
+  R gm1;             // gamma - 1 = 2/(K + 2)
+  R c4K;             // 4/(K + 2)
   R prfix;           // 1/Pr - 1 (heat-flux correction)
-  double mu, c1, c2, dt;
+  double mu, c1, c2, dt, inv_dt;
+  R mu_r, c1_r, c2_r, dt_r, inv_dt_r;   // the same in the compute type
 };
+
+// dt/tau above which the time coefficients show no cancellation and the FP32
+// path evaluates them in FP32 (e^{-dt/tau} < 0.02); at or below it they are
+// computed in FP64 with expm1
+const double TIME_COEF_FP32_RATIO = 4.0;
 
 template <class R> FD_HD R rpow(R x, int r) { return r == 3 ? x * x * x : x * x; }
 
@@ -74,29 +110,55 @@ template <class R> FD_HD R rpow(R x, int r) { return r == 3 ? x * x * x : x * x;
 // of a high-order value/derivative with ENO-weighted sub-stencil values and
 // derivatives (the same weights serve both).
 // ---------------------------------------------------------------------------
+template <class R> struct IsF32 { static constexpr bool v = false; };
+template <> struct IsF32<float> { static constexpr bool v = true; };
+
 template <class R>
 FD_HD R geno_chi(const GenoK<R>& g, R IS0, R IS1, R IS2) {
   if (g.linear) return R(1);
   R ISL = s_min(IS0, s_min(IS1, IS2));
   R ISH = s_max(IS0, s_max(IS1, IS2));
   R tau = s_abs(R(0.5) * (IS1 + IS2) - IS0);
-  R aH = R(1) + rpow(tau / (ISH + g.eps_a), g.r);
-  R aL = R(1) + rpow(tau / (ISL + g.eps_a), g.r);
-  R alpha = R(2) * aH / (aH + aL);
+  R alpha;
+  if (IsF32<R>::v) {
+    // FP32: quotient form (the product form could overflow for large IS)
+    R aH = R(1) + rpow(s_div(tau, ISH + g.eps_a), g.r);
+    R aL = R(1) + rpow(s_div(tau, ISL + g.eps_a), g.r);
+    alpha = s_div(R(2) * aH, aH + aL);
+  } else {
+    // alpha = 2 aH/(aH + aL), aH = 1 + (tau/h)^r, aL = 1 + (tau/l)^r, written
+    // over the common denominator h^r l^r; tanh(C alpha) rounds to 1 when
+    // C alpha > z_sat, which is tested before dividing
+    R hr = rpow(ISH + g.eps_a, g.r), lr = rpow(ISL + g.eps_a, g.r), tr = rpow(tau, g.r);
+    R num = R(2) * (hr + tr) * lr;
+    R den = (hr + tr) * lr + (lr + tr) * hr;
+    if (g.C * num > R(TanhSat<R>::z) * den) return g.inv_tanhC;
+    alpha = num / den;
+  }
   R z = g.C * alpha;
   // tanh(z) is exactly 1 in this precision above the saturation point
-  if (z > R(TanhSat<R>::z)) return R(1) / g.tanhC;
-  return s_tanh(z) / g.tanhC;
+  if (z > R(TanhSat<R>::z)) return g.inv_tanhC;
+  return s_tanh(z) * g.inv_tanhC;
 }
 
 template <class R>
 FD_HD void geno_weights(const GenoK<R>& g, const R d[3], R IS0, R IS1, R IS2, R w[3]) {
   R e0 = IS0 + g.eps_w, e1 = IS1 + g.eps_w, e2 = IS2 + g.eps_w;
-  R t0 = d[0] / (e0 * e0), t1 = d[1] / (e1 * e1), t2 = d[2] / (e2 * e2);
-  R inv = R(1) / (t0 + t1 + t2);
-  w[0] = t0 * inv;
-  w[1] = t1 * inv;
-  w[2] = t2 * inv;
+  R s0 = e0 * e0, s1 = e1 * e1, s2 = e2 * e2;
+  if (IsF32<R>::v) {
+    R t0 = s_div(d[0], s0), t1 = s_div(d[1], s1), t2 = s_div(d[2], s2);
+    R inv = s_div(R(1), t0 + t1 + t2);
+    w[0] = t0 * inv;
+    w[1] = t1 * inv;
+    w[2] = t2 * inv;
+  } else {
+    // d_k/s_k normalised = d_k P_k / sum_m d_m P_m with P_k the product of the other two s
+    R t0 = d[0] * s1 * s2, t1 = d[1] * s0 * s2, t2 = d[2] * s0 * s1;
+    R inv = R(1) / (t0 + t1 + t2);
+    w[0] = t0 * inv;
+    w[1] = t1 * inv;
+    w[2] = t2 * inv;
+  }
 }
 
 // left and right states at the interface between Q[1] and Q[2] of a 4-point
@@ -203,17 +265,23 @@ FD_HD R recon_node(const GenoK<R>& g, const R Q[3], const R Qx[3], R h, R ih) {
 template <class R>
 struct Maxw {
   R rho, U, V, lam;
+  R ir;    // 1/rho
+  R p;     // pressure rho/(2 lam)
+  R i2l;   // 1/(2 lam) = p/rho
 };
 
+// conservative W -> Maxwellian; rho E = rho (U^2 + V^2 + (K+2)/(2 lam))/2,
+// so p = (gamma - 1)(rho E - rho (U^2+V^2)/2) and lam = rho/(2 p)
 template <class R>
-FD_HD Maxw<R> maxw_from_W(const R W[4], R K) {
+FD_HD Maxw<R> maxw_from_W(const R W[4], R gm1) {
   Maxw<R> g;
   g.rho = W[0];
-  R ir = R(1) / W[0];
-  g.U = W[1] * ir;
-  g.V = W[2] * ir;
-  R eint = W[3] - R(0.5) * W[0] * (g.U * g.U + g.V * g.V);   // rho (K+2)/(4 lam)
-  g.lam = (K + R(2)) * W[0] / (R(4) * eint);
+  g.ir = s_div(R(1), W[0]);
+  g.U = W[1] * g.ir;
+  g.V = W[2] * g.ir;
+  g.p = gm1 * (W[3] - R(0.5) * W[0] * (g.U * g.U + g.V * g.V));
+  g.i2l = g.p * g.ir;
+  g.lam = s_div(R(0.5), g.i2l);
   return g;
 }
 
@@ -234,7 +302,7 @@ FD_HD void recur(R m, R i2l, R* t) {
 // full-space tables of g
 template <class R>
 FD_HD void tab_full(const Maxw<R>& g, R K, Tab<R>& T) {
-  R i2l = R(0.5) / g.lam;
+  R i2l = g.i2l;
   T.u[0] = R(1); T.u[1] = g.U;
   T.v[0] = R(1); T.v[1] = g.V;
   recur(g.U, i2l, T.u);
@@ -247,12 +315,13 @@ FD_HD void tab_full(const Maxw<R>& g, R K, Tab<R>& T) {
 // u-half-space tables (sign +1: u > 0, -1: u < 0), sharing v and xi with T
 template <class R>
 FD_HD void tab_half(const Maxw<R>& g, int sign, const Tab<R>& full, Tab<R>& H) {
-  R i2l = R(0.5) / g.lam;
+  R i2l = g.i2l;
   R sl = s_sqrt(g.lam);
+  R isl = sl * (R(2) * i2l);                   // 1/sqrt(lam)
   R e = s_exp(-g.lam * g.U * g.U);
   const R isqpi = R(0.56418958354775628695);   // 1/sqrt(pi)
-  H.u[0] = R(0.5) * s_erfc(-R(sign) * sl * g.U);
-  H.u[1] = g.U * H.u[0] + R(sign) * R(0.5) * e * isqpi / sl;
+  H.u[0] = R(0.5) * s_erfc_e(-R(sign) * sl * g.U, e);
+  H.u[1] = g.U * H.u[0] + R(sign) * R(0.5) * e * isqpi * isl;
   recur(g.U, i2l, H.u);
 #pragma unroll
   for (int n = 0; n < NT; ++n) H.v[n] = full.v[n];
@@ -288,12 +357,12 @@ FD_HD void mslope(const Tab<R>& T, const R s[4], R o[4]) {
 
 // slope s with <s psi> = r (r = dW / rho), closed form of the 4x4 moment system
 template <class R>
-FD_HD void slope_solve(const Maxw<R>& g, R K, const R r[4], R s[4]) {
-  R q = g.U * g.U + g.V * g.V + (K + R(2)) * R(0.5) / g.lam;
+FD_HD void slope_solve(const Maxw<R>& g, R K, R c4K, const R r[4], R s[4]) {
+  R q = g.U * g.U + g.V * g.V + (K + R(2)) * g.i2l;
   R Ah = r[1] - g.U * r[0];
   R Ch = r[2] - g.V * r[0];
   R B = R(2) * r[3] - q * r[0];
-  s[3] = R(4) * g.lam * g.lam / (K + R(2)) * (B - R(2) * g.U * Ah - R(2) * g.V * Ch);
+  s[3] = c4K * g.lam * g.lam * (B - R(2) * g.U * Ah - R(2) * g.V * Ch);
   s[2] = R(2) * g.lam * Ch - g.V * s[3];
   s[1] = R(2) * g.lam * Ah - g.U * s[3];
   s[0] = r[0] - g.U * s[1] - g.V * s[2] - R(0.5) * s[3] * q;
@@ -324,18 +393,18 @@ struct TimeCoef {
   TW E, e1;   // exp(-dt/tau), 1 - exp(-dt/tau)
 };
 
+// integrals over [0, d] of the equilibrium coefficients c1..c3 of f(0,t);
+// the initial-data coefficients follow from c1 + c4 = 1, c2 + c5 = -tau,
+// c3 + c6 = t - tau
 template <class TW>
-FD_HD void time_integrals_d(TW tau, TW d, TW E, TW e1, TW C[6]) {
+FD_HD void time_integrals_d(TW tau, TW d, TW E, TW e1, TW C[3]) {
   C[0] = d - tau * e1;
   C[1] = -tau * d * (TW(1) + E) + TW(2) * tau * tau * e1;
   C[2] = TW(0.5) * d * d - tau * d + tau * tau * e1;
-  C[3] = tau * e1;
-  C[4] = tau * d * E - TW(2) * tau * tau * e1;
-  C[5] = -tau * tau * e1;
 }
 
 template <class TW>
-FD_HD TimeCoef<TW> time_coef(TW tau, TW dt) {
+FD_HD TimeCoef<TW> time_coef(TW tau, TW dt, TW inv_dt) {
   TimeCoef<TW> t;
   // one transcendental: em = exp(-dt/(2 tau)) - 1, then
   // exp(-dt/tau) - 1 = em (em + 2) without cancellation
@@ -343,14 +412,23 @@ FD_HD TimeCoef<TW> time_coef(TW tau, TW dt) {
   TW Eh = TW(1) + em, e1h = -em;
   t.E = Eh * Eh;
   t.e1 = -em * (em + TW(2));
-  TW Ch[6], Cf[6];
+  TW Ch[3], Cf[3];
   time_integrals_d(tau, TW(0.5) * dt, Eh, e1h, Ch);
   time_integrals_d(tau, dt, t.E, t.e1, Cf);
-  TW idt = TW(1) / dt;
-  for (int k = 0; k < 6; ++k) {
-    t.cn[k] = (TW(4) * Ch[k] - Cf[k]) * idt;
-    t.ct[k] = TW(4) * (Cf[k] - TW(2) * Ch[k]) * idt * idt;
+  for (int k = 0; k < 3; ++k) {
+    // linear-in-time fit of App. A1: f^n = (4 fbar(dt/2) - fbar(dt))/dt,
+    // f_t^n = 4 (fbar(dt) - 2 fbar(dt/2))/dt^2
+    t.cn[k] = (TW(4) * Ch[k] - Cf[k]) * inv_dt;
+    t.ct[k] = TW(4) * (Cf[k] - TW(2) * Ch[k]) * inv_dt * inv_dt;
   }
+  // fits of c4..c6: the fit of (c1 + c4) = 1 is 1 (value) and 0 (slope),
+  // of (c2 + c5) = -tau is -tau and 0, of (c3 + c6) = t - tau is -tau and 1
+  t.cn[3] = TW(1) - t.cn[0];
+  t.ct[3] = -t.ct[0];
+  t.cn[4] = -tau - t.cn[1];
+  t.ct[4] = -t.ct[1];
+  t.cn[5] = -tau - t.cn[2];
+  t.ct[5] = TW(1) - t.ct[2];
   return t;
 }
 
@@ -369,7 +447,7 @@ template <class R>
 FD_HD void iface_solve_x(const GasK<R>& gas, const R Wl[4], const R Wr[4], const R Wln[4], const R Wrn[4],
                          const R Wt[4], bool want_n, IfaceOut<R>& o) {
   const R K = gas.K;
-  Maxw<R> gl = maxw_from_W(Wl, K), gr = maxw_from_W(Wr, K);
+  Maxw<R> gl = maxw_from_W(Wl, gas.gm1), gr = maxw_from_W(Wr, gas.gm1);
   Tab<R> Tl, Tr, Tlp, Trn;
   tab_full(gl, K, Tl);
   tab_full(gr, K, Tr);
@@ -382,31 +460,31 @@ FD_HD void iface_solve_x(const GasK<R>& gas, const R Wl[4], const R Wr[4], const
   mpsi<0, 0, 0>(Trn, t4);
 #pragma unroll
   for (int k = 0; k < 4; ++k) W0[k] = gl.rho * W0[k] + gr.rho * t4[k];
-  Maxw<R> g0 = maxw_from_W(W0, K);
+  Maxw<R> g0 = maxw_from_W(W0, gas.gm1);
   Tab<R> T0;
   tab_full(g0, K, T0);
 
   // slopes (x: normal, y: tangential)
   R al[4], bl[4], ar[4], br[4], a0[4], b0[4], r[4];
-  R irl = R(1) / gl.rho, irr = R(1) / gr.rho, ir0 = R(1) / g0.rho;
+  R irl = gl.ir, irr = gr.ir, ir0 = g0.ir;
 #pragma unroll
   for (int k = 0; k < 4; ++k) r[k] = Wln[k] * irl;
-  slope_solve(gl, K, r, al);
+  slope_solve(gl, K, gas.c4K, r, al);
 #pragma unroll
   for (int k = 0; k < 4; ++k) r[k] = Wt[k] * irl;
-  slope_solve(gl, K, r, bl);
+  slope_solve(gl, K, gas.c4K, r, bl);
 #pragma unroll
   for (int k = 0; k < 4; ++k) r[k] = Wrn[k] * irr;
-  slope_solve(gr, K, r, ar);
+  slope_solve(gr, K, gas.c4K, r, ar);
 #pragma unroll
   for (int k = 0; k < 4; ++k) r[k] = Wt[k] * irr;
-  slope_solve(gr, K, r, br);
+  slope_solve(gr, K, gas.c4K, r, br);
 #pragma unroll
   for (int k = 0; k < 4; ++k) r[k] = R(0.5) * (Wln[k] + Wrn[k]) * ir0;
-  slope_solve(g0, K, r, a0);
+  slope_solve(g0, K, gas.c4K, r, a0);
 #pragma unroll
   for (int k = 0; k < 4; ++k) r[k] = Wt[k] * ir0;
-  slope_solve(g0, K, r, b0);
+  slope_solve(g0, K, gas.c4K, r, b0);
 
   // time slopes from compatibility <(a u + b v + A) psi> = 0
   R Al[4], Ar[4], A0[4], rl[4], rr[4], r0[4], x1[4], x2[4];
@@ -414,28 +492,41 @@ FD_HD void iface_solve_x(const GasK<R>& gas, const R Wl[4], const R Wr[4], const
   mslope<0, 1>(Tl, bl, x2);
 #pragma unroll
   for (int k = 0; k < 4; ++k) rl[k] = -(x1[k] + x2[k]);
-  slope_solve(gl, K, rl, Al);
+  slope_solve(gl, K, gas.c4K, rl, Al);
   mslope<1, 0>(Tr, ar, x1);
   mslope<0, 1>(Tr, br, x2);
 #pragma unroll
   for (int k = 0; k < 4; ++k) rr[k] = -(x1[k] + x2[k]);
-  slope_solve(gr, K, rr, Ar);
+  slope_solve(gr, K, gas.c4K, rr, Ar);
   mslope<1, 0>(T0, a0, x1);
   mslope<0, 1>(T0, b0, x2);
 #pragma unroll
   for (int k = 0; k < 4; ++k) r0[k] = -(x1[k] + x2[k]);
-  slope_solve(g0, K, r0, A0);
+  slope_solve(g0, K, gas.c4K, r0, A0);
 
-  // collision time and time coefficients (FP64)
+  // collision time and time coefficients: FP64 with expm1 where they cancel
+  // (dt/tau small); in the FP32 path, FP32 where dt/tau > 4
   typedef typename Wide<R>::T TW;
-  TW pl = to_w(gl.rho / (R(2) * gl.lam)), pr = to_w(gr.rho / (R(2) * gr.lam));
-  TW p0 = to_w(g0.rho / (R(2) * g0.lam));
-  TW dtw = TW(gas.dt);
-  TW tau = TW(gas.c1) * dtw + TW(gas.mu) / p0 + TW(gas.c2) * dtw * s_abs(pl - pr) / (pl + pr);
-  TimeCoef<TW> tc = time_coef(tau, dtw);
-  R cn[6], ct[6];
+  R cn[6], ct[6], E, e1;
+  R ip0r = R(2) * g0.lam * g0.ir;              // 1/p0
+  R taur = gas.c1_r * gas.dt_r + gas.mu_r * ip0r + gas.c2_r * gas.dt_r * s_div(s_abs(gl.p - gr.p), gl.p + gr.p);
+  if (IsF32<R>::v && gas.dt_r > R(TIME_COEF_FP32_RATIO) * taur) {
+    TimeCoef<R> tc = time_coef(taur, gas.dt_r, gas.inv_dt_r);
 #pragma unroll
-  for (int k = 0; k < 6; ++k) { cn[k] = from_w<R>(tc.cn[k]); ct[k] = from_w<R>(tc.ct[k]); }
+    for (int k = 0; k < 6; ++k) { cn[k] = tc.cn[k]; ct[k] = tc.ct[k]; }
+    E = tc.E;
+    e1 = tc.e1;
+  } else {
+    TW pl = to_w(gl.p), pr = to_w(gr.p);
+    TW ip0 = to_w(ip0r);
+    TW dtw = TW(gas.dt);
+    TW tau = TW(gas.c1) * dtw + TW(gas.mu) * ip0 + TW(gas.c2) * dtw * s_abs(pl - pr) / (pl + pr);
+    TimeCoef<TW> tc = time_coef(tau, dtw, TW(gas.inv_dt));
+#pragma unroll
+    for (int k = 0; k < 6; ++k) { cn[k] = from_w<R>(tc.cn[k]); ct[k] = from_w<R>(tc.ct[k]); }
+    E = from_w<R>(tc.E);
+    e1 = from_w<R>(tc.e1);
+  }
 
   // moment vectors of the six basis terms, flux (u psi) and W (psi)
   R F[4], Ftt[4], We[4], Wet[4];
@@ -463,11 +554,10 @@ FD_HD void iface_solve_x(const GasK<R>& gas, const R Wl[4], const R Wr[4], const
 #pragma unroll
   for (int k = 0; k < 4; ++k) { mf[k] = g0.rho * (x1[k] + x2[k]); mw[k] = -g0.rho * r0[k]; }
   acc(1, mf, mw);
-  // 3: A0 g0
+  // 3: A0 g0; int psi A0 g0 = rho0 r0 by construction of A0 (compatibility)
   mslope<1, 0>(T0, A0, x1);
-  mslope<0, 0>(T0, A0, x2);
 #pragma unroll
-  for (int k = 0; k < 4; ++k) { mf[k] = g0.rho * x1[k]; mw[k] = g0.rho * x2[k]; }
+  for (int k = 0; k < 4; ++k) { mf[k] = g0.rho * x1[k]; mw[k] = g0.rho * r0[k]; }
   acc(2, mf, mw);
   // 4: gl H(u) + gr (1 - H(u))
   mpsi<1, 0, 0>(Tlp, x1);
@@ -504,7 +594,6 @@ FD_HD void iface_solve_x(const GasK<R>& gas, const R Wl[4], const R Wr[4], const
 
   // interface flow variables, Eq. (eq:W-model) with tau_0 = tau; the one-sided
   // time derivatives are W_t = -rho <(a u + b v) psi> = rho * (compatibility rhs)
-  R E = from_w<R>(tc.E), e1 = from_w<R>(tc.e1);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     o.Ft[k] = Ftt[k];
@@ -545,26 +634,25 @@ template <class R>
 FD_HD void nodal_flux(const GasK<R>& gas, const R W[4], const R Wx[4], const R Wy[4], R F[4], R G[4], R Ft[4],
                       R Gt[4]) {
   const R K = gas.K;
-  Maxw<R> g = maxw_from_W(W, K);
+  Maxw<R> g = maxw_from_W(W, gas.gm1);
   Tab<R> T;
   tab_full(g, K, T);
-  R a[4], b[4], A[4], r[4], ir = R(1) / g.rho;
+  R a[4], b[4], A[4], r[4], ir = g.ir;
 #pragma unroll
   for (int k = 0; k < 4; ++k) r[k] = Wx[k] * ir;
-  slope_solve(g, K, r, a);
+  slope_solve(g, K, gas.c4K, r, a);
 #pragma unroll
   for (int k = 0; k < 4; ++k) r[k] = Wy[k] * ir;
-  slope_solve(g, K, r, b);
+  slope_solve(g, K, gas.c4K, r, b);
   R x1[4], x2[4], Wt[4];
   mslope<1, 0>(T, a, x1);
   mslope<0, 1>(T, b, x2);
 #pragma unroll
   for (int k = 0; k < 4; ++k) r[k] = -(x1[k] + x2[k]);
-  slope_solve(g, K, r, A);
+  slope_solve(g, K, gas.c4K, r, A);
 #pragma unroll
   for (int k = 0; k < 4; ++k) Wt[k] = g.rho * r[k];   // int psi A g
-  typedef typename Wide<R>::T TW;
-  R tau = from_w<R>(TW(gas.c1) * TW(gas.dt) + TW(gas.mu) / to_w(g.rho / (R(2) * g.lam)));
+  R tau = gas.c1_r * gas.dt_r + gas.mu_r * (R(2) * g.lam * g.ir);   // c1 dt + mu/p
 
   R e0[4], ea[4], eb[4], eA[4];
   // x-flux

@@ -132,12 +132,24 @@ template <int P> CN<P> s_abs(CN<P> x) {
 }
 template <int P> CN<P> s_min(CN<P> a, CN<P> b) { return a.v < b.v ? a : b; }
 template <int P> CN<P> s_max(CN<P> a, CN<P> b) { return a.v > b.v ? a : b; }
+template <int P> CN<P> s_div(CN<P> a, CN<P> b) { return a / b; }
+// erfc given exp(-x^2): FP64 calls erfc, FP32 evaluates the rational approximation
+inline CD s_erfc_e(CD x, CD e) { (void)e; return s_erfc(x); }
+inline CF s_erfc_e(CF x, CF ex2) {
+  CF ax = s_abs(x);
+  CF t = CF(1.0f) / (CF(1.0f) + CF(0.3275911f) * ax);
+  CF poly = t * (CF(0.254829592f) + t * (CF(-0.284496736f) + t * (CF(1.421413741f) +
+            t * (CF(-1.453152027f) + t * CF(1.061405429f)))));
+  CF r = poly * ex2;
+  return x.v >= 0.0f ? r : CF(2.0f) - r;
+}
 }  // namespace fdk
 
 #include "fdcgks_math.cuh"
 
 namespace fdk {
 template <> struct TanhSat<CD> { static constexpr double z = 19.5; };
+template <> struct IsF32<CF> { static constexpr bool v = true; };
 template <> struct TanhSat<CF> { static constexpr float z = 9.5f; };
 template <> struct Wide<CD> { typedef CD T; };
 template <> struct Wide<CF> { typedef CD T; };
@@ -163,6 +175,7 @@ GenoK<R> geno_of(int variant) {
   g.linear = variant == 2;
   g.C = R(20.0);
   g.tanhC = R(std::tanh(20.0));
+  g.inv_tanhC = R(1.0 / std::tanh(20.0));
   g.eps_w = R(1e-6);
   if (variant == 1) {
     g.r = 3; g.eps_a = R(1e-15);
@@ -178,9 +191,13 @@ GenoK<R> geno_of(int variant) {
 template <class R>
 GasK<R> gas_of(const double* gp) {   // gamma, mu, Pr, c1, c2, dt
   GasK<R> g;
-  g.K = R((4.0 - 2.0 * gp[0]) / (gp[0] - 1.0));
+  const double K = (4.0 - 2.0 * gp[0]) / (gp[0] - 1.0);
+  g.K = R(K);
+  g.gm1 = R(gp[0] - 1.0);
+  g.c4K = R(4.0 / (K + 2.0));
   g.prfix = R(1.0 / gp[2] - 1.0);
-  g.mu = gp[1]; g.c1 = gp[3]; g.c2 = gp[4]; g.dt = gp[5];
+  g.mu = gp[1]; g.c1 = gp[3]; g.c2 = gp[4]; g.dt = gp[5]; g.inv_dt = 1.0 / gp[5];
+  g.mu_r = R(gp[1]); g.c1_r = R(gp[3]); g.c2_r = R(gp[4]); g.dt_r = R(gp[5]); g.inv_dt_r = R(1.0 / gp[5]);
   return g;
 }
 

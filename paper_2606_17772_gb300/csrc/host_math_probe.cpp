@@ -19,6 +19,7 @@ GenoK<R> geno_of(int variant) {
   g.linear = variant == 2;
   g.C = (R)20.0;
   g.tanhC = (R)std::tanh(20.0);
+  g.inv_tanhC = (R)(1.0 / std::tanh(20.0));
   g.eps_w = (R)1e-6;
   if (variant == 1) {
     g.r = 3; g.eps_a = (R)1e-15;
@@ -34,9 +35,13 @@ GenoK<R> geno_of(int variant) {
 template <class R>
 GasK<R> gas_of(double gamma, double mu, double Pr, double c1, double c2, double dt) {
   GasK<R> g;
-  g.K = (R)((4.0 - 2.0 * gamma) / (gamma - 1.0));
+  const double K = (4.0 - 2.0 * gamma) / (gamma - 1.0);
+  g.K = (R)K;
+  g.gm1 = (R)(gamma - 1.0);
+  g.c4K = (R)(4.0 / (K + 2.0));
   g.prfix = (R)(1.0 / Pr - 1.0);
-  g.mu = mu; g.c1 = c1; g.c2 = c2; g.dt = dt;
+  g.mu = mu; g.c1 = c1; g.c2 = c2; g.dt = dt; g.inv_dt = 1.0 / dt;
+  g.mu_r = (R)mu; g.c1_r = (R)c1; g.c2_r = (R)c2; g.dt_r = (R)dt; g.inv_dt_r = (R)(1.0 / dt);
   return g;
 }
 
@@ -76,6 +81,15 @@ void probe_nodal(double gamma, double mu, double Pr, double c1, double dt, int n
       out[t * 16 + k] = F[k]; out[t * 16 + 4 + k] = G[k];
       out[t * 16 + 8 + k] = Ft[k]; out[t * 16 + 12 + k] = Gt[k];
     }
+  }
+}
+
+// FP32 erfc of the mixed path (host build of the same source), for checks
+// against the approximation's published error bound
+void probe_erfc32(int n, const double* x, double* out) {
+  for (int t = 0; t < n; ++t) {
+    float xf = (float)x[t];
+    out[t] = (double)s_erfc_e(xf, std::exp(-xf * xf));
   }
 }
 

@@ -142,8 +142,16 @@ def step_counts(case, state, dt, precision=0, nsample=4000, seed=0):
     # (F, F_t in x and y at both faces), 18 operator/gradient flops in the compute
     # type and 19 FP64 flops of the S2O4 combination; stage 2 evaluates 4 fluxes,
     # 9 + 8 flops; 6 FP64 flops of the positivity check per node
-    upd1 = comb((cflux, 32), (glue(4 * 18, 4 * 19 + 6), 1))
-    upd2 = comb((cflux, 16), (glue(4 * 9, 4 * 8 + 6), 1))
+    if precision == 1:
+        # mixed path: the S2O4 increments are formed in FP32 (stage 1: 5 + 5 per
+        # component for W* and W_acc, 2 x 2 for the gradients; stage 2: 3 + 2 x 2)
+        # and added to float-float pairs (8 flops per addition: 4 per component at
+        # stage 1, 3 at stage 2); positivity check 6 flops per node, all FP32
+        upd1 = comb((cflux, 32), (glue(4 * (18 + 14 + 32) + 6, 0), 1))
+        upd2 = comb((cflux, 16), (glue(4 * (9 + 7 + 24) + 6, 0), 1))
+    else:
+        upd1 = comb((cflux, 32), (glue(4 * 18, 4 * 19 + 6), 1))
+        upd2 = comb((cflux, 16), (glue(4 * 9, 4 * 8 + 6), 1))
     # per node pair per step: 2 points + 2 nodes + 2 updates in each stage
     pair = comb((point1, 2), (point2, 2), (node, 4), (upd1, 2), (upd2, 2))
     per_node = {p: {k: pair[p][k] / 2.0 for k in KINDS} for p in ("fp64", "fp32")}

@@ -277,3 +277,35 @@ def test_full_size_vortex_sampled_against_oracle(precision):
     for g in (0, 2):
         tot0, tot1 = S[g].sum(axis=(1, 2)), got[g].sum(axis=(1, 2))
         assert np.all(np.abs(tot1 - tot0) <= 1e-11 * np.abs(S[g]).sum(axis=(1, 2)))
+
+
+# ---------------------------------------------------------------------------
+# mixed precision: FP32 reconstruction/flux arithmetic, FP64 state and time
+# coefficients; bounded error against the FP64 oracle
+# ---------------------------------------------------------------------------
+
+def test_mixed_interface_solve_within_fp32_bounds():
+    rng = np.random.default_rng(77)
+    n, dt = 200, 0.004
+    Wl = _rand_states(rng, n)
+    Wr = Wl * (1 + 0.02 * rng.normal(size=(n, 4)))
+    inp = np.concatenate([Wl, Wr] + [0.3 * rng.normal(size=(n, 4)) for _ in range(3)], 1)
+    gas = dict(mu=0.0, Pr=1.0, tau_c1=0.05, tau_c2=1.0)
+    prm = fdcgks.make_params(8, 8, gamma=GAMMA, precision=fdcgks.MIXED, **gas)
+    out = fdcgks.iface_batch(prm, 0, dt, torch.from_numpy(np.ascontiguousarray(inp)).cuda()).cpu().numpy()
+    op = oracle.make_params(8, 8, gamma=GAMMA, **gas)
+    ref = np.array([np.concatenate([o[k] for k in ("Fh", "Fht", "Whl", "Whr", "Whlt", "Whrt")]) for o in
+                    (oracle.iface_solve(op, 0, dt, *[inp[t, 4 * k:4 * k + 4] for k in range(5)]) for t in range(n))])
+    bounds = [2e-6, 1e-4, 2e-6, 2e-6, 1e-4, 1e-4]   # values vs time derivatives (fitted, divided by dt^2)
+    for k in range(6):
+        assert rel_err(out[:, 4 * k:4 * k + 4], ref[:, 4 * k:4 * k + 4]) < bounds[k], k
+
+
+@pytest.mark.parametrize("nsteps,bound_w,bound_g", [(1, 1e-6, 2e-5), (20, 1e-5, 2e-4)])
+def test_mixed_steps_within_stated_error(nsteps, bound_w, bound_g):
+    case = inputs.vortex(40)
+    dt = 0.02
+    errs = field_errors(gpu_run(case, dt, nsteps, fdcgks.MIXED), oracle_run(case, dt, nsteps))
+    w = max(v for k, v in errs.items() if k.startswith("W"))
+    g = max(v for k, v in errs.items() if k.startswith("G"))
+    assert w < bound_w and g < bound_g, errs
