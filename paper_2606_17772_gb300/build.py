@@ -35,16 +35,22 @@ def up_to_date():
     return all(os.path.getmtime(p) <= t for p in _inputs())
 
 
-def build(force=False, verbose=False):
-    """Compile the library if needed; returns the path of the .so."""
-    if not force and up_to_date():
+def build(force=False, verbose=False, out_dir=None, defines=()):
+    """Compile the library if needed; returns the path of the .so.
+
+    out_dir / defines build a variant elsewhere (tuning of the -D knobs
+    documented in csrc/fdcgks_kernels.cuh); the default build uses neither.
+    """
+    out = out_dir or OUT
+    lib = os.path.join(out, "libfdcgks.so")
+    if not force and out_dir is None and up_to_date():
         return LIB
-    os.makedirs(OUT, exist_ok=True)
+    os.makedirs(out, exist_ok=True)
     nvcc = _nvcc()
 
     def compile_one(src):
-        obj = os.path.join(OUT, os.path.splitext(src)[0] + ".o")
-        cmd = [nvcc] + NVCC_FLAGS + ["-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(out, os.path.splitext(src)[0] + ".o")
+        cmd = [nvcc] + NVCC_FLAGS + ["-D" + d for d in defines] + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, r.stdout, r.stderr))
@@ -54,13 +60,13 @@ def build(force=False, verbose=False):
 
     with concurrent.futures.ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + ".tmp.%d" % os.getpid()
+    tmp = lib + ".tmp.%d" % os.getpid()
     cmd = [nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp] + objs + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

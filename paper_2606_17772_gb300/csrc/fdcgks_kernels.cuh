@@ -7,14 +7,61 @@
 
 #include "fdcgks_internal.cuh"
 
+// Tuning knobs of the interface-point kernel (defaults are the tuned values):
+// FDK_POINT_MINB   minimum resident blocks per SM in the launch bounds
+//                  (caps registers per thread), per compute type
+// FDK_UPDATE_MINB_F32, FDK_NODAL_MINB_F32  the same for the FP32 update and
+//                  nodal kernels (the FP64 kernels are FP64-pipe bound and
+//                  are left uncapped)
+// FDK_SOLVE_NOINLINE  1: the kinetic solve is an out-of-line function called
+//                  twice (one code copy per kernel), 0: inlined twice
+#ifndef FDK_POINT_MINB_F64
+#define FDK_POINT_MINB_F64 1
+#endif
+#ifndef FDK_POINT_MINB_F32
+#define FDK_POINT_MINB_F32 4
+#endif
+#ifndef FDK_UPDATE_MINB_F32
+#define FDK_UPDATE_MINB_F32 6
+#endif
+#ifndef FDK_NODAL_MINB_F32
+#define FDK_NODAL_MINB_F32 8
+#endif
+#ifndef FDK_SOLVE_NOINLINE_F64
+#define FDK_SOLVE_NOINLINE_F64 0
+#endif
+#ifndef FDK_SOLVE_NOINLINE_F32
+#define FDK_SOLVE_NOINLINE_F32 0
+#endif
+
 namespace fdk {
+
+template <class R> struct PointTune;
+template <> struct PointTune<double> {
+  static constexpr int minb = FDK_POINT_MINB_F64;
+  static constexpr int update_minb = 1;
+  static constexpr int nodal_minb = 1;
+  static constexpr bool noinline = FDK_SOLVE_NOINLINE_F64;
+};
+template <> struct PointTune<float> {
+  static constexpr int minb = FDK_POINT_MINB_F32;
+  static constexpr int update_minb = FDK_UPDATE_MINB_F32;
+  static constexpr int nodal_minb = FDK_NODAL_MINB_F32;
+  static constexpr bool noinline = FDK_SOLVE_NOINLINE_F32;
+};
+
+template <class R>
+__device__ __noinline__ void iface_solve_call(const GasK<R>& gas, int normal, const R* Wl, const R* Wr, const R* Wln,
+                                             const R* Wrn, const R* Wt, bool want_n, IfaceOut<R>& o) {
+  iface_solve(gas, normal, Wl, Wr, Wln, Wrn, Wt, want_n, o);
+}
 
 // ---------------------------------------------------------------------------
 // nodal reconstruction and flux (Sec. 4 item 2; Sec. 2.1 nodal fluxes)
 // one thread per node, nodes i in [-1, n_x], j in [-1, n_y] of grid blockIdx.z
 // ---------------------------------------------------------------------------
 template <class R>
-__global__ void __launch_bounds__(128) nodal_kernel(KArgs<R> a) {
+__global__ void __launch_bounds__(128, PointTune<R>::nodal_minb) nodal_kernel(KArgs<R> a) {
   const int g = blockIdx.z;
   const Layout& L = a.L;
   const int nxg = g == 0 ? L.nx : L.nxd, nyg = g == 0 ? L.ny : L.nyd;
@@ -73,7 +120,7 @@ FD_HD void recon_line(const GenoK<R>& geno, const R* S, long plane, long c0, lon
 // TYPE 1 = point B (i, j+1/2): primary y-interface, dual x-interface of dual row j+1
 // ---------------------------------------------------------------------------
 template <class R, int TYPE>
-__global__ void __launch_bounds__(128) point_kernel(KArgs<R> a) {
+__global__ void __launch_bounds__(128, PointTune<R>::minb) point_kernel(KArgs<R> a) {
   const Layout& L = a.L;
   const int i = blockIdx.x * blockDim.x + threadIdx.x - 2;
   const int j = blockIdx.y * blockDim.y + threadIdx.y - 2;
@@ -103,8 +150,13 @@ __global__ void __launch_bounds__(128) point_kernel(KArgs<R> a) {
   }
   const bool wn = a.want_n != 0;
   IfaceOut<R> o0, o1;
-  iface_solve(a.gas, n0, l0v, r0v, l0d, r0d, t0, wn, o0);
-  iface_solve(a.gas, 1 - n0, l1v, r1v, l1d, r1d, t1, wn, o1);
+  if (PointTune<R>::noinline) {
+    iface_solve_call(a.gas, n0, l0v, r0v, l0d, r0d, t0, wn, o0);
+    iface_solve_call(a.gas, 1 - n0, l1v, r1v, l1d, r1d, t1, wn, o1);
+  } else {
+    iface_solve(a.gas, n0, l0v, r0v, l0d, r0d, t0, wn, o0);
+    iface_solve(a.gas, 1 - n0, l1v, r1v, l1d, r1d, t1, wn, o1);
+  }
 
   R* P = (TYPE == 0 ? a.PA : a.PB) + pcell(L, i, j);
   const long pp = L.pplane;
@@ -213,7 +265,7 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float b) {
 }
 
 template <class R>
-__global__ void __launch_bounds__(128) update_kernel(KArgs<R> a, int mode) {
+__global__ void __launch_bounds__(128, PointTune<R>::update_minb) update_kernel(KArgs<R> a, int mode) {
   const int g = blockIdx.z;
   const Layout& L = a.L;
   const int nxg = g == 0 ? L.nx : L.nxd, nyg = g == 0 ? L.ny : L.nyd;

@@ -607,23 +607,27 @@ FD_HD void iface_solve_x(const GasK<R>& gas, const R Wl[4], const R Wr[4], const
   }
 }
 
-// y-normal solve through the x <-> y transposition of the equations
+// y-normal solve through the x <-> y transposition of the equations; the
+// transposition is a register select, so one copy of the x-normal solve
+// serves both normals
 template <class R>
-FD_HD void swap_uv(const R a[4], R b[4]) { b[0] = a[0]; b[1] = a[2]; b[2] = a[1]; b[3] = a[3]; }
+FD_HD void swap_uv(const R a[4], R b[4], bool sw) {
+  b[0] = a[0];
+  b[1] = sw ? a[2] : a[1];
+  b[2] = sw ? a[1] : a[2];
+  b[3] = a[3];
+}
 
 template <class R>
 FD_HD void iface_solve(const GasK<R>& gas, int normal, const R Wl[4], const R Wr[4], const R Wln[4],
                        const R Wrn[4], const R Wt[4], bool want_n, IfaceOut<R>& o) {
-  if (normal == 0) {
-    iface_solve_x(gas, Wl, Wr, Wln, Wrn, Wt, want_n, o);
-    return;
-  }
+  const bool sw = normal != 0;
   R a[4], b[4], c[4], d[4], e[4];
-  swap_uv(Wl, a); swap_uv(Wr, b); swap_uv(Wln, c); swap_uv(Wrn, d); swap_uv(Wt, e);
+  swap_uv(Wl, a, sw); swap_uv(Wr, b, sw); swap_uv(Wln, c, sw); swap_uv(Wrn, d, sw); swap_uv(Wt, e, sw);
   IfaceOut<R> t;
   iface_solve_x(gas, a, b, c, d, e, want_n, t);
-  swap_uv(t.Ft, o.Ft); swap_uv(t.Wlt, o.Wlt); swap_uv(t.Wrt, o.Wrt);
-  if (want_n) { swap_uv(t.F, o.F); swap_uv(t.Wl, o.Wl); swap_uv(t.Wr, o.Wr); }
+  swap_uv(t.Ft, o.Ft, sw); swap_uv(t.Wlt, o.Wlt, sw); swap_uv(t.Wrt, o.Wrt, sw);
+  if (want_n) { swap_uv(t.F, o.F, sw); swap_uv(t.Wl, o.Wl, sw); swap_uv(t.Wr, o.Wr, sw); }
 }
 
 // ---------------------------------------------------------------------------
