@@ -10,6 +10,7 @@
 #include "fdcgks_internal.cuh"
 
 using namespace fdk;
+using fdk::check_params;
 
 struct fdcgks_ctx {
   fdcgks_params p;
@@ -69,49 +70,7 @@ static fdcgks_status fail(fdcgks_t c, fdcgks_status s, const char* fmt, ...) {
 // ---------------------------------------------------------------------------
 // run constants
 // ---------------------------------------------------------------------------
-template <class R>
-static GenoK<R> make_geno(int variant) {
-  GenoK<R> g;
-  g.linear = variant == 2;
-  g.C = (R)20.0;
-  g.tanhC = (R)std::tanh(20.0);
-  g.inv_tanhC = (R)(1.0 / std::tanh(20.0));
-  g.eps_w = (R)1e-6;
-  if (variant == 1) {
-    g.r = 3;
-    g.eps_a = (R)1e-15;
-    g.d_iface[0] = 1; g.d_iface[1] = 8; g.d_iface[2] = 1;
-  } else {
-    g.r = 2;
-    g.eps_a = (R)1e-12;
-    g.d_iface[0] = 8; g.d_iface[1] = 1; g.d_iface[2] = 1;
-  }
-  g.d_node[0] = 8; g.d_node[1] = 1; g.d_node[2] = 1;
-  return g;
-}
-
-template <class R>
-static GasK<R> make_gas(const fdcgks_params& p, double dt) {
-  GasK<R> g;
-  const double K = (4.0 - 2.0 * p.gamma) / (p.gamma - 1.0);
-  g.K = (R)K;
-  g.gm1 = (R)(p.gamma - 1.0);
-  g.c4K = (R)(4.0 / (K + 2.0));
-  g.prfix = (R)(1.0 / p.Pr - 1.0);
-  g.mu = p.mu;
-  g.c1 = p.tau_c1;
-  g.c2 = p.tau_c2;
-  g.dt = dt;
-  g.inv_dt = 1.0 / dt;
-  g.mu_r = (R)p.mu;
-  g.c1_r = (R)p.tau_c1;
-  g.c2_r = (R)p.tau_c2;
-  g.dt_r = (R)dt;
-  g.inv_dt_r = (R)(1.0 / dt);
-  return g;
-}
-
-static const char* check_params(const fdcgks_params* p) {
+const char* fdk::check_params(const fdcgks_params* p) {
   if (!p) return "params is NULL";
   if (p->nx < 1 || p->ny < 1) return "nx and ny must be >= 1";
   if (p->nx > (1 << 20) || p->ny > (1 << 20)) return "nx or ny too large";
@@ -143,47 +102,8 @@ static size_t rsize(const fdcgks_params& p) { return p.precision == FDCGKS_MIXED
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void ghost_kernel(T* S, Layout L, int bc0, int bc1, int dir) {
-  const int g = blockIdx.z;
-  const int nxg = g == 0 ? L.nx : L.nxd, nyg = g == 0 ? L.ny : L.nyd;
-  const int n = dir == 0 ? nxg : nyg;
-  const int tcount = dir == 0 ? nyg : nxg + 2 * GH;
-  const int toff = dir == 0 ? 0 : -GH;
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;   // over (t, side, k)
-  if (idx >= tcount * 2 * GH) return;
-  const int k = 1 + idx % GH;
-  const int side = (idx / GH) % 2;
-  const int t = idx / (2 * GH) + toff;
-  const int b = side == 0 ? bc0 : bc1;
-  const int ghost = side == 0 ? -k : n - 1 + k;
-  int src;
-  if (b == FDCGKS_BC_PERIODIC) src = ((ghost % n) + n) % n;   // also for n < GH
-  else if (b == FDCGKS_BC_TRANSMISSIVE) src = side == 0 ? 0 : n - 1;
-  else if (g == 0) src = side == 0 ? k - 1 : n - k;
-  else src = side == 0 ? k : n - 1 - k;
-  const long gc = dir == 0 ? cell(L, ghost, t) : cell(L, t, ghost);
-  const long sc = dir == 0 ? cell(L, src, t) : cell(L, t, src);
-  T* Sg = S + (long)g * NFLD * L.plane;
-  for (int c = 0; c < 4; ++c) {
-    T sW = 1;
-    if (b == FDCGKS_BC_SYMMETRY || b == FDCGKS_BC_NOSLIP) {
-      if (c == 1 + dir) sW = -1.0;
-      if (c == 2 - dir && b == FDCGKS_BC_NOSLIP) sW = -1.0;
-    }
-    T w = Sg[(long)c * L.plane + sc];
-    T gx = Sg[(long)(4 + c) * L.plane + sc];
-    T gy = Sg[(long)(8 + c) * L.plane + sc];
-    if (b == FDCGKS_BC_TRANSMISSIVE) {
-      gx = 0;
-      gy = 0;
-    } else if (b != FDCGKS_BC_PERIODIC) {
-      w *= sW;
-      gx *= (dir == 0 ? -sW : sW);
-      gy *= (dir == 1 ? -sW : sW);
-    }
-    Sg[(long)c * L.plane + gc] = w;
-    Sg[(long)(4 + c) * L.plane + gc] = gx;
-    Sg[(long)(8 + c) * L.plane + gc] = gy;
-  }
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  ghost_body(S, L, bc0, bc1, dir, blockIdx.z, idx);
 }
 
 template <class T>

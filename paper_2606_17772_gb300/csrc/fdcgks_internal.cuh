@@ -4,6 +4,9 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
+
+#include "../../include/fdcgks.h"
 #include "fdcgks_math.cuh"
 
 namespace fdk {
@@ -66,10 +69,106 @@ struct KArgs {
   double* op[8];         // operator outputs (Lp, Ltp, gbp, gtp, Ld, Ltd, gbd, gtd), interior layout
 };
 
+// Ghost layers of one grid g of a padded state (W, x- and y-gradients):
+// periodic wrap, mirror (symmetry: normal momentum odd; no-slip: both momenta
+// odd; gradients take the field's parity times -1 along the mirror normal) or
+// constant extrapolation with zero gradients (transmissive).  Work item idx
+// covers (row or column t, side, layer k); dir 0 fills x ghosts of interior
+// rows, dir 1 y ghosts of all columns (so corners are consistent).
+template <class T>
+__device__ __forceinline__ void ghost_body(T* S, const Layout& L, int bc0, int bc1, int dir, int g, int idx) {
+  const int nxg = g == 0 ? L.nx : L.nxd, nyg = g == 0 ? L.ny : L.nyd;
+  const int n = dir == 0 ? nxg : nyg;
+  const int tcount = dir == 0 ? nyg : nxg + 2 * GH;
+  const int toff = dir == 0 ? 0 : -GH;
+  if (idx < 0 || idx >= tcount * 2 * GH) return;
+  const int k = 1 + idx % GH;
+  const int side = (idx / GH) % 2;
+  const int t = idx / (2 * GH) + toff;
+  const int b = side == 0 ? bc0 : bc1;
+  const int ghost = side == 0 ? -k : n - 1 + k;
+  int src;
+  if (b == 0) src = ((ghost % n) + n) % n;                 // periodic, also for n < GH
+  else if (b == 1) src = side == 0 ? 0 : n - 1;            // transmissive
+  else if (g == 0) src = side == 0 ? k - 1 : n - k;        // mirror about the boundary line
+  else src = side == 0 ? k : n - 1 - k;
+  const long gc = dir == 0 ? cell(L, ghost, t) : cell(L, t, ghost);
+  const long sc = dir == 0 ? cell(L, src, t) : cell(L, t, src);
+  T* Sg = S + (long)g * NFLD * L.plane;
+  for (int c = 0; c < 4; ++c) {
+    T sW = 1;
+    if (b == 2 || b == 3) {
+      if (c == 1 + dir) sW = -1;
+      if (c == 2 - dir && b == 3) sW = -1;
+    }
+    T w = Sg[(long)c * L.plane + sc];
+    T gx = Sg[(long)(4 + c) * L.plane + sc];
+    T gy = Sg[(long)(8 + c) * L.plane + sc];
+    if (b == 1) {
+      gx = 0;
+      gy = 0;
+    } else if (b != 0) {
+      w *= sW;
+      gx *= (dir == 0 ? -sW : sW);
+      gy *= (dir == 1 ? -sW : sW);
+    }
+    Sg[(long)c * L.plane + gc] = w;
+    Sg[(long)(4 + c) * L.plane + gc] = gx;
+    Sg[(long)(8 + c) * L.plane + gc] = gy;
+  }
+}
+
 enum { UPD_STAGE1 = 0, UPD_STAGE2 = 1, UPD_OPERATOR = 2 };
 
 // message returned by fdcgks_last_error(NULL)
 void set_global_error(const char* msg);
+
+// validation of user parameters (nullptr when valid)
+const char* check_params(const fdcgks_params* p);
+
+// run constants in the compute type
+template <class R>
+inline GenoK<R> make_geno(int variant) {
+  GenoK<R> g;
+  g.linear = variant == 2;
+  g.C = (R)20.0;
+  g.tanhC = (R)std::tanh(20.0);
+  g.inv_tanhC = (R)(1.0 / std::tanh(20.0));
+  g.eps_w = (R)1e-6;
+  if (variant == 1) {
+    g.r = 3;
+    g.eps_a = (R)1e-15;
+    g.d_iface[0] = 1; g.d_iface[1] = 8; g.d_iface[2] = 1;
+  } else {
+    g.r = 2;
+    g.eps_a = (R)1e-12;
+    g.d_iface[0] = 8; g.d_iface[1] = 1; g.d_iface[2] = 1;
+  }
+  g.d_node[0] = 8; g.d_node[1] = 1; g.d_node[2] = 1;
+  return g;
+}
+
+template <class R>
+inline GasK<R> make_gas(const fdcgks_params& p, double dt) {
+  GasK<R> g;
+  const double K = (4.0 - 2.0 * p.gamma) / (p.gamma - 1.0);
+  g.K = (R)K;
+  g.gm1 = (R)(p.gamma - 1.0);
+  g.c4K = (R)(4.0 / (K + 2.0));
+  g.prfix = (R)(1.0 / p.Pr - 1.0);
+  g.mu = p.mu;
+  g.c1 = p.tau_c1;
+  g.c2 = p.tau_c2;
+  g.dt = dt;
+  g.inv_dt = 1.0 / dt;
+  g.mu_r = (R)p.mu;
+  g.c1_r = (R)p.tau_c1;
+  g.c2_r = (R)p.tau_c2;
+  g.dt_r = (R)dt;
+  g.inv_dt_r = (R)(1.0 / dt);
+  return g;
+}
+
 
 template <class R> cudaError_t launch_nodal(const KArgs<R>& a, cudaStream_t s);
 template <class R> cudaError_t launch_points(const KArgs<R>& a, cudaStream_t s);

@@ -61,13 +61,10 @@ __device__ __noinline__ void iface_solve_call(const GasK<R>& gas, int normal, co
 // one thread per node, nodes i in [-1, n_x], j in [-1, n_y] of grid blockIdx.z
 // ---------------------------------------------------------------------------
 template <class R>
-__global__ void __launch_bounds__(128, PointTune<R>::nodal_minb) nodal_kernel(KArgs<R> a) {
-  const int g = blockIdx.z;
+__device__ __forceinline__ void nodal_body(const KArgs<R>& a, int g, int i, int j) {
   const Layout& L = a.L;
   const int nxg = g == 0 ? L.nx : L.nxd, nyg = g == 0 ? L.ny : L.nyd;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x - 1;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y - 1;
-  if (i > nxg || j > nyg) return;
+  if (i < -1 || j < -1 || i > nxg || j > nyg) return;
   const R* S = a.Sr + (long)g * NFLD * L.plane;
   const long c0 = cell(L, i, j);
   R W[4], Wx[4], Wy[4];
@@ -96,6 +93,11 @@ __global__ void __launch_bounds__(128, PointTune<R>::nodal_minb) nodal_kernel(KA
   }
 }
 
+template <class R>
+__global__ void __launch_bounds__(128, PointTune<R>::nodal_minb) nodal_kernel(KArgs<R> a) {
+  nodal_body(a, blockIdx.z, blockIdx.x * blockDim.x + threadIdx.x - 1, blockIdx.y * blockDim.y + threadIdx.y - 1);
+}
+
 // reconstruct one 4-point line of one grid at its virtual interface
 // (between entries 1 and 2): starting cell c0 (entry 0), stride between
 // entries, gradient field offset gfield (4: x-gradient, 8: y-gradient)
@@ -120,13 +122,11 @@ FD_HD void recon_line(const GenoK<R>& geno, const R* S, long plane, long c0, lon
 // TYPE 1 = point B (i, j+1/2): primary y-interface, dual x-interface of dual row j+1
 // ---------------------------------------------------------------------------
 template <class R, int TYPE>
-__global__ void __launch_bounds__(128, PointTune<R>::minb) point_kernel(KArgs<R> a) {
+__device__ __forceinline__ void point_body(const KArgs<R>& a, int i, int j) {
   const Layout& L = a.L;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x - 2;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y - 2;
   const int imax = TYPE == 0 ? L.nx : L.nxd;
   const int jmax = TYPE == 0 ? L.nyd : L.ny;
-  if (i > imax || j > jmax) return;
+  if (i < -2 || j < -2 || i > imax || j > jmax) return;
   const R* SP = a.Sr;
   const R* SD = a.Sr + (long)NFLD * L.plane;
   const int n0 = TYPE;        // normal of the primary-grid solve
@@ -182,6 +182,11 @@ __global__ void __launch_bounds__(128, PointTune<R>::minb) point_kernel(KArgs<R>
   }
   P[PO_CHI * pp] = chi0;
   P[(NPS + PO_CHI) * pp] = chi1;
+}
+
+template <class R, int TYPE>
+__global__ void __launch_bounds__(128, PointTune<R>::minb) point_kernel(KArgs<R> a) {
+  point_body<R, TYPE>(a, blockIdx.x * blockDim.x + threadIdx.x - 2, blockIdx.y * blockDim.y + threadIdx.y - 2);
 }
 
 // ---------------------------------------------------------------------------
@@ -265,13 +270,10 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float b) {
 }
 
 template <class R>
-__global__ void __launch_bounds__(128, PointTune<R>::update_minb) update_kernel(KArgs<R> a, int mode) {
-  const int g = blockIdx.z;
+__device__ __forceinline__ void update_body(const KArgs<R>& a, int mode, int g, int i, int j) {
   const Layout& L = a.L;
   const int nxg = g == 0 ? L.nx : L.nxd, nyg = g == 0 ? L.ny : L.nyd;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= nxg || j >= nyg) return;
+  if (i < 0 || j < 0 || i >= nxg || j >= nyg) return;
   NodeOp<R> o;
   node_operator(a, g, i, j, mode != UPD_STAGE2, o);
   const long c0 = cell(L, i, j);
@@ -403,6 +405,11 @@ __global__ void __launch_bounds__(128, PointTune<R>::update_minb) update_kernel(
     double p = Wnew[3] - 0.5 * (Wnew[1] * Wnew[1] + Wnew[2] * Wnew[2]) / Wnew[0];
     if (!(Wnew[0] > 0.0) || !(p > 0.0)) atomicOr(a.flag, 1);
   }
+}
+
+template <class R>
+__global__ void __launch_bounds__(128, PointTune<R>::update_minb) update_kernel(KArgs<R> a, int mode) {
+  update_body(a, mode, blockIdx.z, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
 }
 
 // ---------------------------------------------------------------------------
