@@ -191,6 +191,95 @@ fdcgks_status fdcgks_recon_batch(const fdcgks_params* params, int kind, double h
 fdcgks_status fdcgks_cfl_dt_noalloc(const fdcgks_params* params, const double* Wp, const double* Wd, double cfl,
                                     double* dt_out);
 
+/* ------------------------------------------------------------------------
+ * Batched ensemble.  The paper has no counterpart: its runs are independent,
+ * and batching them is an execution strategy for parameter sweeps and
+ * uncertainty studies with many small and mid-sized grids, which one at a
+ * time cannot fill the GPU.  An ensemble holds `count` independent runs
+ * ("members"), each with its own fdcgks_params (grid size, domain, boundary
+ * conditions, gas constants, variants); every member advances exactly as a
+ * context created with the same params would (same kernels per node, same
+ * time-step formula), so member results equal single-context results.
+ *   - All members share params[0].precision (FDCGKS_ERR_ARG otherwise).
+ *   - params[m].stream is ignored: the ensemble owns one CUDA stream, given
+ *     by fdcgks_ens_info, and every entry point below synchronizes it before
+ *     returning except fdcgks_ens_run.
+ *   - A step of the ensemble: each member's CFL time step is reduced on the
+ *     device (the formula of fdcgks_cfl_dt), or taken from a fixed array,
+ *     and both S2O4 stages of every member follow; one step is captured into
+ *     a CUDA graph on first use and replayed.
+ *   - Per-member status bits (fdcgks_ens_status): NONPHYSICAL when a stage
+ *     produced non-positive or non-finite density or pressure; NO_WAVE_SPEED
+ *     when no finite CFL rate was found; FROZEN once either happened (at the
+ *     start of the next step): a frozen member is no longer advanced and its
+ *     time stops, the others continue.  fdcgks_ens_set_state clears them.
+ *   - Errors are reported through fdcgks_ens_last_error(ens); a failed
+ *     fdcgks_ens_create reports through fdcgks_last_error(NULL).
+ * ------------------------------------------------------------------------ */
+typedef struct fdcgks_ens* fdcgks_ens_t;
+
+#define FDCGKS_ENS_NONPHYSICAL 1
+#define FDCGKS_ENS_NO_WAVE_SPEED 2
+#define FDCGKS_ENS_FROZEN 4
+
+/* Create an ensemble of `count` >= 1 members described by params[count]
+ * (each validated as by fdcgks_create).  Allocates every member's buffers
+ * in one device allocation.  *out is NULL on failure. */
+fdcgks_status fdcgks_ens_create(const fdcgks_params* params, int count, fdcgks_ens_t* out);
+
+/* Release an ensemble and its device memory.  NULL is accepted. */
+void fdcgks_ens_destroy(fdcgks_ens_t ens);
+
+/* Load / read the state of member m (arrays as for fdcgks_set_state /
+ * fdcgks_get_state with that member's dims; host or device pointers per
+ * on_device).  set_state validates density and pressure
+ * (FDCGKS_ERR_NONPHYSICAL otherwise, member not loaded) and resets the
+ * member's time and status. */
+fdcgks_status fdcgks_ens_set_state(fdcgks_ens_t ens, int m, const double* Wp, const double* Gp, const double* Wd,
+                                   const double* Gd, int on_device);
+fdcgks_status fdcgks_ens_get_state(fdcgks_ens_t ens, int m, double* Wp, double* Gp, double* Wd, double* Gd,
+                                   int on_device);
+
+/* Advance every member nsteps steps.  dt == NULL: each member takes its own
+ * CFL time step (number cfl > 0) at every step, computed on the device.
+ * dt != NULL: host array dt[count] of fixed positive time steps (cfl is
+ * ignored).  Asynchronous on the ensemble's stream (the host array is
+ * copied before the call returns).  Every member must have a state. */
+fdcgks_status fdcgks_ens_run(fdcgks_ens_t ens, double cfl, const double* dt, int nsteps);
+
+/* Per-member elapsed time since its set_state, last time step taken and
+ * status bits (FDCGKS_ENS_*), into host arrays [count]; any may be NULL. */
+fdcgks_status fdcgks_ens_status(fdcgks_ens_t ens, double* t, double* last_dt, int* status);
+
+/* Tile configuration cfg[4]: log2 of the tile width (0..7; the tile height is
+ * 128 / width) of the nodal, point and update phases, then the dispatch
+ * (1: persistent grid of resident blocks taking tiles from an atomic queue;
+ * 0: one block per tile).  Default {5, 5, 5, 0}.  Results do not depend on
+ * it. */
+fdcgks_status fdcgks_ens_set_tiles(fdcgks_ens_t ens, const int* cfg);
+fdcgks_status fdcgks_ens_get_tiles(fdcgks_ens_t ens, int* cfg);
+
+/* Autotuner: times trial_steps CFL steps (number cfl) per candidate
+ * configuration (coordinate descent over the three tile widths 8..128,
+ * then the dispatch), keeps the fastest, and writes it to cfg_out[4] and
+ * its ms per step to *ms_out (either may be NULL).  Every member's state,
+ * time and status are restored afterwards (the tuner allocates a temporary
+ * copy of all states).  Every member must have a state. */
+fdcgks_status fdcgks_ens_tune(fdcgks_ens_t ens, double cfl, int trial_steps, int* cfg_out, double* ms_out);
+
+/* Phase timing: runs nsteps CFL steps outside the graph with CUDA events
+ * between phases and returns the summed milliseconds in ms[5]: CFL + time
+ * step, ghost fill, nodal, points, update.  Advances the members. */
+fdcgks_status fdcgks_ens_profile(fdcgks_ens_t ens, double cfl, int nsteps, double* ms);
+
+/* The ensemble's cudaStream_t, the number of kernels its stepping path has
+ * launched, and the total number of primary plus dual nodes (the node
+ * updates of one step); any may be NULL. */
+fdcgks_status fdcgks_ens_info(fdcgks_ens_t ens, void** stream, long long* launches, long long* nodes);
+
+/* Message of the last failed call on ens (NULL: as fdcgks_last_error(NULL)). */
+const char* fdcgks_ens_last_error(fdcgks_ens_t ens);
+
 /* Message of the last failed call on ctx (or of the last failed
  * context-free call when ctx is NULL). */
 const char* fdcgks_last_error(fdcgks_t ctx);

@@ -131,10 +131,18 @@ __global__ void join_ff_kernel(const float* hi, const float* lo, double* S, long
     S[t] = (double)hi[t] + (double)lo[t];
 }
 
+cudaError_t fdk::launch_split_ff(const double* S, float* hi, float* lo, long n, cudaStream_t s) {
+  split_ff_kernel<<<1024, 256, 0, s>>>(S, hi, lo, n);
+  return cudaGetLastError();
+}
+cudaError_t fdk::launch_join_ff(const float* hi, const float* lo, double* S, long n, cudaStream_t s) {
+  join_ff_kernel<<<1024, 256, 0, s>>>(hi, lo, S, n);
+  return cudaGetLastError();
+}
+
 static cudaError_t join_state(fdcgks_t c) {
   if (!c->Sf) return cudaSuccess;
-  join_ff_kernel<<<1024, 256, 0, c->stream>>>(c->Sf, c->Slo, c->S, 2L * NFLD * c->L.plane);
-  return cudaGetLastError();
+  return launch_join_ff(c->Sf, c->Slo, c->S, 2L * NFLD * c->L.plane, c->stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -154,6 +162,12 @@ __global__ void validate_kernel(const double* S, Layout L, double gamma, int* fl
   if (!ok) atomicOr(flag, 1);
 }
 
+cudaError_t fdk::launch_validate(const double* S, const Layout& L, double gamma, int* flag, cudaStream_t s) {
+  const int mx = L.nx > L.nxd ? L.nx : L.nxd, my = L.ny > L.nyd ? L.ny : L.nyd;
+  validate_kernel<<<dim3((mx + 127) / 128, my, 2), 128, 0, s>>>(S, L, gamma, flag);
+  return cudaGetLastError();
+}
+
 // per-block maxima of (|U|+c)/hx, (|V|+c)/hy (as one rate) and nu = mu/rho
 __global__ void cfl_kernel(const double* S, Layout L, double gamma, double mu, double ihx, double ihy, double* out) {
   double rate = 0.0, numax = 0.0;
@@ -165,11 +179,8 @@ __global__ void cfl_kernel(const double* S, Layout L, double gamma, double mu, d
     int i = (int)(q % nxg), j = (int)(q / nxg);
     const double* Sg = S + (long)g * NFLD * L.plane;
     const long c0 = cell(L, i, j);
-    double r = Sg[c0], U = Sg[L.plane + c0] / r, V = Sg[2 * L.plane + c0] / r;
-    double p = (gamma - 1.0) * (Sg[3 * L.plane + c0] - 0.5 * r * (U * U + V * V));
-    double cs = sqrt(gamma * p / r);
-    rate = fmax(rate, fmax((fabs(U) + cs) * ihx, (fabs(V) + cs) * ihy));
-    numax = fmax(numax, mu / r);
+    cfl_rates(Sg[c0], Sg[L.plane + c0], Sg[2 * L.plane + c0], Sg[3 * L.plane + c0], gamma, mu, ihx, ihy, rate,
+              numax);
   }
   // warp-shuffle max, then across warps in shared memory
   for (int o = 16; o > 0; o >>= 1) {
@@ -340,18 +351,8 @@ fdcgks_status fdcgks_create(const fdcgks_params* p, fdcgks_t* out) {
   c->stream = (cudaStream_t)p->stream;
   c->hx = (p->x1 - p->x0) / p->nx;
   c->hy = (p->y1 - p->y0) / p->ny;
-  Layout& L = c->L;
-  L.nx = p->nx;
-  L.ny = p->ny;
-  L.nxd = p->nx + (p->bc[0] == FDCGKS_BC_PERIODIC ? 0 : 1);
-  L.nyd = p->ny + (p->bc[2] == FDCGKS_BC_PERIODIC ? 0 : 1);
-  int mx = L.nx > L.nxd ? L.nx : L.nxd, my = L.ny > L.nyd ? L.ny : L.nyd;
-  L.pitch = ((mx + 2 * GH) + 31) / 32 * 32;
-  L.rows = my + 2 * GH;
-  L.plane = (long)L.pitch * L.rows;
-  L.ppitch = ((mx + 3) + 31) / 32 * 32;
-  L.prows = my + 3;
-  L.pplane = (long)L.ppitch * L.prows;
+  c->L = make_layout(*p);
+  const Layout& L = c->L;
   const size_t rs = rsize(*p);
   const bool mixed = p->precision == FDCGKS_MIXED;
   const size_t fp = sizeof(float) * L.plane;
@@ -441,14 +442,9 @@ fdcgks_status fdcgks_set_state(fdcgks_t c, const double* Wp, const double* Gp, c
       CUDA_TRY(c, copy_field(c, Sg + (long)f * L.plane, src, nullptr, nxg, nyg, true, on_device));
     }
   }
-  if (c->Sf) {
-    split_ff_kernel<<<1024, 256, 0, c->stream>>>(c->S, c->Sf, c->Slo, 2L * NFLD * L.plane);
-    CUDA_TRY(c, cudaGetLastError());
-  }
+  if (c->Sf) CUDA_TRY(c, launch_split_ff(c->S, c->Sf, c->Slo, 2L * NFLD * L.plane, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
-  int mx = L.nx > L.nxd ? L.nx : L.nxd, my = L.ny > L.nyd ? L.ny : L.nyd;
-  validate_kernel<<<dim3((mx + 127) / 128, my, 2), 128, 0, c->stream>>>(c->S, L, c->p.gamma, c->flag);
-  CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, launch_validate(c->S, L, c->p.gamma, c->flag, c->stream));
   int h = 0;
   CUDA_TRY(c, cudaMemcpyAsync(&h, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));

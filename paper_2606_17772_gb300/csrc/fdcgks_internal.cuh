@@ -36,6 +36,35 @@ struct Layout {
 FD_HD long cell(const Layout& L, int i, int j) { return (long)(j + GH) * L.pitch + (i + GH); }
 FD_HD long pcell(const Layout& L, int i, int j) { return (long)(j + 2) * L.ppitch + (i + 2); }
 
+// padded layout of a run: rows padded to multiples of 32 entries
+inline Layout make_layout(const fdcgks_params& p) {
+  Layout L;
+  L.nx = p.nx;
+  L.ny = p.ny;
+  L.nxd = p.nx + (p.bc[0] == FDCGKS_BC_PERIODIC ? 0 : 1);
+  L.nyd = p.ny + (p.bc[2] == FDCGKS_BC_PERIODIC ? 0 : 1);
+  const int mx = L.nx > L.nxd ? L.nx : L.nxd, my = L.ny > L.nyd ? L.ny : L.nyd;
+  L.pitch = ((mx + 2 * GH) + 31) / 32 * 32;
+  L.rows = my + 2 * GH;
+  L.plane = (long)L.pitch * L.rows;
+  L.ppitch = ((mx + 3) + 31) / 32 * 32;
+  L.prows = my + 3;
+  L.pplane = (long)L.ppitch * L.prows;
+  return L;
+}
+
+// CFL rates of one node (Sec. 5 time step): the larger of (|U| + c)/hx and
+// (|V| + c)/hy, and the kinematic viscosity mu/rho, folded into running
+// maxima (fmax: a NaN never replaces a number)
+FD_HD void cfl_rates(double r, double ru, double rv, double E, double gamma, double mu, double ihx, double ihy,
+                     double& rate, double& numax) {
+  const double U = ru / r, V = rv / r;
+  const double p = (gamma - 1.0) * (E - 0.5 * r * (U * U + V * V));
+  const double cs = sqrt(gamma * p / r);
+  rate = fmax(rate, fmax((fabs(U) + cs) * ihx, (fabs(V) + cs) * ihy));
+  numax = fmax(numax, mu / r);
+}
+
 template <class R>
 struct KArgs {
   Layout L;
@@ -169,6 +198,13 @@ inline GasK<R> make_gas(const fdcgks_params& p, double dt) {
   return g;
 }
 
+
+// whole-plane helpers of the host runtime (fdcgks_api.cu), on stream s:
+// positivity/finiteness check of the interior of an FP64 state (sets bit 0 of
+// *flag), and the FP64 <-> float-float conversion of n entries
+cudaError_t launch_validate(const double* S, const Layout& L, double gamma, int* flag, cudaStream_t s);
+cudaError_t launch_split_ff(const double* S, float* hi, float* lo, long n, cudaStream_t s);
+cudaError_t launch_join_ff(const float* hi, const float* lo, double* S, long n, cudaStream_t s);
 
 template <class R> cudaError_t launch_nodal(const KArgs<R>& a, cudaStream_t s);
 template <class R> cudaError_t launch_points(const KArgs<R>& a, cudaStream_t s);

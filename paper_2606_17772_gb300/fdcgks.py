@@ -21,7 +21,12 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "non-physical stat
 EXPORTS = ["fdcgks_create", "fdcgks_destroy", "fdcgks_dims", "fdcgks_set_state", "fdcgks_get_state",
            "fdcgks_step", "fdcgks_steps", "fdcgks_cfl_dt", "fdcgks_check", "fdcgks_stage_operator",
            "fdcgks_iface_batch", "fdcgks_nodal_batch", "fdcgks_recon_batch", "fdcgks_last_error",
-           "fdcgks_status_string", "fdcgks_set_profiling", "fdcgks_get_profile", "fdcgks_cfl_dt_noalloc"]
+           "fdcgks_status_string", "fdcgks_set_profiling", "fdcgks_get_profile", "fdcgks_cfl_dt_noalloc",
+           "fdcgks_ens_create", "fdcgks_ens_destroy", "fdcgks_ens_set_state", "fdcgks_ens_get_state",
+           "fdcgks_ens_run", "fdcgks_ens_status", "fdcgks_ens_set_tiles", "fdcgks_ens_get_tiles",
+           "fdcgks_ens_tune", "fdcgks_ens_profile", "fdcgks_ens_info", "fdcgks_ens_last_error"]
+
+ENS_NONPHYSICAL, ENS_NO_WAVE_SPEED, ENS_FROZEN = 1, 2, 4
 
 
 class Params(ctypes.Structure):
@@ -83,6 +88,21 @@ def load(path=None):
                                        ctypes.POINTER(ctypes.c_longlong)]
     lib.fdcgks_cfl_dt_noalloc.argtypes = [ctypes.POINTER(Params), _VP, _VP, ctypes.c_double,
                                           ctypes.POINTER(ctypes.c_double)]
+    lib.fdcgks_ens_create.argtypes = [ctypes.POINTER(Params), ctypes.c_int, ctypes.POINTER(_VP)]
+    lib.fdcgks_ens_destroy.argtypes = [_VP]
+    lib.fdcgks_ens_destroy.restype = None
+    lib.fdcgks_ens_set_state.argtypes = [_VP, ctypes.c_int, _VP, _VP, _VP, _VP, ctypes.c_int]
+    lib.fdcgks_ens_get_state.argtypes = [_VP, ctypes.c_int, _VP, _VP, _VP, _VP, ctypes.c_int]
+    lib.fdcgks_ens_run.argtypes = [_VP, ctypes.c_double, _VP, ctypes.c_int]
+    lib.fdcgks_ens_status.argtypes = [_VP, _VP, _VP, _VP]
+    lib.fdcgks_ens_set_tiles.argtypes = [_VP, _VP]
+    lib.fdcgks_ens_get_tiles.argtypes = [_VP, _VP]
+    lib.fdcgks_ens_tune.argtypes = [_VP, ctypes.c_double, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_double)]
+    lib.fdcgks_ens_profile.argtypes = [_VP, ctypes.c_double, ctypes.c_int, _VP]
+    lib.fdcgks_ens_info.argtypes = [_VP, ctypes.POINTER(_VP), ctypes.POINTER(ctypes.c_longlong),
+                                    ctypes.POINTER(ctypes.c_longlong)]
+    lib.fdcgks_ens_last_error.argtypes = [_VP]
+    lib.fdcgks_ens_last_error.restype = ctypes.c_char_p
     lib.fdcgks_last_error.argtypes = [_VP]
     lib.fdcgks_last_error.restype = ctypes.c_char_p
     lib.fdcgks_status_string.argtypes = [ctypes.c_int]
@@ -90,7 +110,9 @@ def load(path=None):
     for name in ("fdcgks_create", "fdcgks_dims", "fdcgks_set_state", "fdcgks_get_state", "fdcgks_step",
                  "fdcgks_steps", "fdcgks_cfl_dt", "fdcgks_check", "fdcgks_stage_operator", "fdcgks_iface_batch",
                  "fdcgks_nodal_batch", "fdcgks_recon_batch", "fdcgks_set_profiling", "fdcgks_get_profile",
-                 "fdcgks_cfl_dt_noalloc"):
+                 "fdcgks_cfl_dt_noalloc", "fdcgks_ens_create", "fdcgks_ens_set_state", "fdcgks_ens_get_state",
+                 "fdcgks_ens_run", "fdcgks_ens_status", "fdcgks_ens_set_tiles", "fdcgks_ens_get_tiles",
+                 "fdcgks_ens_tune", "fdcgks_ens_profile", "fdcgks_ens_info"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -316,3 +338,136 @@ def cfl_dt_noalloc(params, Wp, Wd, cfl):
     _check(load().fdcgks_cfl_dt_noalloc(ctypes.byref(params), _dptr(Wp, 4 * params.nx * params.ny),
                                         _dptr(Wd, 4 * nxd * nyd), ctypes.c_double(cfl), ctypes.byref(out)))
     return out.value
+
+
+def _echeck(status, ens):
+    if status != 0:
+        raise FdcgksError(status, load().fdcgks_ens_last_error(ens).decode())
+
+
+class Ensemble:
+    """A batch of independent runs advanced together (fdcgks_ens_create ... fdcgks_ens_destroy).
+
+    members: a list of Params (one per run; all with the same precision).
+    The ensemble works on its own CUDA stream (`stream`); every method but
+    run() synchronizes it before returning.
+    """
+
+    def __init__(self, members):
+        lib = load()
+        self.count = len(members)
+        arr = (Params * self.count)(*members)
+        h = _VP()
+        _check(lib.fdcgks_ens_create(arr, self.count, ctypes.byref(h)))
+        self._h = h
+        self.dims = []
+        for p in members:
+            nxd = p.nx + (0 if p.bc[0] == BC_PERIODIC else 1)
+            nyd = p.ny + (0 if p.bc[2] == BC_PERIODIC else 1)
+            self.dims.append((p.nx, p.ny, nxd, nyd))
+        st, n = _VP(), ctypes.c_longlong()
+        _echeck(lib.fdcgks_ens_info(h, ctypes.byref(st), None, ctypes.byref(n)), h)
+        self.stream = st.value
+        self.nodes = n.value
+
+    @classmethod
+    def from_cases(cls, cases, precision=FP64):
+        return cls([params_for_case(c, precision) for c in cases])
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().fdcgks_ens_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def shapes(self, m):
+        if not 0 <= m < self.count:
+            raise IndexError("member %d out of range [0, %d)" % (m, self.count))
+        nx, ny, nxd, nyd = self.dims[m]
+        return ((4, ny, nx), (2, 4, ny, nx), (4, nyd, nxd), (2, 4, nyd, nxd))
+
+    def _ptrs(self, m, arrs, on_device):
+        sizes = [int(np.prod(s)) for s in self.shapes(m)]
+        conv = _dptr if on_device else _hptr
+        return [conv(a, n) for a, n in zip(arrs, sizes)]
+
+    def set_state(self, m, Wp, Gp, Wd, Gd):
+        import torch
+        on_device = isinstance(Wp, torch.Tensor) and Wp.is_cuda
+        if on_device:
+            torch.cuda.current_stream().synchronize()
+        _echeck(load().fdcgks_ens_set_state(self._h, int(m), *self._ptrs(m, (Wp, Gp, Wd, Gd), on_device),
+                                            int(on_device)), self._h)
+
+    def get_state(self, m, out=None, device=True):
+        import torch
+        if out is None:
+            if device:
+                out = [torch.empty(s, dtype=torch.float64, device="cuda") for s in self.shapes(m)]
+            else:
+                out = [np.empty(s) for s in self.shapes(m)]
+        on_device = isinstance(out[0], torch.Tensor) and out[0].is_cuda
+        _echeck(load().fdcgks_ens_get_state(self._h, int(m), *self._ptrs(m, out, on_device), int(on_device)),
+                self._h)
+        return tuple(out)
+
+    def run(self, nsteps, cfl=0.4, dt=None):
+        """nsteps steps; dt None: per-member CFL steps (cfl), else a sequence of fixed per-member steps."""
+        if dt is None:
+            ptr = None
+        else:
+            arr = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (self.count,)))
+            ptr = ctypes.c_void_p(arr.ctypes.data)
+        _echeck(load().fdcgks_ens_run(self._h, ctypes.c_double(cfl), ptr, int(nsteps)), self._h)
+
+    def status(self):
+        """(time since set_state, last dt, status bits) per member as numpy arrays."""
+        t = np.zeros(self.count)
+        d = np.zeros(self.count)
+        s = np.zeros(self.count, dtype=np.int32)
+        _echeck(load().fdcgks_ens_status(self._h, ctypes.c_void_p(t.ctypes.data), ctypes.c_void_p(d.ctypes.data),
+                                         ctypes.c_void_p(s.ctypes.data)), self._h)
+        return t, d, s
+
+    def set_tiles(self, cfg):
+        a = (ctypes.c_int * 4)(*cfg)
+        _echeck(load().fdcgks_ens_set_tiles(self._h, a), self._h)
+
+    def get_tiles(self):
+        a = (ctypes.c_int * 4)()
+        _echeck(load().fdcgks_ens_get_tiles(self._h, a), self._h)
+        return list(a)
+
+    def tune(self, cfl=0.4, trial_steps=3):
+        """Autotune the tile configuration; returns (cfg, ms per step)."""
+        a = (ctypes.c_int * 4)()
+        ms = ctypes.c_double()
+        _echeck(load().fdcgks_ens_tune(self._h, ctypes.c_double(cfl), int(trial_steps), a, ctypes.byref(ms)),
+                self._h)
+        return list(a), ms.value
+
+    def profile(self, nsteps, cfl=0.4):
+        """Advance nsteps CFL steps outside the graph; ms per phase (cfl, ghost, nodal, points, update)."""
+        a = (ctypes.c_double * 5)()
+        _echeck(load().fdcgks_ens_profile(self._h, ctypes.c_double(cfl), int(nsteps), a), self._h)
+        return dict(zip(("cfl", "ghost", "nodal", "points", "update"), list(a)))
+
+    def launches(self):
+        n = ctypes.c_longlong()
+        _echeck(load().fdcgks_ens_info(self._h, None, ctypes.byref(n), None), self._h)
+        return n.value
+
+    def synchronize(self):
+        import torch
+        torch.cuda.ExternalStream(self.stream).synchronize()
