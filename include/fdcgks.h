@@ -205,9 +205,11 @@ fdcgks_status fdcgks_cfl_dt_noalloc(const fdcgks_params* params, const double* W
  *     by fdcgks_ens_info, and every entry point below synchronizes it before
  *     returning except fdcgks_ens_run.
  *   - A step of the ensemble: each member's CFL time step is reduced on the
- *     device (the formula of fdcgks_cfl_dt), or taken from a fixed array,
- *     and both S2O4 stages of every member follow; one step is captured into
- *     a CUDA graph on first use and replayed.
+ *     device (the formula of fdcgks_cfl_dt, in FP64; the mixed path screens
+ *     nodes with FP32 estimates first and evaluates in FP64 only those that
+ *     can hold the maxima, which leaves the result unchanged), or taken from
+ *     a fixed array, and both S2O4 stages of every member follow; one step
+ *     is captured into a CUDA graph on first use and replayed.
  *   - Per-member status bits (fdcgks_ens_status): NONPHYSICAL when a stage
  *     produced non-positive or non-finite density or pressure; NO_WAVE_SPEED
  *     when no finite CFL rate was found; FROZEN once either happened (at the

@@ -41,8 +41,8 @@ const int CFL_TILE = 1024;     // nodes per CFL tile (8 per thread)
 
 // launch phases of one stage
 enum { PH_GHOSTX = 0, PH_GHOSTY, PH_NODAL, PH_POINTS, PH_UPDATE, PH_CFL, PH_N };
-// queue heads of one step: the 5 stage phases twice, then the CFL reduction
-const int N_COUNTERS = 2 * 5 + 1;
+// queue heads of one step: the 5 stage phases twice, then the CFL passes
+const int N_COUNTERS = 2 * 5 + 2;
 
 // per-member constants of the CFL time step
 struct MemberMeta {
@@ -120,13 +120,87 @@ __device__ __forceinline__ double state_at(const KArgs<float>& a, long off) {
   return (double)a.Sn_hi[off] + (double)a.Sn_lo[off];
 }
 
+// FP32 estimate of one node's CFL rate and viscosity from the high parts of
+// the mixed state.  Reliable (relative error below 3e-6 against the FP64
+// formula on the joined pair) while p > 0.05 E: the inputs carry 2^-24
+// relative error, E - rho(U^2+V^2)/2 loses a factor E/p < 20 of it, and
+// the sound speed halves what reaches p.  Otherwise *ok is false.
+__device__ __forceinline__ void cfl_estimate(const float* hi, long c0, long plane, float gf, float muf, float ihxf,
+                                             float ihyf, float& rt, float& nu, bool& ok) {
+  const float r = hi[c0], ru = hi[c0 + plane], rv = hi[c0 + 2 * plane], E = hi[c0 + 3 * plane];
+  const float ir = __fdividef(1.0f, r), U = ru * ir, V = rv * ir;
+  const float p = (gf - 1.0f) * (E - 0.5f * r * (U * U + V * V));
+  const float c = sqrtf(fmaxf(gf * p * ir, 0.0f));
+  rt = fmaxf((fabsf(U) + c) * ihxf, (fabsf(V) + c) * ihyf);
+  nu = muf * ir;
+  ok = r > 0.0f && p > 0.05f * E && rt < INFINITY && nu < INFINITY;
+}
+
+// margin of the screening: a node is evaluated in FP64 when its estimate is
+// within this fraction of the member's largest reliable estimate (more than
+// twice the estimates' error bound, so the nodes holding the FP64 maxima are
+// always evaluated)
+const float SCREEN_MARGIN = 2e-5f;
+
+// mixed path, first pass: each member's largest reliable FP32 estimates,
+// folded with atomicMax on the bit patterns (non-negative floats)
+template <class R>
+__global__ void __launch_bounds__(ENS_THREADS) ens_cfl_screen_kernel(const KArgs<R>* args, const MemberMeta* meta,
+                                                                     PhaseQ q, unsigned* mxf) {
+  __shared__ float sr[ENS_THREADS / 32], sn[ENS_THREADS / 32];
+  __shared__ int s_tile;
+  for (int iter = 0;; ++iter) {
+    const int t = q.persistent ? next_tile<1>(q, iter, &s_tile) : next_tile<0>(q, iter, &s_tile);
+    if (t >= q.ntiles) break;
+    const int4 tl = q.tiles[t];
+    const int m = tl.x, g = tl.y;
+    float mr = 0.0f, mn = 0.0f;
+    if (!(q.mstat[m] & FDCGKS_ENS_FROZEN)) {
+      const KArgs<R>& a = args[2 * m];
+      const Layout L = a.L;
+      const MemberMeta mm = meta[m];
+      const int nxg = g == 0 ? L.nx : L.nxd, nyg = g == 0 ? L.ny : L.nyd, nn = nxg * nyg;
+      const float* hi = a.Sn_hi + (long)g * NFLD * L.plane;
+      for (int k = threadIdx.x; k < CFL_TILE; k += ENS_THREADS) {
+        const int n = tl.z + k;
+        if (n >= nn) break;
+        float rt, nu;
+        bool ok;
+        cfl_estimate(hi, cell(L, n % nxg, n / nxg), L.plane, (float)mm.gamma, (float)mm.mu, (float)mm.ihx,
+                     (float)mm.ihy, rt, nu, ok);
+        if (ok) {
+          mr = fmaxf(mr, rt);
+          mn = fmaxf(mn, nu);
+        }
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      mr = fmaxf(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+      mn = fmaxf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    }
+    const int w = threadIdx.x / 32;
+    if ((threadIdx.x & 31) == 0) { sr[w] = mr; sn[w] = mn; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int k = 1; k < ENS_THREADS / 32; ++k) { mr = fmaxf(mr, sr[k]); mn = fmaxf(mn, sn[k]); }
+      if (mr > 0.0f) atomicMax(mxf + 2 * m, __float_as_uint(mr));
+      if (mn > 0.0f) atomicMax(mxf + 2 * m + 1, __float_as_uint(mn));
+    }
+    __syncthreads();
+  }
+}
+
 // CFL maxima of each member: tiles (member, grid, first node, -) of CFL_TILE
 // nodes of one grid; block maxima folded into the member's pair with
 // atomicMax on the bit patterns (both maxima are >= 0, where the order of the
-// patterns is the order of the values)
+// patterns is the order of the values).  FP64 path: every node evaluated.
+// Mixed path: the FP64 rates (from the joined float-float pairs) only where
+// the FP32 estimate is unreliable or within SCREEN_MARGIN of the member's
+// largest estimate (first pass); the maxima are exactly those of evaluating
+// every node.
 template <class R>
 __global__ void __launch_bounds__(ENS_THREADS) ens_cfl_kernel(const KArgs<R>* args, const MemberMeta* meta, PhaseQ q,
-                                                              unsigned long long* mx) {
+                                                              const unsigned* mxf, unsigned long long* mx) {
   __shared__ double sr[ENS_THREADS / 32], sn[ENS_THREADS / 32];
   __shared__ int s_tile;
   for (int iter = 0;; ++iter) {
@@ -139,14 +213,28 @@ __global__ void __launch_bounds__(ENS_THREADS) ens_cfl_kernel(const KArgs<R>* ar
       const KArgs<R>& a = args[2 * m];
       const Layout L = a.L;
       const MemberMeta mm = meta[m];
-      const int nxg = g == 0 ? L.nx : L.nxd, nyg = g == 0 ? L.ny : L.nyd;
-      const long nn = (long)nxg * nyg, base = (long)g * NFLD * L.plane;
+      const int nxg = g == 0 ? L.nx : L.nxd, nyg = g == 0 ? L.ny : L.nyd, nn = nxg * nyg;
+      const long base = (long)g * NFLD * L.plane;
+      float tr = 0.0f, tn = INFINITY;
+      if constexpr (IsF32<R>::v) {
+        const float mr = __uint_as_float(mxf[2 * m]), mn = __uint_as_float(mxf[2 * m + 1]);
+        tr = mr * (1.0f - SCREEN_MARGIN);
+        if (mn > 0.0f) tn = mn * (1.0f - SCREEN_MARGIN);   // with mu = 0 nu never decides
+      }
       for (int k = threadIdx.x; k < CFL_TILE; k += ENS_THREADS) {
-        const long n = (long)tl.z + k;
+        const int n = tl.z + k;
         if (n >= nn) break;
-        const long c0 = base + cell(L, (int)(n % nxg), (int)(n / nxg));
-        cfl_rates(state_at(a, c0), state_at(a, c0 + L.plane), state_at(a, c0 + 2 * L.plane),
-                  state_at(a, c0 + 3 * L.plane), mm.gamma, mm.mu, mm.ihx, mm.ihy, rate, numax);
+        const long c0 = cell(L, n % nxg, n / nxg);
+        if constexpr (IsF32<R>::v) {
+          float rt, nu;
+          bool ok;
+          cfl_estimate(a.Sn_hi + base, c0, L.plane, (float)mm.gamma, (float)mm.mu, (float)mm.ihx, (float)mm.ihy,
+                       rt, nu, ok);
+          if (ok && rt < tr && nu < tn) continue;
+        }
+        const long cg = base + c0;
+        cfl_rates(state_at(a, cg), state_at(a, cg + L.plane), state_at(a, cg + 2 * L.plane),
+                  state_at(a, cg + 3 * L.plane), mm.gamma, mm.mu, mm.ihx, mm.ihy, rate, numax);
       }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -245,6 +333,7 @@ struct fdcgks_ens {
   double* fixed_dt = nullptr;
   double* cfl = nullptr;
   unsigned long long* mx = nullptr;
+  unsigned* mxf = nullptr;
   int* heads = nullptr;
   int* vflag = nullptr;
   double* staging = nullptr;              // FP64 padded state of the largest member
@@ -393,12 +482,17 @@ fdcgks_status enqueue_step(fdcgks_ens_t e, bool fixed, PhaseTimer* tm, int* nk) 
   ENS_TRY(e, cudaMemsetAsync(e->heads, 0, sizeof(int) * N_COUNTERS, e->stream));
   if (!fixed) {
     ENS_TRY(e, cudaMemsetAsync(e->mx, 0, sizeof(unsigned long long) * 2 * e->M, e->stream));
-    if (e->t_cnt[PH_CFL] > 0) {
-      ens_cfl_kernel<R><<<grid_of(e, PH_CFL), ENS_THREADS, 0, e->stream>>>(
-          (const KArgs<R>*)e->args, e->meta, phase_q(e, PH_CFL, 0, 10), e->mx);
+    if constexpr (IsF32<R>::v) {
+      ENS_TRY(e, cudaMemsetAsync(e->mxf, 0, sizeof(unsigned) * 2 * e->M, e->stream));
+      ens_cfl_screen_kernel<R><<<grid_of(e, PH_CFL), ENS_THREADS, 0, e->stream>>>(
+          (const KArgs<R>*)e->args, e->meta, phase_q(e, PH_CFL, 0, 11), e->mxf);
       ENS_TRY(e, cudaGetLastError());
       ++k;
     }
+    ens_cfl_kernel<R><<<grid_of(e, PH_CFL), ENS_THREADS, 0, e->stream>>>(
+        (const KArgs<R>*)e->args, e->meta, phase_q(e, PH_CFL, 0, 10), e->mxf, e->mx);
+    ENS_TRY(e, cudaGetLastError());
+    ++k;
   }
   ens_dt_kernel<R><<<(e->M + 127) / 128, 128, 0, e->stream>>>((KArgs<R>*)e->args, e->meta, e->mx,
                                                                fixed ? e->fixed_dt : nullptr, e->cfl, e->mstat,
@@ -427,7 +521,9 @@ fdcgks_status enqueue(fdcgks_ens_t e, bool fixed, PhaseTimer* tm, int* nk) {
   return e->precision == FDCGKS_MIXED ? enqueue_step<float>(e, fixed, tm, nk) : enqueue_step<double>(e, fixed, tm, nk);
 }
 
-int kernels_per_step(fdcgks_ens_t e, bool fixed) { return (fixed ? 0 : 1) + 1 + 10; }
+int kernels_per_step(fdcgks_ens_t e, bool fixed) {
+  return (fixed ? 0 : (e->precision == FDCGKS_MIXED ? 2 : 1)) + 1 + 10;
+}
 
 fdcgks_status ensure_graph(fdcgks_ens_t e, bool fixed) {
   cudaGraphExec_t& ge = e->graph[fixed ? 1 : 0];
@@ -622,7 +718,7 @@ void fdcgks_ens_destroy(fdcgks_ens_t e) {
   if (!e) return;
   drop_graphs(e);
   void* bufs[] = {e->arena, e->args, e->meta, e->mstat, e->time, e->last_dt, e->fixed_dt, e->cfl,
-                  e->mx, e->heads, e->vflag, e->staging, e->tiles};
+                  e->mx, e->mxf, e->heads, e->vflag, e->staging, e->tiles};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (e->stream) cudaStreamDestroy(e->stream);
@@ -706,6 +802,7 @@ fdcgks_status fdcgks_ens_create(const fdcgks_params* params, int count, fdcgks_e
       {(void**)&e->fixed_dt, sizeof(double) * count},
       {(void**)&e->cfl, sizeof(double)},
       {(void**)&e->mx, sizeof(unsigned long long) * 2 * count},
+      {(void**)&e->mxf, sizeof(unsigned) * 2 * count},
       {(void**)&e->heads, sizeof(int) * N_COUNTERS},
       {(void**)&e->vflag, sizeof(int)},
       {(void**)&e->staging, mixed ? sizeof(double) * 2 * NFLD * max_plane : 0},

@@ -58,11 +58,12 @@ inline Layout make_layout(const fdcgks_params& p) {
 // maxima (fmax: a NaN never replaces a number)
 FD_HD void cfl_rates(double r, double ru, double rv, double E, double gamma, double mu, double ihx, double ihy,
                      double& rate, double& numax) {
-  const double U = ru / r, V = rv / r;
+  const double ir = 1.0 / r;
+  const double U = ru * ir, V = rv * ir;
   const double p = (gamma - 1.0) * (E - 0.5 * r * (U * U + V * V));
-  const double cs = sqrt(gamma * p / r);
+  const double cs = sqrt(gamma * p * ir);
   rate = fmax(rate, fmax((fabs(U) + cs) * ihx, (fabs(V) + cs) * ihy));
-  numax = fmax(numax, mu / r);
+  numax = fmax(numax, mu * ir);
 }
 
 template <class R>

@@ -124,6 +124,33 @@ def test_members_equal_single_runs_cfl(precision):
             assert_close(member_state(ens, m), ref, precision, m)
 
 
+def hypersonic_strip():
+    """Mach ~250 flow (p/E ~ 1e-5): FP32 estimates of the sound speed are
+    unreliable here, so the mixed CFL screening must evaluate these nodes."""
+    import math
+
+    def prim(x, y):
+        return (1.0 + 0.1 * np.sin(2 * math.pi * x), 30.0 + np.sin(2 * math.pi * y), 0.5 + 0 * x,
+                0.01 * (1.0 + 0.5 * np.cos(2 * math.pi * x)))
+    return inputs.Case("hypersonic", 24, 8, 0.0, 1.0, 0.0, 1.0 / 3.0, (0, 0, 0, 0), prim=prim, tau_c1=0.05)
+
+
+@pytest.mark.parametrize("precision", [fdcgks.FP64, fdcgks.MIXED])
+def test_device_cfl_step_equals_host_formula(precision):
+    """The first CFL step of every member equals fdcgks_cfl_dt on the same
+    state (the mixed path screens nodes in FP32 and evaluates the candidates
+    in FP64: the maxima, hence dt, must still be those over all nodes)."""
+    cases = members() + [hypersonic_strip(), inputs.viscous_shock_tube(40, 20), inputs.sod_strip(64, 3)]
+    with make_ensemble(cases, precision) as ens:
+        ens.run(1, cfl=0.37)
+        _, last, st = ens.status()
+    for m, c in enumerate(cases):
+        with fdcgks.Solver.from_case(c, precision) as s:
+            s.set_state(*c.initial_state())
+            ref = s.cfl_dt(0.37)
+        assert last[m] == pytest.approx(ref, rel=1e-15), (m, last[m], ref)
+
+
 def test_member_matches_oracle():
     cases = members()
     dts = fixed_dts(cases)
@@ -177,14 +204,16 @@ def test_profile_advances_like_run():
             assert_same(member_state(a, m), member_state(b, m), m)
 
 
-def test_launch_count():
+@pytest.mark.parametrize("precision,cfl_kernels", [(fdcgks.FP64, 1), (fdcgks.MIXED, 2)])
+def test_launch_count(precision, cfl_kernels):
+    """Per step: CFL pass(es), the time-step kernel, then 5 phases per stage."""
     cases = members()[:3]
-    with make_ensemble(cases, fdcgks.FP64) as ens:
+    with make_ensemble(cases, precision) as ens:
         n0 = ens.launches()
         ens.run(3, cfl=0.4)
         ens.run(2, dt=[1e-3] * 3)
         ens.synchronize()
-        assert ens.launches() - n0 == 3 * 12 + 2 * 11
+        assert ens.launches() - n0 == 3 * (cfl_kernels + 11) + 2 * 11
 
 
 def test_blown_up_member_is_frozen_and_others_continue():
