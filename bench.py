@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--ens-steps", type=int, default=200)
     ap.add_argument("--ens-nmax", type=int, default=512, help="largest ensemble grid")
     ap.add_argument("--ens-no-tune", action="store_true", help="default tiles (profiling runs)")
+    ap.add_argument("--no-viscous-tube", action="store_true")
+    ap.add_argument("--vt-steps", type=int, default=100, help="timed steps of the viscous shock tube window")
     ap.add_argument("--ensemble-only", action="store_true",
                     help="run only the ensemble workload and print its object (profiling runs)")
     return ap.parse_args()
@@ -309,6 +311,37 @@ def run_ensemble(args, world, rank, local):
     }
 
 
+def run_viscous_tube(args, world):
+    """Viscous shock tube (Sec. 5.8) at 1000 x 500: throughput of a window of
+    steps after the first CFL steps, FP64 and mixed (the time step held at the
+    CFL value at the start of the window)."""
+    import torch
+    from paper_2606_17772_gb300 import fdcgks, inputs
+    case = inputs.viscous_shock_tube(1000, 500)
+    nodes = case.nx * case.ny + case.nxd * case.nyd
+    out = {"config": {"workload": "viscous shock tube, [0,1]x[0,0.5], 1000x500 (+1001x501 dual), Re 200, "
+                                  "Pr 0.73, no-slip walls, symmetry top; window after 10 CFL-0.4 steps",
+                      "node_updates_per_step": nodes}}
+    for name, prec, k in (("fp64", fdcgks.FP64, args.vt_steps), ("mixed", fdcgks.MIXED, 10 * args.vt_steps)):
+        with fdcgks.Solver.from_case(case, prec) as s:
+            s.set_state(*case.initial_state())
+            for _ in range(10):
+                s.step(s.cfl_dt(0.4))
+            dt = s.cfl_dt(0.4)
+            torch.cuda.synchronize()
+            barrier(world)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s.steps(dt, k)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = max_over_ranks(e0.elapsed_time(e1), world)
+            bad = s.check()
+        out[name] = {"value": nodes * k * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / k, "steps": k,
+                     "dt": dt, "nonphysical": bool(bad)}
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -424,6 +457,8 @@ def main():
 
     if not args.no_ensemble:
         line["ensemble"] = run_ensemble(args, world, rank, local)
+    if not args.no_viscous_tube:
+        line["viscous_tube"] = run_viscous_tube(args, world)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ns, nst = 128, 2

@@ -39,6 +39,9 @@
 //     corners; n dual nodes per periodic direction, n+1 per bounded one.
 //     Ghost layers by periodic wrap, mirror (symmetry / no-slip wall) or
 //     constant extrapolation (transmissive).
+//   * Positivity safeguard (the paper describes none): a reconstructed
+//     interface state with non-positive density or pressure falls back to the
+//     adjacent node's state with zero normal slope, and chi = 0 there.
 //
 // Parity unpinned: the form and constants of the collision time tau and the
 // choice tau_0 = tau are exercised by no number the paper prints (its
@@ -694,6 +697,30 @@ void recon_line(const GenoConst& gc, const double Q[4][4], const double Qx[4][4]
   *chi = std::fmin(chil, chir);
 }
 
+// Positivity safeguard (the paper describes none; the build's reading): a
+// reconstructed interface state with non-positive (or non-finite) density or
+// pressure is replaced by the state of the node on its side of the interface
+// with zero normal slope (first order), and the interface's flux weight chi
+// is set to 0, so that its compact flux falls back to the low-order form.
+// Smooth data never triggers it.
+// rho > 0 and p = (gamma - 1)(E - (m_x^2 + m_y^2)/(2 rho)) > 0, i.e. 2 E rho > m^2
+// (gamma > 1), both finite; NaN fails every comparison
+bool physical_state(const double W[4]) {
+  return W[0] > 0.0 && 2.0 * W[3] * W[0] > W[1] * W[1] + W[2] * W[2] && W[0] < INFINITY && W[3] < INFINITY;
+}
+
+void positivity_fallback(const double Q[4][4], double Wl[4], double Wr[4], double Wln[4], double Wrn[4],
+                         double* chi) {
+  if (!physical_state(Wl)) {
+    for (int c = 0; c < 4; ++c) { Wl[c] = Q[1][c]; Wln[c] = 0.0; }
+    *chi = 0.0;
+  }
+  if (!physical_state(Wr)) {
+    for (int c = 0; c < 4; ++c) { Wr[c] = Q[2][c]; Wrn[c] = 0.0; }
+    *chi = 0.0;
+  }
+}
+
 // both solves at one virtual-interface point (Sec. 4 item 1, App. A3).
 // line 0: the grid whose interface normal is `n0`; line 1: the other grid,
 // normal n1 = 1 - n0.
@@ -704,6 +731,8 @@ PointOut point_solve(const Gas& gas, const GenoConst& gc, double dt, int n0, con
   double Wl1[4], Wr1[4], Wl1n[4], Wr1n[4], chi1;
   recon_line(gc, Q0, Q0x, h0, Wl0, Wr0, Wl0n, Wr0n, &chi0);
   recon_line(gc, Q1, Q1x, h1, Wl1, Wr1, Wl1n, Wr1n, &chi1);
+  positivity_fallback(Q0, Wl0, Wr0, Wl0n, Wr0n, &chi0);
+  positivity_fallback(Q1, Wl1, Wr1, Wl1n, Wr1n, &chi1);
   double t0[4], t1[4];
   for (int c = 0; c < 4; ++c) {
     t0[c] = 0.5 * (Wl1n[c] + Wr1n[c]);   // tangential derivative for solve 0

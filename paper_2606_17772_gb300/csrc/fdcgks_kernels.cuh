@@ -116,6 +116,39 @@ FD_HD void recon_line(const GenoK<R>& geno, const R* S, long plane, long c0, lon
   }
 }
 
+// Positivity safeguard of the interface states (the paper describes none): a
+// reconstructed state with non-positive or non-finite density or pressure
+// (rho > 0 and 2 E rho > m_x^2 + m_y^2 fail) is replaced by the state of the
+// node on its side (line entries 1 and 2, at e1 and e2) with zero normal
+// slope, and the interface's chi by 0, so its compact flux takes the
+// low-order form.  Never triggered by smooth data.
+template <class R>
+FD_HD bool physical_state(const R W[4]) {
+  return W[0] > R(0) && R(2) * W[3] * W[0] > W[1] * W[1] + W[2] * W[2] && W[0] < R(INFINITY) &&
+         W[3] < R(INFINITY);
+}
+
+template <class R>
+FD_HD void positivity_fallback(const R* S, long plane, long e1, long e2, R vl[4], R dl[4], R vr[4], R dr[4],
+                               R& chi) {
+  if (!physical_state(vl)) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      vl[c] = S[(long)c * plane + e1];
+      dl[c] = R(0);
+    }
+    chi = R(0);
+  }
+  if (!physical_state(vr)) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      vr[c] = S[(long)c * plane + e2];
+      dr[c] = R(0);
+    }
+    chi = R(0);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // virtual-interface points (Sec. 4 item 1; App. A3).
 // TYPE 0 = point A (i+1/2, j): primary x-interface, dual y-interface of dual column i+1
@@ -136,10 +169,14 @@ __device__ __forceinline__ void point_body(const KArgs<R>& a, int i, int j) {
     // primary nodes (i-1..i+2, j) along x; dual nodes (i+1, j-1..j+2) along y
     recon_line(a.geno, SP, L.plane, cell(L, i - 1, j), 1, 4, a.h[0], a.ih[0], l0v, l0d, r0v, r0d, chi0);
     recon_line(a.geno, SD, L.plane, cell(L, i + 1, j - 1), L.pitch, 8, a.h[1], a.ih[1], l1v, l1d, r1v, r1d, chi1);
+    positivity_fallback(SP, L.plane, cell(L, i, j), cell(L, i + 1, j), l0v, l0d, r0v, r0d, chi0);
+    positivity_fallback(SD, L.plane, cell(L, i + 1, j), cell(L, i + 1, j + 1), l1v, l1d, r1v, r1d, chi1);
   } else {
     // primary nodes (i, j-1..j+2) along y; dual nodes (i-1..i+2, j+1) along x
     recon_line(a.geno, SP, L.plane, cell(L, i, j - 1), L.pitch, 8, a.h[1], a.ih[1], l0v, l0d, r0v, r0d, chi0);
     recon_line(a.geno, SD, L.plane, cell(L, i - 1, j + 1), 1, 4, a.h[0], a.ih[0], l1v, l1d, r1v, r1d, chi1);
+    positivity_fallback(SP, L.plane, cell(L, i, j), cell(L, i, j + 1), l0v, l0d, r0v, r0d, chi0);
+    positivity_fallback(SD, L.plane, cell(L, i, j + 1), cell(L, i + 1, j + 1), l1v, l1d, r1v, r1d, chi1);
   }
   // tangential derivative of each solve: mean of the other line's l/r derivatives
   R t0[4], t1[4];

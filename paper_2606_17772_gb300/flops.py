@@ -135,8 +135,9 @@ def step_counts(case, state, dt, precision=0, nsample=4000, seed=0):
 
     # glue of the point kernel: tangential derivatives (16) + W~ combination
     # (12 per component for the time derivatives, 12 more for the values at stage 1)
-    point1 = comb((rec_i, 8), (solve, 2), (glue(16 + 4 * 24, 0), 1))
-    point2 = comb((rec_i, 8), (solve, 2), (glue(16 + 4 * 12, 0), 1))
+    # + the positivity check of the four reconstructed states (5 each)
+    point1 = comb((rec_i, 8), (solve, 2), (glue(16 + 4 * 24 + 20, 0), 1))
+    point2 = comb((rec_i, 8), (solve, 2), (glue(16 + 4 * 12 + 20, 0), 1))
     node = comb((rec_n, 8), (nodal, 1))
     # update kernel per node: stage 1 evaluates 8 compact fluxes per component
     # (F, F_t in x and y at both faces), 18 operator/gradient flops in the compute

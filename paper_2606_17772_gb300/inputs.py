@@ -166,6 +166,20 @@ def sod_strip(nx=200, ny=4, **kw):
     return Case("sod_strip", nx, ny, 0.0, 1.0, 0.0, ny * h, (1, 1, 0, 0), prim=prim, **kw)
 
 
+def strong_shock_strip(nx=200, ny=1, gamma=1.4, **kw):
+    """1-D Riemann problem with the viscous shock tube's states (Sec. 5.8), inviscid, on a
+    y-periodic strip with transmissive x ends: (rho, U, p) = (120, 0, 120/gamma) for x < 0.5
+    and (1.2, 0, 1.2/gamma) for x >= 0.5 (density and pressure ratio 100)."""
+    h = 1.0 / nx
+
+    def prim(x, y):
+        right = x >= 0.5
+        rho = np.where(right, 1.2, 120.0)
+        return rho, 0.0, 0.0, rho / gamma
+    kw.setdefault("tau_c2", 1.0)
+    return Case("strong_shock_strip", nx, ny, 0.0, 1.0, 0.0, ny * h, (1, 1, 0, 0), gamma=gamma, prim=prim, **kw)
+
+
 def viscous_shock_tube(nx=1000, ny=500, gamma=1.4, mu=0.005, Pr=0.73, **kw):
     """Sec. 5.8: [0,1] x [0,0.5], diaphragm x = 0.5, (120,0,0,120/gamma) | (1.2,0,0,1.2/gamma).
 
