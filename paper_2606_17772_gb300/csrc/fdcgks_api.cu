@@ -51,6 +51,23 @@ static char g_err[512] = "";
 
 void fdk::set_global_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
 
+bool fdk::ctx_view(fdcgks_t c, CtxView* v) {
+  if (!c || !v) return false;
+  v->p = c->p;
+  v->L = c->L;
+  v->hx = c->hx;
+  v->hy = c->hy;
+  v->stream = c->stream;
+  v->S = c->S;
+  v->has_state = c->has_state;
+  return true;
+}
+
+void fdk::ctx_set_error(fdcgks_t c, const char* msg) {
+  if (c) snprintf(c->err, sizeof(c->err), "%s", msg);
+  else set_global_error(msg);
+}
+
 static fdcgks_status fail(fdcgks_t c, fdcgks_status s, const char* fmt, ...) {
   char* dst = c ? c->err : g_err;
   va_list ap;

@@ -105,32 +105,49 @@ struct KArgs {
 // constant extrapolation with zero gradients (transmissive).  Work item idx
 // covers (row or column t, side, layer k); dir 0 fills x ghosts of interior
 // rows, dir 1 y ghosts of all columns (so corners are consistent).
-template <class T>
-__device__ __forceinline__ void ghost_body(T* S, const Layout& L, int bc0, int bc1, int dir, int g, int idx) {
+// ghost_map gives the ghost cell, its source cell and the boundary kind of
+// item idx (false when idx is out of range); ghost_sign the parity of field
+// component c (of W and of the x- and y-gradients; 0 = set to zero).
+FD_HD bool ghost_map(const Layout& L, int bc0, int bc1, int dir, int g, int idx, long& gc, long& sc, int& b) {
   const int nxg = g == 0 ? L.nx : L.nxd, nyg = g == 0 ? L.ny : L.nyd;
   const int n = dir == 0 ? nxg : nyg;
   const int tcount = dir == 0 ? nyg : nxg + 2 * GH;
   const int toff = dir == 0 ? 0 : -GH;
-  if (idx < 0 || idx >= tcount * 2 * GH) return;
+  if (idx < 0 || idx >= tcount * 2 * GH) return false;
   const int k = 1 + idx % GH;
   const int side = (idx / GH) % 2;
   const int t = idx / (2 * GH) + toff;
-  const int b = side == 0 ? bc0 : bc1;
+  b = side == 0 ? bc0 : bc1;
   const int ghost = side == 0 ? -k : n - 1 + k;
   int src;
   if (b == 0) src = ((ghost % n) + n) % n;                 // periodic, also for n < GH
   else if (b == 1) src = side == 0 ? 0 : n - 1;            // transmissive
   else if (g == 0) src = side == 0 ? k - 1 : n - k;        // mirror about the boundary line
   else src = side == 0 ? k : n - 1 - k;
-  const long gc = dir == 0 ? cell(L, ghost, t) : cell(L, t, ghost);
-  const long sc = dir == 0 ? cell(L, src, t) : cell(L, t, src);
+  gc = dir == 0 ? cell(L, ghost, t) : cell(L, t, ghost);
+  sc = dir == 0 ? cell(L, src, t) : cell(L, t, src);
+  return true;
+}
+
+FD_HD void ghost_sign(int b, int dir, int c, int& sW, int& sgx, int& sgy) {
+  if (b == 0) { sW = sgx = sgy = 1; return; }
+  if (b == 1) { sW = 1; sgx = sgy = 0; return; }
+  sW = 1;
+  if (c == 1 + dir) sW = -1;
+  if (c == 2 - dir && b == 3) sW = -1;
+  sgx = dir == 0 ? -sW : sW;
+  sgy = dir == 1 ? -sW : sW;
+}
+
+template <class T>
+__device__ __forceinline__ void ghost_body(T* S, const Layout& L, int bc0, int bc1, int dir, int g, int idx) {
+  long gc, sc;
+  int b;
+  if (!ghost_map(L, bc0, bc1, dir, g, idx, gc, sc, b)) return;
   T* Sg = S + (long)g * NFLD * L.plane;
   for (int c = 0; c < 4; ++c) {
-    T sW = 1;
-    if (b == 2 || b == 3) {
-      if (c == 1 + dir) sW = -1;
-      if (c == 2 - dir && b == 3) sW = -1;
-    }
+    int sW, sgx, sgy;
+    ghost_sign(b, dir, c, sW, sgx, sgy);
     T w = Sg[(long)c * L.plane + sc];
     T gx = Sg[(long)(4 + c) * L.plane + sc];
     T gy = Sg[(long)(8 + c) * L.plane + sc];
@@ -138,9 +155,9 @@ __device__ __forceinline__ void ghost_body(T* S, const Layout& L, int bc0, int b
       gx = 0;
       gy = 0;
     } else if (b != 0) {
-      w *= sW;
-      gx *= (dir == 0 ? -sW : sW);
-      gy *= (dir == 1 ? -sW : sW);
+      w *= (T)sW;
+      gx *= (T)sgx;
+      gy *= (T)sgy;
     }
     Sg[(long)c * L.plane + gc] = w;
     Sg[(long)(4 + c) * L.plane + gc] = gx;
@@ -152,6 +169,18 @@ enum { UPD_STAGE1 = 0, UPD_STAGE2 = 1, UPD_OPERATOR = 2 };
 
 // message returned by fdcgks_last_error(NULL)
 void set_global_error(const char* msg);
+
+// what other translation units of the library see of a context
+struct CtxView {
+  fdcgks_params p;
+  Layout L;
+  double hx, hy;
+  cudaStream_t stream;
+  double* S;        // FP64 state [2][12][plane] (the state itself on the FP64 path)
+  bool has_state;
+};
+bool ctx_view(fdcgks_t c, CtxView* v);
+void ctx_set_error(fdcgks_t c, const char* msg);
 
 // validation of user parameters (nullptr when valid)
 const char* check_params(const fdcgks_params* p);

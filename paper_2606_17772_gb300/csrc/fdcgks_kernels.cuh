@@ -60,6 +60,40 @@ __device__ __noinline__ void iface_solve_call(const GasK<R>& gas, int normal, co
 // nodal reconstruction and flux (Sec. 4 item 2; Sec. 2.1 nodal fluxes)
 // one thread per node, nodes i in [-1, n_x], j in [-1, n_y] of grid blockIdx.z
 // ---------------------------------------------------------------------------
+// One node: GENO node derivatives along x and y, then the nodal flux.
+// ld(e, f): field f (0-3 W, 4-7 x-gradient, 8-11 y-gradient) of node e (0 the
+// node, 1/2 its x neighbours -/+, 3/4 its y neighbours -/+); st(k, v): output
+// k (F[4], G[4], F_t[4], G_t[4]).  Shared by the kernel (loads from the state)
+// and its adjoint (seeded dual numbers).
+template <class R, class LD, class ST>
+FD_HD void nodal_compute(const GenoK<R>& geno, const GasK<R>& gas, const R h[2], const R ih[2], LD ld, ST st) {
+  R W[4], Wx[4], Wy[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    W[c] = ld(0, c);
+    R qx[3] = {ld(1, c), W[c], ld(2, c)};
+    R gxv[3] = {ld(1, 4 + c), ld(0, 4 + c), ld(2, 4 + c)};
+    Wx[c] = recon_node(geno, qx, gxv, h[0], ih[0]);
+    R qy[3] = {ld(3, c), W[c], ld(4, c)};
+    R gyv[3] = {ld(3, 8 + c), ld(0, 8 + c), ld(4, 8 + c)};
+    Wy[c] = recon_node(geno, qy, gyv, h[1], ih[1]);
+  }
+  R F[4], G[4], Ft[4], Gt[4];
+  nodal_flux(gas, W, Wx, Wy, F, G, Ft, Gt);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    st(c, F[c]);
+    st(4 + c, G[c]);
+    st(8 + c, Ft[c]);
+    st(12 + c, Gt[c]);
+  }
+}
+
+// offset of node e of the nodal stencil (see nodal_compute) from the node
+FD_HD long nodal_offset(const Layout& L, int e) {
+  return e == 0 ? 0 : e == 1 ? -1 : e == 2 ? 1 : e == 3 ? -(long)L.pitch : (long)L.pitch;
+}
+
 template <class R>
 __device__ __forceinline__ void nodal_body(const KArgs<R>& a, int g, int i, int j) {
   const Layout& L = a.L;
@@ -67,30 +101,10 @@ __device__ __forceinline__ void nodal_body(const KArgs<R>& a, int g, int i, int 
   if (i < -1 || j < -1 || i > nxg || j > nyg) return;
   const R* S = a.Sr + (long)g * NFLD * L.plane;
   const long c0 = cell(L, i, j);
-  R W[4], Wx[4], Wy[4];
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const R* f = S + (long)c * L.plane;
-    const R* gx = S + (long)(4 + c) * L.plane;
-    const R* gy = S + (long)(8 + c) * L.plane;
-    W[c] = (R)f[c0];
-    R qx[3] = {(R)f[c0 - 1], W[c], (R)f[c0 + 1]};
-    R gxv[3] = {(R)gx[c0 - 1], (R)gx[c0], (R)gx[c0 + 1]};
-    Wx[c] = recon_node(a.geno, qx, gxv, a.h[0], a.ih[0]);
-    R qy[3] = {(R)f[c0 - L.pitch], W[c], (R)f[c0 + L.pitch]};
-    R gyv[3] = {(R)gy[c0 - L.pitch], (R)gy[c0], (R)gy[c0 + L.pitch]};
-    Wy[c] = recon_node(a.geno, qy, gyv, a.h[1], a.ih[1]);
-  }
-  R F[4], G[4], Ft[4], Gt[4];
-  nodal_flux(a.gas, W, Wx, Wy, F, G, Ft, Gt);
   R* NF = a.NF + (long)g * NNF * L.plane + c0;
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    NF[(long)c * L.plane] = F[c];
-    NF[(long)(4 + c) * L.plane] = G[c];
-    NF[(long)(8 + c) * L.plane] = Ft[c];
-    NF[(long)(12 + c) * L.plane] = Gt[c];
-  }
+  nodal_compute<R>(
+      a.geno, a.gas, a.h, a.ih, [&](int e, int f) -> R { return S[(long)f * L.plane + c0 + nodal_offset(L, e)]; },
+      [&](int k, R v) { NF[(long)k * L.plane] = v; });
 }
 
 template <class R>
@@ -98,43 +112,36 @@ __global__ void __launch_bounds__(128, PointTune<R>::nodal_minb) nodal_kernel(KA
   nodal_body(a, blockIdx.z, blockIdx.x * blockDim.x + threadIdx.x - 1, blockIdx.y * blockDim.y + threadIdx.y - 1);
 }
 
-// reconstruct one 4-point line of one grid at its virtual interface
-// (between entries 1 and 2): starting cell c0 (entry 0), stride between
-// entries, gradient field offset gfield (4: x-gradient, 8: y-gradient)
-template <class R>
-FD_HD void recon_line(const GenoK<R>& geno, const R* S, long plane, long c0, long stride, int gfield, R h,
-                      R ih, R vl[4], R dl[4], R vr[4], R dr[4], R& chi) {
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const R* f = S + (long)c * plane + c0;
-    const R* gr = S + (long)(gfield + c) * plane + c0;
-    R Q[4] = {(R)f[0], (R)f[stride], (R)f[2 * stride], (R)f[3 * stride]};
-    R Qx[4] = {(R)gr[0], (R)gr[stride], (R)gr[2 * stride], (R)gr[3 * stride]};
-    R cl, cr;
-    recon_interface(geno, Q, Qx, h, ih, vl[c], dl[c], cl, vr[c], dr[c], cr);
-    if (c == 0) chi = s_min(cl, cr);   // chi_{j+1/2} = min(chi^{l,rho}, chi^{r,rho})
-  }
-}
-
 // Positivity safeguard of the interface states (the paper describes none): a
 // reconstructed state with non-positive or non-finite density or pressure
 // (rho > 0 and 2 E rho > m_x^2 + m_y^2 fail) is replaced by the state of the
-// node on its side (line entries 1 and 2, at e1 and e2) with zero normal
-// slope, and the interface's chi by 0, so its compact flux takes the
-// low-order form.  Never triggered by smooth data.
+// node on its side (line entries 1 and 2) with zero normal slope, and the
+// interface's chi by 0, so its compact flux takes the low-order form.
+// Never triggered by smooth data.
 template <class R>
 FD_HD bool physical_state(const R W[4]) {
   return W[0] > R(0) && R(2) * W[3] * W[0] > W[1] * W[1] + W[2] * W[2] && W[0] < R(INFINITY) &&
          W[3] < R(INFINITY);
 }
 
-template <class R>
-FD_HD void positivity_fallback(const R* S, long plane, long e1, long e2, R vl[4], R dl[4], R vr[4], R dr[4],
-                               R& chi) {
+// Reconstruct one 4-point line at its virtual interface (between entries 1
+// and 2), with the safeguard above.  ld(l, e, f) = field f (0-3 W, 4-7 the
+// averaged gradient along the line) of entry e (0-3) of line l.
+template <class R, class LD>
+FD_HD void recon_line_ld(const GenoK<R>& geno, LD ld, int l, R h, R ih, R vl[4], R dl[4], R vr[4], R dr[4],
+                         R& chi) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    R Q[4] = {ld(l, 0, c), ld(l, 1, c), ld(l, 2, c), ld(l, 3, c)};
+    R Qx[4] = {ld(l, 0, 4 + c), ld(l, 1, 4 + c), ld(l, 2, 4 + c), ld(l, 3, 4 + c)};
+    R cl, cr;
+    recon_interface(geno, Q, Qx, h, ih, vl[c], dl[c], cl, vr[c], dr[c], cr);
+    if (c == 0) chi = s_min(cl, cr);   // chi_{j+1/2} = min(chi^{l,rho}, chi^{r,rho})
+  }
   if (!physical_state(vl)) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      vl[c] = S[(long)c * plane + e1];
+      vl[c] = ld(l, 1, c);
       dl[c] = R(0);
     }
     chi = R(0);
@@ -142,11 +149,86 @@ FD_HD void positivity_fallback(const R* S, long plane, long e1, long e2, R vl[4]
   if (!physical_state(vr)) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      vr[c] = S[(long)c * plane + e2];
+      vr[c] = ld(l, 2, c);
       dr[c] = R(0);
     }
     chi = R(0);
   }
+}
+
+// One virtual-interface point: the two line reconstructions (with the
+// safeguard), the tangential derivatives, the two kinetic solves and the W~
+// combination.  ld(l, e, f) as for recon_line_ld, line 0 being the
+// primary-grid line (normal TYPE, spacing h[TYPE]) and line 1 the dual-grid
+// line (normal 1 - TYPE); st(k, v): output k (PO_* of solve 0, NPS + PO_* of
+// solve 1; F and W~ values only when wn).  Shared by the kernel and its adjoint.
+template <class R, int TYPE, class LD, class ST>
+FD_HD void point_compute(const GenoK<R>& geno, const GasK<R>& gas, const R h[2], const R ih[2], bool wn, LD ld,
+                         ST st) {
+  const int n0 = TYPE;        // normal of the primary-grid solve
+  R l0v[4], l0d[4], r0v[4], r0d[4], chi0;
+  R l1v[4], l1d[4], r1v[4], r1d[4], chi1;
+  recon_line_ld(geno, ld, 0, h[n0], ih[n0], l0v, l0d, r0v, r0d, chi0);
+  recon_line_ld(geno, ld, 1, h[1 - n0], ih[1 - n0], l1v, l1d, r1v, r1d, chi1);
+  // tangential derivative of each solve: mean of the other line's l/r derivatives
+  R t0[4], t1[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    t0[c] = R(0.5) * (l1d[c] + r1d[c]);
+    t1[c] = R(0.5) * (l0d[c] + r0d[c]);
+  }
+  IfaceOut<R> o0, o1;
+  if constexpr (PointTune<R>::noinline) {
+    iface_solve_call(gas, n0, l0v, r0v, l0d, r0d, t0, wn, o0);
+    iface_solve_call(gas, 1 - n0, l1v, r1v, l1d, r1d, t1, wn, o1);
+  } else {
+    iface_solve(gas, n0, l0v, r0v, l0d, r0d, t0, wn, o0);
+    iface_solve(gas, 1 - n0, l1v, r1v, l1d, r1d, t1, wn, o1);
+  }
+  // W~ of Eq. (eq:W-model-2d): half of the own solve plus a quarter of each side of the other
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    R m1t = R(0.25) * (o1.Wlt[c] + o1.Wrt[c]), m0t = R(0.25) * (o0.Wlt[c] + o0.Wrt[c]);
+    st(PO_FT + c, o0.Ft[c]);
+    st(PO_WLT + c, R(0.5) * o0.Wlt[c] + m1t);
+    st(PO_WRT + c, R(0.5) * o0.Wrt[c] + m1t);
+    st(NPS + PO_FT + c, o1.Ft[c]);
+    st(NPS + PO_WLT + c, R(0.5) * o1.Wlt[c] + m0t);
+    st(NPS + PO_WRT + c, R(0.5) * o1.Wrt[c] + m0t);
+    if (wn) {
+      R m1 = R(0.25) * (o1.Wl[c] + o1.Wr[c]), m0 = R(0.25) * (o0.Wl[c] + o0.Wr[c]);
+      st(PO_F + c, o0.F[c]);
+      st(PO_WL + c, R(0.5) * o0.Wl[c] + m1);
+      st(PO_WR + c, R(0.5) * o0.Wr[c] + m1);
+      st(NPS + PO_F + c, o1.F[c]);
+      st(NPS + PO_WL + c, R(0.5) * o1.Wl[c] + m0);
+      st(NPS + PO_WR + c, R(0.5) * o1.Wr[c] + m0);
+    }
+  }
+  st(PO_CHI, chi0);
+  st(NPS + PO_CHI, chi1);
+}
+
+// Where the lines of point (i, j) lie in the padded state: entry e of line l
+// is at base[l] + e * stride[l] of grid l (primary 0, dual 1), its gradient
+// along the line in fields gfield[l]..gfield[l] + 3.
+struct PointLines {
+  long base[2], stride[2];
+  int gfield[2];
+};
+template <int TYPE>
+FD_HD PointLines point_lines(const Layout& L, int i, int j) {
+  PointLines p;
+  if (TYPE == 0) {
+    // primary nodes (i-1..i+2, j) along x; dual nodes (i+1, j-1..j+2) along y
+    p.base[0] = cell(L, i - 1, j); p.stride[0] = 1; p.gfield[0] = 4;
+    p.base[1] = cell(L, i + 1, j - 1); p.stride[1] = L.pitch; p.gfield[1] = 8;
+  } else {
+    // primary nodes (i, j-1..j+2) along y; dual nodes (i-1..i+2, j+1) along x
+    p.base[0] = cell(L, i, j - 1); p.stride[0] = L.pitch; p.gfield[0] = 8;
+    p.base[1] = cell(L, i - 1, j + 1); p.stride[1] = 1; p.gfield[1] = 4;
+  }
+  return p;
 }
 
 // ---------------------------------------------------------------------------
@@ -160,65 +242,17 @@ __device__ __forceinline__ void point_body(const KArgs<R>& a, int i, int j) {
   const int imax = TYPE == 0 ? L.nx : L.nxd;
   const int jmax = TYPE == 0 ? L.nyd : L.ny;
   if (i < -2 || j < -2 || i > imax || j > jmax) return;
-  const R* SP = a.Sr;
-  const R* SD = a.Sr + (long)NFLD * L.plane;
-  const int n0 = TYPE;        // normal of the primary-grid solve
-  R l0v[4], l0d[4], r0v[4], r0d[4], chi0;
-  R l1v[4], l1d[4], r1v[4], r1d[4], chi1;
-  if (TYPE == 0) {
-    // primary nodes (i-1..i+2, j) along x; dual nodes (i+1, j-1..j+2) along y
-    recon_line(a.geno, SP, L.plane, cell(L, i - 1, j), 1, 4, a.h[0], a.ih[0], l0v, l0d, r0v, r0d, chi0);
-    recon_line(a.geno, SD, L.plane, cell(L, i + 1, j - 1), L.pitch, 8, a.h[1], a.ih[1], l1v, l1d, r1v, r1d, chi1);
-    positivity_fallback(SP, L.plane, cell(L, i, j), cell(L, i + 1, j), l0v, l0d, r0v, r0d, chi0);
-    positivity_fallback(SD, L.plane, cell(L, i + 1, j), cell(L, i + 1, j + 1), l1v, l1d, r1v, r1d, chi1);
-  } else {
-    // primary nodes (i, j-1..j+2) along y; dual nodes (i-1..i+2, j+1) along x
-    recon_line(a.geno, SP, L.plane, cell(L, i, j - 1), L.pitch, 8, a.h[1], a.ih[1], l0v, l0d, r0v, r0d, chi0);
-    recon_line(a.geno, SD, L.plane, cell(L, i - 1, j + 1), 1, 4, a.h[0], a.ih[0], l1v, l1d, r1v, r1d, chi1);
-    positivity_fallback(SP, L.plane, cell(L, i, j), cell(L, i, j + 1), l0v, l0d, r0v, r0d, chi0);
-    positivity_fallback(SD, L.plane, cell(L, i, j + 1), cell(L, i + 1, j + 1), l1v, l1d, r1v, r1d, chi1);
-  }
-  // tangential derivative of each solve: mean of the other line's l/r derivatives
-  R t0[4], t1[4];
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    t0[c] = R(0.5) * (l1d[c] + r1d[c]);
-    t1[c] = R(0.5) * (l0d[c] + r0d[c]);
-  }
-  const bool wn = a.want_n != 0;
-  IfaceOut<R> o0, o1;
-  if (PointTune<R>::noinline) {
-    iface_solve_call(a.gas, n0, l0v, r0v, l0d, r0d, t0, wn, o0);
-    iface_solve_call(a.gas, 1 - n0, l1v, r1v, l1d, r1d, t1, wn, o1);
-  } else {
-    iface_solve(a.gas, n0, l0v, r0v, l0d, r0d, t0, wn, o0);
-    iface_solve(a.gas, 1 - n0, l1v, r1v, l1d, r1d, t1, wn, o1);
-  }
-
+  const PointLines pl = point_lines<TYPE>(L, i, j);
+  const R* S = a.Sr;
   R* P = (TYPE == 0 ? a.PA : a.PB) + pcell(L, i, j);
   const long pp = L.pplane;
-  // W~ of Eq. (eq:W-model-2d): half of the own solve plus a quarter of each side of the other
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    R m1t = R(0.25) * (o1.Wlt[c] + o1.Wrt[c]), m0t = R(0.25) * (o0.Wlt[c] + o0.Wrt[c]);
-    P[(PO_FT + c) * pp] = o0.Ft[c];
-    P[(PO_WLT + c) * pp] = R(0.5) * o0.Wlt[c] + m1t;
-    P[(PO_WRT + c) * pp] = R(0.5) * o0.Wrt[c] + m1t;
-    P[(NPS + PO_FT + c) * pp] = o1.Ft[c];
-    P[(NPS + PO_WLT + c) * pp] = R(0.5) * o1.Wlt[c] + m0t;
-    P[(NPS + PO_WRT + c) * pp] = R(0.5) * o1.Wrt[c] + m0t;
-    if (wn) {
-      R m1 = R(0.25) * (o1.Wl[c] + o1.Wr[c]), m0 = R(0.25) * (o0.Wl[c] + o0.Wr[c]);
-      P[(PO_F + c) * pp] = o0.F[c];
-      P[(PO_WL + c) * pp] = R(0.5) * o0.Wl[c] + m1;
-      P[(PO_WR + c) * pp] = R(0.5) * o0.Wr[c] + m1;
-      P[(NPS + PO_F + c) * pp] = o1.F[c];
-      P[(NPS + PO_WL + c) * pp] = R(0.5) * o1.Wl[c] + m0;
-      P[(NPS + PO_WR + c) * pp] = R(0.5) * o1.Wr[c] + m0;
-    }
-  }
-  P[PO_CHI * pp] = chi0;
-  P[(NPS + PO_CHI) * pp] = chi1;
+  point_compute<R, TYPE>(
+      a.geno, a.gas, a.h, a.ih, a.want_n != 0,
+      [&](int l, int e, int f) -> R {
+        const int field = f < 4 ? f : pl.gfield[l] + (f - 4);
+        return S[((long)l * NFLD + field) * L.plane + pl.base[l] + e * pl.stride[l]];
+      },
+      [&](int k, R v) { P[(long)k * pp] = v; });
 }
 
 template <class R, int TYPE>
