@@ -191,6 +191,31 @@ fdcgks_status fdcgks_recon_batch(const fdcgks_params* params, int kind, double h
 fdcgks_status fdcgks_cfl_dt_noalloc(const fdcgks_params* params, const double* Wp, const double* Wd, double cfl,
                                     double* dt_out);
 
+/* Adjoint of nsteps steps (reverse mode).  The paper has no counterpart: the
+ * gradient of a scalar objective J of the state after nsteps steps of size dt
+ * with respect to the initial state, for sensitivity studies and
+ * optimisation through the solver.
+ *   - Inputs (device arrays, the layouts of fdcgks_set_state): the initial
+ *     state Wp0, Gp0, Wd0, Gd0, and dJ/d(final state) aWp, aGp, aWd, aGd.
+ *   - Output (device arrays, same layouts): dJ/d(initial state) gWp, gGp,
+ *     gWd, gGd.  The derivative is that of the discrete FP64 step, taking at
+ *     every branch (GENO saturation, the positivity safeguard, the no-slip
+ *     reset) the one the forward took; at exact ties of min/max and at
+ *     |p_l - p_r| = 0 in tau it takes the mean of the one-sided derivatives.
+ *   - The context runs the nsteps steps from the initial state and keeps
+ *     the final state, as after fdcgks_set_state + fdcgks_steps.
+ *   - Memory: checkpoints every checkpoint_every steps; each segment's states
+ *     are recomputed from its checkpoint, each step's stage intermediates once
+ *     more before its reverse pass (about three forward sweeps in all).  The
+ *     call allocates a workspace of about ceil(nsteps / checkpoint_every) +
+ *     checkpoint_every + 20 padded states and frees it before returning.
+ *   - FP64 contexts only (FDCGKS_ERR_ARG otherwise).  Synchronizes the
+ *     context stream. */
+fdcgks_status fdcgks_vjp_steps(fdcgks_t ctx, double dt, int nsteps, int checkpoint_every, const double* Wp0,
+                               const double* Gp0, const double* Wd0, const double* Gd0, const double* aWp,
+                               const double* aGp, const double* aWd, const double* aGd, double* gWp, double* gGp,
+                               double* gWd, double* gGd);
+
 /* ------------------------------------------------------------------------
  * Batched ensemble.  The paper has no counterpart: its runs are independent,
  * and batching them is an execution strategy for parameter sweeps and

@@ -24,7 +24,8 @@ EXPORTS = ["fdcgks_create", "fdcgks_destroy", "fdcgks_dims", "fdcgks_set_state",
            "fdcgks_status_string", "fdcgks_set_profiling", "fdcgks_get_profile", "fdcgks_cfl_dt_noalloc",
            "fdcgks_ens_create", "fdcgks_ens_destroy", "fdcgks_ens_set_state", "fdcgks_ens_get_state",
            "fdcgks_ens_run", "fdcgks_ens_status", "fdcgks_ens_set_tiles", "fdcgks_ens_get_tiles",
-           "fdcgks_ens_tune", "fdcgks_ens_profile", "fdcgks_ens_info", "fdcgks_ens_last_error"]
+           "fdcgks_ens_tune", "fdcgks_ens_profile", "fdcgks_ens_info", "fdcgks_ens_last_error",
+           "fdcgks_vjp_steps"]
 
 ENS_NONPHYSICAL, ENS_NO_WAVE_SPEED, ENS_FROZEN = 1, 2, 4
 
@@ -101,6 +102,7 @@ def load(path=None):
     lib.fdcgks_ens_profile.argtypes = [_VP, ctypes.c_double, ctypes.c_int, _VP]
     lib.fdcgks_ens_info.argtypes = [_VP, ctypes.POINTER(_VP), ctypes.POINTER(ctypes.c_longlong),
                                     ctypes.POINTER(ctypes.c_longlong)]
+    lib.fdcgks_vjp_steps.argtypes = [_VP, ctypes.c_double, ctypes.c_int, ctypes.c_int] + [_VP] * 12
     lib.fdcgks_ens_last_error.argtypes = [_VP]
     lib.fdcgks_ens_last_error.restype = ctypes.c_char_p
     lib.fdcgks_last_error.argtypes = [_VP]
@@ -112,7 +114,7 @@ def load(path=None):
                  "fdcgks_nodal_batch", "fdcgks_recon_batch", "fdcgks_set_profiling", "fdcgks_get_profile",
                  "fdcgks_cfl_dt_noalloc", "fdcgks_ens_create", "fdcgks_ens_set_state", "fdcgks_ens_get_state",
                  "fdcgks_ens_run", "fdcgks_ens_status", "fdcgks_ens_set_tiles", "fdcgks_ens_get_tiles",
-                 "fdcgks_ens_tune", "fdcgks_ens_profile", "fdcgks_ens_info"):
+                 "fdcgks_ens_tune", "fdcgks_ens_profile", "fdcgks_ens_info", "fdcgks_vjp_steps"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -268,6 +270,20 @@ class Solver:
 
     def launches(self):
         return self.get_profile()[2]
+
+    def vjp_steps(self, dt, nsteps, state0, adj_final, checkpoint_every=50):
+        """dJ/d(initial state) for dJ/d(final state) `adj_final` after `nsteps`
+        steps of size dt from `state0` (both 4-tuples of CUDA float64 tensors in
+        the set_state layouts).  The solver keeps the final state."""
+        import torch
+        torch.cuda.current_stream().synchronize()
+        out = [torch.zeros(s, dtype=torch.float64, device="cuda") for s in self.shapes()]
+        sizes = [int(np.prod(s)) for s in self.shapes()]
+        ptrs = ([_dptr(a, n) for a, n in zip(state0, sizes)] + [_dptr(a, n) for a, n in zip(adj_final, sizes)] +
+                [_dptr(a, n) for a, n in zip(out, sizes)])
+        _check(load().fdcgks_vjp_steps(self._h, ctypes.c_double(dt), int(nsteps), int(checkpoint_every), *ptrs),
+               self._h)
+        return tuple(out)
 
     def stage_operator(self, dt):
         import torch
@@ -471,3 +487,45 @@ class Ensemble:
     def synchronize(self):
         import torch
         torch.cuda.ExternalStream(self.stream).synchronize()
+
+
+def _steps_function():
+    import torch
+
+    class StepsFunction(torch.autograd.Function):
+        """Differentiable n-step FD-CGKS map (FP64 contexts): forward runs the
+        library's steps, backward its adjoint (fdcgks_vjp_steps)."""
+
+        @staticmethod
+        def forward(ctx, Wp, Gp, Wd, Gd, solver, dt, nsteps, checkpoint_every):
+            state0 = tuple(t.detach().contiguous() for t in (Wp, Gp, Wd, Gd))
+            solver.set_state(*state0)
+            solver.steps(dt, nsteps)
+            out = solver.get_state()
+            torch.cuda.current_stream().synchronize()
+            ctx.solver, ctx.dt, ctx.nsteps, ctx.ck = solver, dt, nsteps, checkpoint_every
+            ctx.save_for_backward(*state0)
+            return out
+
+        @staticmethod
+        def backward(ctx, gWp, gGp, gWd, gGd):
+            state0 = ctx.saved_tensors
+            adj = []
+            for g, s in zip((gWp, gGp, gWd, gGd), state0):
+                adj.append(torch.zeros_like(s) if g is None else g.contiguous().to(torch.float64))
+            grads = ctx.solver.vjp_steps(ctx.dt, ctx.nsteps, state0, adj, ctx.ck)
+            return grads + (None, None, None, None)
+
+    return StepsFunction
+
+
+_STEPS_FN = None
+
+
+def steps_autograd(solver, Wp, Gp, Wd, Gd, dt, nsteps, checkpoint_every=50):
+    """(Wp, Gp, Wd, Gd) after nsteps steps, differentiable with torch.autograd
+    (the backward pass runs the library's adjoint kernels)."""
+    global _STEPS_FN
+    if _STEPS_FN is None:
+        _STEPS_FN = _steps_function()
+    return _STEPS_FN.apply(Wp, Gp, Wd, Gd, solver, dt, nsteps, checkpoint_every)
