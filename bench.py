@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--ens-no-tune", action="store_true", help="default tiles (profiling runs)")
     ap.add_argument("--no-viscous-tube", action="store_true")
     ap.add_argument("--vt-steps", type=int, default=100, help="timed steps of the viscous shock tube window")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adj-steps", type=int, default=20, help="steps of the adjoint window")
     ap.add_argument("--ensemble-only", action="store_true",
                     help="run only the ensemble workload and print its object (profiling runs)")
     return ap.parse_args()
@@ -342,6 +344,79 @@ def run_viscous_tube(args, world):
     return out
 
 
+def run_adjoint(args, world):
+    """Gradient of a density misfit after a window of steps of the 256^2 vortex
+    (strength 5) with respect to the primary initial state: forward and
+    adjoint (checkpoint every 50 steps) times, and the gradient along 2 random
+    unit directions against central differences on the linear-reconstruction,
+    c1-only collision time variant (where differences are in their linear
+    regime; with GENO's nonlinear weights the vortex far field is not)."""
+    import numpy as np
+    import torch
+    from paper_2606_17772_gb300 import fdcgks, inputs
+
+    def setup(case, nsteps):
+        S0 = [torch.from_numpy(a).cuda() for a in case.initial_state()]
+        rng = np.random.default_rng(1)
+        X, Y = case.node_xy(False)
+        bump = np.zeros_like(X)
+        for _ in range(8):
+            cx, cy = rng.uniform(0, 10, 2)
+            bump += np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (2 * 0.5 ** 2))
+        return S0, bump
+
+    out = {"config": {"workload": "isentropic vortex 256^2 (+dual), strength 5, %d steps (CFL 0.4 dt), "
+                                  "J = 1/2 sum (rho - rho_target)^2 h^2, target from rho + 8 Gaussian bumps "
+                                  "(sigma 0.5, amplitude 1e-3, seed 1); gradient w.r.t. primary W^0; "
+                                  "checkpoint every 50 steps" % args.adj_steps}}
+    for name, kw, ndir in (("geno", {}, 0), ("linear", dict(geno_variant=2, tau_c1=0.05, tau_c2=0.0), 2)):
+        case = inputs.vortex(256, strength=5.0, **kw)
+        S0, bump = setup(case, args.adj_steps)
+        h2 = case.hx * case.hy
+        n = args.adj_steps
+        with fdcgks.Solver.from_case(case) as s:
+            s.set_state(*S0)
+            dt = s.cfl_dt(0.4)
+            Wt = S0[0].clone()
+            Wt[0] += torch.from_numpy(1e-3 * bump).cuda()
+            s.set_state(Wt, *S0[1:])
+            s.steps(dt, n)
+            target = s.get_state()[0][0].clone()
+
+            def J(Wp0):
+                s.set_state(Wp0, *S0[1:])
+                s.steps(dt, n)
+                return 0.5 * float(((s.get_state()[0][0] - target) ** 2).sum()) * h2
+
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            J0 = J(S0[0])
+            torch.cuda.synchronize()
+            tf = time.perf_counter() - t0
+            fin = s.get_state()
+            seed = [torch.zeros_like(t) for t in S0]
+            seed[0][0] = (fin[0][0] - target) * h2
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g = s.vjp_steps(dt, n, S0, seed, checkpoint_every=50)
+            torch.cuda.synchronize()
+            ta = time.perf_counter() - t0
+            checks = []
+            drng = np.random.default_rng(2)
+            for _ in range(ndir):
+                d = torch.from_numpy(drng.standard_normal(S0[0].shape)).cuda()
+                d /= d.norm()
+                eps = 2.56e-6
+                fd = (J(S0[0] + eps * d) - J(S0[0] - eps * d)) / (2 * eps)
+                ad = float((g[0] * d).sum())
+                checks.append(abs(ad - fd) / abs(fd))
+        out[name] = {"J": J0, "dt": dt, "forward_ms_per_step": 1e3 * tf / n, "adjoint_ms_per_step": 1e3 * ta / n,
+                     "adjoint_over_forward": ta / tf, "gradient_norm": float(g[0].norm())}
+        if checks:
+            out[name]["fd_rel_err"] = checks
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -459,6 +534,8 @@ def main():
         line["ensemble"] = run_ensemble(args, world, rank, local)
     if not args.no_viscous_tube:
         line["viscous_tube"] = run_viscous_tube(args, world)
+    if not args.no_adjoint:
+        line["adjoint"] = run_adjoint(args, world)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ns, nst = 128, 2
