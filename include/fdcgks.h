@@ -81,6 +81,11 @@ typedef struct {
                                  at interfaces, c1 dt + mu/p at nodes (paper App. A cites the
                                  GKS literature for tau; these constants are run parameters) */
   void* stream;               /* cudaStream_t for all work; NULL = legacy default stream */
+  int recon_vars;             /* interface reconstruction (Sec. 3.1) on 0: conservative components
+                                 (default), 1: characteristic components along the interface normal
+                                 (eigenvectors of the Euler flux Jacobian at the mean of the two
+                                 adjacent nodes; chi of the flux from the U +- c fields, Sec. 3.2).
+                                 Single contexts only: the ensemble and the adjoint take 0. */
 } fdcgks_params;
 
 /* Create a context: validates params and allocates the device buffers of the

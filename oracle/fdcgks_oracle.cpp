@@ -24,7 +24,9 @@
 //     d=8 on the central sub-stencil); variant 2 = linear (chi = 1).
 //   * Node sub-stencils numbered as in Sec. 3.2 (central first).
 //   * GENO weights chi, omega_k are applied to the derivative as well.
-//   * Component-wise reconstruction of conservative variables.
+//   * Component-wise reconstruction of conservative variables (recon_vars 0,
+//     default) or of characteristic variables along the line's normal
+//     (recon_vars 1), the flux weight then from the U +- c fields.
 //   * tau_0 of Eq. (eq:W-model) = the interface collision time tau.
 //   * W^{l,r}(t) of Eq. (eq:W-model): free transport of the one-sided
 //     Chapman-Enskog distribution over the whole velocity space.
@@ -590,6 +592,7 @@ typedef struct {
   int geno_variant;     // 0 text, 1 App. D, 2 linear
   int grad_base;        // 0 reading B (re-evaluated), 1 reading A (stored)
   double tau_c1, tau_c2;
+  int recon_vars;       // 0 conservative components, 1 characteristic components
 } oracle_params;
 
 }  // extern "C"
@@ -721,16 +724,107 @@ void positivity_fallback(const double Q[4][4], double Wl[4], double Wr[4], doubl
   }
 }
 
+// Characteristic components (Sec. 3.1: "Q denote an arbitrary characteristic
+// component of W"; the choice of the U +- c fields for the flux weight,
+// Sec. 3.2).  The eigenvectors of the Euler flux Jacobian in the line's
+// normal direction, in the textbook form, frozen at the arithmetic mean of the
+// conservative states of the two entries next to the interface; variables
+// ordered (rho, normal momentum, tangential momentum, E).  Rows of L / columns
+// of R: the U - c field, entropy, shear, U + c.  ok = false when the mean
+// state is not physical (the line then falls back to conservative components).
+struct CharBasis {
+  double L[4][4], R[4][4];
+  int in, it;   // indices of the normal and tangential momenta in W
+  bool ok;
+};
+
+CharBasis char_basis(double gamma, int normal, const double Wa[4], const double Wb[4]) {
+  CharBasis b;
+  b.in = normal == 0 ? 1 : 2;
+  b.it = normal == 0 ? 2 : 1;
+  double r = 0.5 * (Wa[0] + Wb[0]);
+  double mn = 0.5 * (Wa[b.in] + Wb[b.in]), mt = 0.5 * (Wa[b.it] + Wb[b.it]);
+  double E = 0.5 * (Wa[3] + Wb[3]);
+  double u = mn / r, v = mt / r;
+  double p = (gamma - 1.0) * (E - 0.5 * r * (u * u + v * v));
+  b.ok = r > 0.0 && p > 0.0;
+  if (!b.ok) return b;
+  double c = std::sqrt(gamma * p / r), H = (E + p) / r, q2 = u * u + v * v;
+  double b1 = (gamma - 1.0) / (c * c), b2 = 0.5 * b1 * q2;
+  double L[4][4] = {{0.5 * (b2 + u / c), -0.5 * (b1 * u + 1.0 / c), -0.5 * b1 * v, 0.5 * b1},
+                    {1.0 - b2, b1 * u, b1 * v, -b1},
+                    {-v, 0.0, 1.0, 0.0},
+                    {0.5 * (b2 - u / c), -0.5 * (b1 * u - 1.0 / c), -0.5 * b1 * v, 0.5 * b1}};
+  double R[4][4] = {{1.0, 1.0, 0.0, 1.0},
+                    {u - c, u, 0.0, u + c},
+                    {v, v, 1.0, v},
+                    {H - u * c, 0.5 * q2, v, H + u * c}};
+  std::memcpy(b.L, L, sizeof(L));
+  std::memcpy(b.R, R, sizeof(R));
+  return b;
+}
+
+// the line reconstruction of recon_line on characteristic components: project
+// values and averaged gradients with L, reconstruct each component, map the
+// left/right values and derivatives back with R; chi of the flux is the
+// smaller of the two acoustic fields' chi
+void recon_line_char(const GenoConst& gc, double gamma, int normal, const double Q[4][4], const double Qx[4][4],
+                     double h, double Wl[4], double Wr[4], double Wlx[4], double Wrx[4], double* chi) {
+  CharBasis b = char_basis(gamma, normal, Q[1], Q[2]);
+  if (!b.ok) {
+    recon_line(gc, Q, Qx, h, Wl, Wr, Wlx, Wrx, chi);
+    return;
+  }
+  const int perm[4] = {0, b.in, b.it, 3};   // (rho, m_n, m_t, E) -> index in W
+  double C[4][4], Cx[4][4];                 // [entry][field]
+  for (int m = 0; m < 4; ++m)
+    for (int k = 0; k < 4; ++k) {
+      C[m][k] = 0.0;
+      Cx[m][k] = 0.0;
+      for (int j = 0; j < 4; ++j) {
+        C[m][k] += b.L[k][j] * Q[m][perm[j]];
+        Cx[m][k] += b.L[k][j] * Qx[m][perm[j]];
+      }
+    }
+  double vl[4], vr[4], dl[4], dr[4], cl[4], cr[4];
+  for (int k = 0; k < 4; ++k) {
+    double q[4] = {C[0][k], C[1][k], C[2][k], C[3][k]};
+    double gl[3] = {Cx[0][k], Cx[1][k], Cx[2][k]};
+    double gr[3] = {Cx[1][k], Cx[2][k], Cx[3][k]};
+    recon_left(gc, q, gl, h, &vl[k], &dl[k], &cl[k]);
+    recon_right(gc, q, gr, h, &vr[k], &dr[k], &cr[k]);
+  }
+  for (int j = 0; j < 4; ++j) {
+    double a = 0.0, bb = 0.0, d = 0.0, e = 0.0;
+    for (int k = 0; k < 4; ++k) {
+      a += b.R[j][k] * vl[k];
+      bb += b.R[j][k] * vr[k];
+      d += b.R[j][k] * dl[k];
+      e += b.R[j][k] * dr[k];
+    }
+    Wl[perm[j]] = a;
+    Wr[perm[j]] = bb;
+    Wlx[perm[j]] = d;
+    Wrx[perm[j]] = e;
+  }
+  *chi = std::fmin(std::fmin(cl[0], cr[0]), std::fmin(cl[3], cr[3]));
+}
+
 // both solves at one virtual-interface point (Sec. 4 item 1, App. A3).
 // line 0: the grid whose interface normal is `n0`; line 1: the other grid,
 // normal n1 = 1 - n0.
 PointOut point_solve(const Gas& gas, const GenoConst& gc, double dt, int n0, const double Q0[4][4],
                      const double Q0x[4][4], double h0, const double Q1[4][4], const double Q1x[4][4],
-                     double h1) {
+                     double h1, int recon_vars) {
   double Wl0[4], Wr0[4], Wl0n[4], Wr0n[4], chi0;
   double Wl1[4], Wr1[4], Wl1n[4], Wr1n[4], chi1;
-  recon_line(gc, Q0, Q0x, h0, Wl0, Wr0, Wl0n, Wr0n, &chi0);
-  recon_line(gc, Q1, Q1x, h1, Wl1, Wr1, Wl1n, Wr1n, &chi1);
+  if (recon_vars == 1) {
+    recon_line_char(gc, gas.gamma, n0, Q0, Q0x, h0, Wl0, Wr0, Wl0n, Wr0n, &chi0);
+    recon_line_char(gc, gas.gamma, 1 - n0, Q1, Q1x, h1, Wl1, Wr1, Wl1n, Wr1n, &chi1);
+  } else {
+    recon_line(gc, Q0, Q0x, h0, Wl0, Wr0, Wl0n, Wr0n, &chi0);
+    recon_line(gc, Q1, Q1x, h1, Wl1, Wr1, Wl1n, Wr1n, &chi1);
+  }
   positivity_fallback(Q0, Wl0, Wr0, Wl0n, Wr0n, &chi0);
   positivity_fallback(Q1, Wl1, Wr1, Wl1n, Wr1n, &chi1);
   double t0[4], t1[4];
@@ -842,7 +936,7 @@ StageOut stage(const Scheme& S, Grid& P, Grid& D, double dt) {
       double Q0[4][4], Q0n[4][4], Q1[4][4], Q1n[4][4];
       gather_line(P, i, j, 0, Q0, Q0n);          // primary (i-1..i+2, j)
       gather_line(D, i + 1, j, 1, Q1, Q1n);      // dual (i+1, j-1..j+2)
-      A.at(i, j) = point_solve(S.gas, S.gc, dt, 0, Q0, Q0n, S.hx, Q1, Q1n, S.hy);
+      A.at(i, j) = point_solve(S.gas, S.gc, dt, 0, Q0, Q0n, S.hx, Q1, Q1n, S.hy, S.p.recon_vars);
     }
   // Type B points (i, j+1/2): primary y-interface and dual x-interface of dual row j+1
   B.init(-2, nxd, -2, ny);
@@ -851,7 +945,7 @@ StageOut stage(const Scheme& S, Grid& P, Grid& D, double dt) {
       double Q0[4][4], Q0n[4][4], Q1[4][4], Q1n[4][4];
       gather_line(P, i, j, 1, Q0, Q0n);          // primary (i, j-1..j+2)
       gather_line(D, i, j + 1, 0, Q1, Q1n);      // dual (i-1..i+2, j+1)
-      B.at(i, j) = point_solve(S.gas, S.gc, dt, 1, Q0, Q0n, S.hy, Q1, Q1n, S.hx);
+      B.at(i, j) = point_solve(S.gas, S.gc, dt, 1, Q0, Q0n, S.hy, Q1, Q1n, S.hx, S.p.recon_vars);
     }
 
   StageOut so;
@@ -926,6 +1020,7 @@ bool make_scheme(const oracle_params* p, Scheme& S) {
     if (a != b) return false;
   }
   if ((p->bc[0] != OBC_PERIODIC && p->nx < 3) || (p->bc[2] != OBC_PERIODIC && p->ny < 3)) return false;
+  if (p->recon_vars != 0 && p->recon_vars != 1) return false;
   S.nxd = p->nx + (p->bc[0] == OBC_PERIODIC ? 0 : 1);
   S.nyd = p->ny + (p->bc[2] == OBC_PERIODIC ? 0 : 1);
   S.hx = (p->x1 - p->x0) / p->nx;
@@ -1151,6 +1246,24 @@ void oracle_recon_left(int variant, const double Q[4], const double Qx[3], doubl
 }
 void oracle_recon_right(int variant, const double Q[4], const double Qx[3], double h, double out[3]) {
   recon_right(geno_const(variant), Q, Qx, h, &out[0], &out[1], &out[2]);
+}
+// characteristic basis of a line (row-major L and R) and the line's
+// characteristic reconstruction: out = Wl[4], Wr[4], Wlx[4], Wrx[4], chi
+int oracle_char_basis(double gamma, int normal, const double Wa[4], const double Wb[4], double L[16], double R[16]) {
+  CharBasis b = char_basis(gamma, normal, Wa, Wb);
+  if (!b.ok) return 1;
+  std::memcpy(L, b.L, sizeof(b.L));
+  std::memcpy(R, b.R, sizeof(b.R));
+  return 0;
+}
+void oracle_recon_line(int variant, int recon_vars, double gamma, int normal, const double Q[16], const double Qx[16],
+                       double h, double out[17]) {
+  GenoConst gc = geno_const(variant);
+  double q[4][4], qx[4][4];
+  std::memcpy(q, Q, sizeof(q));
+  std::memcpy(qx, Qx, sizeof(qx));
+  if (recon_vars == 1) recon_line_char(gc, gamma, normal, q, qx, h, out, out + 4, out + 8, out + 12, out + 16);
+  else recon_line(gc, q, qx, h, out, out + 4, out + 8, out + 12, out + 16);
 }
 void oracle_recon_node(int variant, const double Q[3], const double Qx[3], double h, double out[2]) {
   recon_node(geno_const(variant), Q, Qx, h, &out[0], &out[1]);

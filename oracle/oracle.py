@@ -24,6 +24,7 @@ class OracleParams(ctypes.Structure):
         ("geno_variant", ctypes.c_int),
         ("grad_base", ctypes.c_int),
         ("tau_c1", ctypes.c_double), ("tau_c2", ctypes.c_double),
+        ("recon_vars", ctypes.c_int),
     ]
 
 
@@ -43,7 +44,7 @@ def lib():
 
 def make_params(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, mu=0.0, Pr=1.0,
                 bc=(0, 0, 0, 0), flux_variant=64, geno_variant=0, grad_base=0,
-                tau_c1=0.0, tau_c2=0.0):
+                tau_c1=0.0, tau_c2=0.0, recon_vars=0):
     p = OracleParams()
     p.nx, p.ny = nx, ny
     p.x0, p.x1, p.y0, p.y1 = x0, x1, y0, y1
@@ -52,6 +53,7 @@ def make_params(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, mu=0.0, Pr=1.
         p.bc[k] = bc[k]
     p.flux_variant, p.geno_variant, p.grad_base = flux_variant, geno_variant, grad_base
     p.tau_c1, p.tau_c2 = tau_c1, tau_c2
+    p.recon_vars = recon_vars
     return p
 
 
@@ -190,3 +192,20 @@ def nodal_flux(p, dt, W, Wx, Wy):
     lib().oracle_nodal_flux(ctypes.byref(p), ctypes.c_double(dt), _ptr(_arr(W, 4)), _ptr(_arr(Wx, 4)),
                             _ptr(_arr(Wy, 4)), _ptr(out))
     return {k: out[4 * i:4 * i + 4].copy() for i, k in enumerate(["F", "G", "Ft", "Gt"])}
+
+
+def char_basis(gamma, normal, Wa, Wb):
+    """(L, R) 4x4 characteristic basis of a line (None if the mean state is not physical)."""
+    L = np.zeros(16)
+    R = np.zeros(16)
+    rc = lib().oracle_char_basis(ctypes.c_double(gamma), int(normal), _ptr(_arr(Wa, 4)), _ptr(_arr(Wb, 4)),
+                                 _ptr(L), _ptr(R))
+    return None if rc else (L.reshape(4, 4), R.reshape(4, 4))
+
+
+def recon_line(variant, recon_vars, gamma, normal, Q, Qx, h):
+    """Line reconstruction from Q[4 entries][4 fields], Qx[4][4]: (Wl, Wr, Wlx, Wrx, chi)."""
+    out = np.zeros(17)
+    lib().oracle_recon_line(int(variant), int(recon_vars), ctypes.c_double(gamma), int(normal),
+                            _ptr(_arr(Q, 16)), _ptr(_arr(Qx, 16)), ctypes.c_double(h), _ptr(out))
+    return out[0:4], out[4:8], out[8:12], out[12:16], out[16]

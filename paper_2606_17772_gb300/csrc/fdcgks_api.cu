@@ -107,6 +107,7 @@ const char* fdk::check_params(const fdcgks_params* p) {
   if (p->grad_base != 0 && p->grad_base != 1) return "grad_base must be 0 or 1";
   if (p->precision != FDCGKS_FP64 && p->precision != FDCGKS_MIXED) return "precision must be 0 or 1";
   if (!(p->tau_c1 >= 0.0) || !(p->tau_c2 >= 0.0)) return "tau constants must be >= 0";
+  if (p->recon_vars != 0 && p->recon_vars != 1) return "recon_vars must be 0 or 1";
   return nullptr;
 }
 
@@ -272,6 +273,7 @@ static KArgs<R> make_args(fdcgks_t c, double dt, const double* S, double* Sout, 
   for (int k = 0; k < 4; ++k) a.bc[k] = c->p.bc[k];
   a.flux_variant = c->p.flux_variant;
   a.grad_base = c->p.grad_base;
+  a.recon_vars = c->p.recon_vars;
   a.want_n = want_n;
   a.dt = dt;
   a.flag = c->flag;

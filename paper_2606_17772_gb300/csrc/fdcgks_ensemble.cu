@@ -733,6 +733,8 @@ fdcgks_status fdcgks_ens_create(const fdcgks_params* params, int count, fdcgks_e
     if (const char* msg = check_params(params + m)) return efail(nullptr, FDCGKS_ERR_ARG, "member %d: %s", m, msg);
     if (params[m].precision != params[0].precision)
       return efail(nullptr, FDCGKS_ERR_ARG, "member %d: all members must share one precision", m);
+    if (params[m].recon_vars != 0)
+      return efail(nullptr, FDCGKS_ERR_ARG, "member %d: the ensemble reconstructs conservative components only", m);
   }
   fdcgks_ens_t e = new (std::nothrow) fdcgks_ens();
   if (!e) return efail(nullptr, FDCGKS_ERR_NOMEM, "host allocation failed");

@@ -94,6 +94,7 @@ struct KArgs {
   double hd[2], ihd[2];
   int bc[4];
   int flux_variant, grad_base, want_n;
+  int recon_vars;        // 0 conservative, 1 characteristic interface reconstruction
   double dt;
   int* flag;             // bit 0: non-physical state found
   double* op[8];         // operator outputs (Lp, Ltp, gbp, gtp, Ld, Ltd, gbd, gtd), interior layout

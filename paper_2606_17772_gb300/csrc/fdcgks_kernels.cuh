@@ -124,20 +124,9 @@ FD_HD bool physical_state(const R W[4]) {
          W[3] < R(INFINITY);
 }
 
-// Reconstruct one 4-point line at its virtual interface (between entries 1
-// and 2), with the safeguard above.  ld(l, e, f) = field f (0-3 W, 4-7 the
-// averaged gradient along the line) of entry e (0-3) of line l.
+// the safeguard applied to the left/right states of line l
 template <class R, class LD>
-FD_HD void recon_line_ld(const GenoK<R>& geno, LD ld, int l, R h, R ih, R vl[4], R dl[4], R vr[4], R dr[4],
-                         R& chi) {
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    R Q[4] = {ld(l, 0, c), ld(l, 1, c), ld(l, 2, c), ld(l, 3, c)};
-    R Qx[4] = {ld(l, 0, 4 + c), ld(l, 1, 4 + c), ld(l, 2, 4 + c), ld(l, 3, 4 + c)};
-    R cl, cr;
-    recon_interface(geno, Q, Qx, h, ih, vl[c], dl[c], cl, vr[c], dr[c], cr);
-    if (c == 0) chi = s_min(cl, cr);   // chi_{j+1/2} = min(chi^{l,rho}, chi^{r,rho})
-  }
+FD_HD void positivity_fix(LD ld, int l, R vl[4], R dl[4], R vr[4], R dr[4], R& chi) {
   if (!physical_state(vl)) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -156,20 +145,111 @@ FD_HD void recon_line_ld(const GenoK<R>& geno, LD ld, int l, R h, R ih, R vl[4],
   }
 }
 
+// Reconstruct one 4-point line at its virtual interface (between entries 1
+// and 2), with the safeguard above.  ld(l, e, f) = field f (0-3 W, 4-7 the
+// averaged gradient along the line) of entry e (0-3) of line l.
+template <class R, class LD>
+FD_HD void recon_line_ld(const GenoK<R>& geno, LD ld, int l, R h, R ih, R vl[4], R dl[4], R vr[4], R dr[4],
+                         R& chi) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    R Q[4] = {ld(l, 0, c), ld(l, 1, c), ld(l, 2, c), ld(l, 3, c)};
+    R Qx[4] = {ld(l, 0, 4 + c), ld(l, 1, 4 + c), ld(l, 2, 4 + c), ld(l, 3, 4 + c)};
+    R cl, cr;
+    recon_interface(geno, Q, Qx, h, ih, vl[c], dl[c], cl, vr[c], dr[c], cr);
+    if (c == 0) chi = s_min(cl, cr);   // chi_{j+1/2} = min(chi^{l,rho}, chi^{r,rho})
+  }
+  positivity_fix(ld, l, vl, dl, vr, dr, chi);
+}
+
+// The same on characteristic components (Sec. 3.1, "characteristic component
+// of W"; recon_vars = 1): the eigenvectors of the Euler flux Jacobian along
+// the line's normal, frozen at the mean of entries 1 and 2, in the order
+// (rho, m_n, m_t, E); rows of L / columns of R: U - c, entropy, shear, U + c.
+// Values and gradients are projected with L, each component reconstructed,
+// values and derivatives mapped back with R; chi of the flux is the smaller
+// of the two acoustic fields' (Sec. 3.2).  A non-physical mean state falls
+// back to conservative components.
+template <class R, class LD>
+FD_HD void recon_line_char(const GenoK<R>& geno, R gm1, int normal, LD ld, int l, R h, R ih, R vl[4], R dl[4],
+                           R vr[4], R dr[4], R& chi) {
+  const int in = normal == 0 ? 1 : 2, it = normal == 0 ? 2 : 1;
+  const int perm[4] = {0, in, it, 3};
+  const R r = R(0.5) * (ld(l, 1, 0) + ld(l, 2, 0));
+  const R mn = R(0.5) * (ld(l, 1, in) + ld(l, 2, in)), mt = R(0.5) * (ld(l, 1, it) + ld(l, 2, it));
+  const R E = R(0.5) * (ld(l, 1, 3) + ld(l, 2, 3));
+  const R ir = s_div(R(1), r), u = mn * ir, v = mt * ir;
+  const R q2 = u * u + v * v;
+  const R p = gm1 * (E - R(0.5) * r * q2);
+  if (!(r > R(0)) || !(p > R(0))) {
+    recon_line_ld(geno, ld, l, h, ih, vl, dl, vr, dr, chi);
+    return;
+  }
+  const R c = s_sqrt((gm1 + R(1)) * p * ir), ic = s_div(R(1), c), H = (E + p) * ir;
+  const R b1 = gm1 * ic * ic, b2 = R(0.5) * b1 * q2;
+  const R Lm[4][4] = {{R(0.5) * (b2 + u * ic), -R(0.5) * (b1 * u + ic), -R(0.5) * b1 * v, R(0.5) * b1},
+                      {R(1) - b2, b1 * u, b1 * v, -b1},
+                      {-v, R(0), R(1), R(0)},
+                      {R(0.5) * (b2 - u * ic), -R(0.5) * (b1 * u - ic), -R(0.5) * b1 * v, R(0.5) * b1}};
+  const R Rm[4][4] = {{R(1), R(1), R(0), R(1)},
+                      {u - c, u, R(0), u + c},
+                      {v, v, R(1), v},
+                      {H - u * c, R(0.5) * q2, v, H + u * c}};
+  R cvl[4], cdl[4], cvr[4], cdr[4], cl[4], cr[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    R Q[4], Qx[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      R a = R(0), b = R(0);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        a += Lm[k][j] * ld(l, m, perm[j]);
+        b += Lm[k][j] * ld(l, m, 4 + perm[j]);
+      }
+      Q[m] = a;
+      Qx[m] = b;
+    }
+    recon_interface(geno, Q, Qx, h, ih, cvl[k], cdl[k], cl[k], cvr[k], cdr[k], cr[k]);
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    R a = R(0), b = R(0), d = R(0), e = R(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      a += Rm[j][k] * cvl[k];
+      b += Rm[j][k] * cvr[k];
+      d += Rm[j][k] * cdl[k];
+      e += Rm[j][k] * cdr[k];
+    }
+    vl[perm[j]] = a;
+    vr[perm[j]] = b;
+    dl[perm[j]] = d;
+    dr[perm[j]] = e;
+  }
+  chi = s_min(s_min(cl[0], cr[0]), s_min(cl[3], cr[3]));
+  positivity_fix(ld, l, vl, dl, vr, dr, chi);
+}
+
 // One virtual-interface point: the two line reconstructions (with the
 // safeguard), the tangential derivatives, the two kinetic solves and the W~
 // combination.  ld(l, e, f) as for recon_line_ld, line 0 being the
 // primary-grid line (normal TYPE, spacing h[TYPE]) and line 1 the dual-grid
 // line (normal 1 - TYPE); st(k, v): output k (PO_* of solve 0, NPS + PO_* of
 // solve 1; F and W~ values only when wn).  Shared by the kernel and its adjoint.
-template <class R, int TYPE, class LD, class ST>
+template <class R, int TYPE, bool CHAR = false, class LD, class ST>
 FD_HD void point_compute(const GenoK<R>& geno, const GasK<R>& gas, const R h[2], const R ih[2], bool wn, LD ld,
                          ST st) {
   const int n0 = TYPE;        // normal of the primary-grid solve
   R l0v[4], l0d[4], r0v[4], r0d[4], chi0;
   R l1v[4], l1d[4], r1v[4], r1d[4], chi1;
-  recon_line_ld(geno, ld, 0, h[n0], ih[n0], l0v, l0d, r0v, r0d, chi0);
-  recon_line_ld(geno, ld, 1, h[1 - n0], ih[1 - n0], l1v, l1d, r1v, r1d, chi1);
+  if constexpr (CHAR) {
+    recon_line_char(geno, gas.gm1, n0, ld, 0, h[n0], ih[n0], l0v, l0d, r0v, r0d, chi0);
+    recon_line_char(geno, gas.gm1, 1 - n0, ld, 1, h[1 - n0], ih[1 - n0], l1v, l1d, r1v, r1d, chi1);
+  } else {
+    recon_line_ld(geno, ld, 0, h[n0], ih[n0], l0v, l0d, r0v, r0d, chi0);
+    recon_line_ld(geno, ld, 1, h[1 - n0], ih[1 - n0], l1v, l1d, r1v, r1d, chi1);
+  }
   // tangential derivative of each solve: mean of the other line's l/r derivatives
   R t0[4], t1[4];
 #pragma unroll
@@ -236,7 +316,7 @@ FD_HD PointLines point_lines(const Layout& L, int i, int j) {
 // TYPE 0 = point A (i+1/2, j): primary x-interface, dual y-interface of dual column i+1
 // TYPE 1 = point B (i, j+1/2): primary y-interface, dual x-interface of dual row j+1
 // ---------------------------------------------------------------------------
-template <class R, int TYPE>
+template <class R, int TYPE, bool CHAR = false>
 __device__ __forceinline__ void point_body(const KArgs<R>& a, int i, int j) {
   const Layout& L = a.L;
   const int imax = TYPE == 0 ? L.nx : L.nxd;
@@ -246,7 +326,7 @@ __device__ __forceinline__ void point_body(const KArgs<R>& a, int i, int j) {
   const R* S = a.Sr;
   R* P = (TYPE == 0 ? a.PA : a.PB) + pcell(L, i, j);
   const long pp = L.pplane;
-  point_compute<R, TYPE>(
+  point_compute<R, TYPE, CHAR>(
       a.geno, a.gas, a.h, a.ih, a.want_n != 0,
       [&](int l, int e, int f) -> R {
         const int field = f < 4 ? f : pl.gfield[l] + (f - 4);
@@ -255,9 +335,10 @@ __device__ __forceinline__ void point_body(const KArgs<R>& a, int i, int j) {
       [&](int k, R v) { P[(long)k * pp] = v; });
 }
 
-template <class R, int TYPE>
+template <class R, int TYPE, bool CHAR>
 __global__ void __launch_bounds__(128, PointTune<R>::minb) point_kernel(KArgs<R> a) {
-  point_body<R, TYPE>(a, blockIdx.x * blockDim.x + threadIdx.x - 2, blockIdx.y * blockDim.y + threadIdx.y - 2);
+  point_body<R, TYPE, CHAR>(a, blockIdx.x * blockDim.x + threadIdx.x - 2,
+                            blockIdx.y * blockDim.y + threadIdx.y - 2);
 }
 
 // ---------------------------------------------------------------------------
@@ -501,10 +582,13 @@ cudaError_t launch_nodal(const KArgs<R>& a, cudaStream_t s) {
 template <class R>
 cudaError_t launch_points(const KArgs<R>& a, cudaStream_t s) {
   dim3 b(32, 4);
-  point_kernel<R, 0><<<grid2(a.L.nx + 3, a.L.nyd + 3, b, 1), b, 0, s>>>(a);
+  const dim3 gA = grid2(a.L.nx + 3, a.L.nyd + 3, b, 1), gB = grid2(a.L.nxd + 3, a.L.ny + 3, b, 1);
+  if (a.recon_vars) point_kernel<R, 0, true><<<gA, b, 0, s>>>(a);
+  else point_kernel<R, 0, false><<<gA, b, 0, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  point_kernel<R, 1><<<grid2(a.L.nxd + 3, a.L.ny + 3, b, 1), b, 0, s>>>(a);
+  if (a.recon_vars) point_kernel<R, 1, true><<<gB, b, 0, s>>>(a);
+  else point_kernel<R, 1, false><<<gB, b, 0, s>>>(a);
   return cudaGetLastError();
 }
 

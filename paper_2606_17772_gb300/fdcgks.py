@@ -43,6 +43,7 @@ class Params(ctypes.Structure):
         ("precision", ctypes.c_int),
         ("tau_c1", ctypes.c_double), ("tau_c2", ctypes.c_double),
         ("stream", ctypes.c_void_p),
+        ("recon_vars", ctypes.c_int),
     ]
 
 
@@ -133,7 +134,7 @@ def _stream():
 
 def make_params(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, mu=0.0, Pr=1.0, bc=(0, 0, 0, 0),
                 flux_variant=64, geno_variant=0, grad_base=0, precision=FP64, tau_c1=0.0, tau_c2=0.0,
-                stream=None):
+                stream=None, recon_vars=0):
     p = Params()
     p.nx, p.ny = nx, ny
     p.x0, p.x1, p.y0, p.y1 = x0, x1, y0, y1
@@ -144,6 +145,7 @@ def make_params(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, mu=0.0, Pr=1.
     p.precision = precision
     p.tau_c1, p.tau_c2 = tau_c1, tau_c2
     p.stream = stream
+    p.recon_vars = recon_vars
     return p
 
 

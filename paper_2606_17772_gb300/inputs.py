@@ -45,6 +45,7 @@ class Case:
     flux_variant: int = 64
     geno_variant: int = 0
     grad_base: int = 0
+    recon_vars: int = 0          # 0 conservative, 1 characteristic components
     prim: object = None          # callable (x, y) -> (rho, U, V, p) arrays
     extra: dict = field(default_factory=dict)
 
@@ -101,7 +102,8 @@ class Case:
         return dict(nx=self.nx, ny=self.ny, x0=self.x0, x1=self.x1, y0=self.y0, y1=self.y1,
                     gamma=self.gamma, mu=self.mu, Pr=self.Pr, bc=tuple(self.bc),
                     flux_variant=self.flux_variant, geno_variant=self.geno_variant,
-                    grad_base=self.grad_base, tau_c1=self.tau_c1, tau_c2=self.tau_c2)
+                    grad_base=self.grad_base, tau_c1=self.tau_c1, tau_c2=self.tau_c2,
+                    recon_vars=self.recon_vars)
 
 
 # ---------------------------------------------------------------------------

@@ -96,6 +96,8 @@ def test_empty_batches_are_noops():
 
 STAGE_CASES = {
     "periodic_ragged": lambda: inputs.random_smooth(37, 21, seed=11, amp=0.08, tau_c1=0.05, tau_c2=1.0),
+    "char_periodic_ragged": lambda: inputs.random_smooth(37, 21, seed=11, amp=0.08, tau_c1=0.05, tau_c2=1.0,
+                                                         recon_vars=1),
     "walls_viscous": lambda: inputs.random_smooth(21, 13, seed=12, amp=0.08, bc=(3, 3, 3, 2), mu=0.01, Pr=0.73,
                                                   tau_c2=1.0),
     "transmissive_6_2_appD": lambda: inputs.random_smooth(19, 6, seed=13, amp=0.08, bc=(1, 1, 0, 0),
@@ -121,6 +123,12 @@ def test_stage_operator_matches_oracle(name):
 
 STEP_CASES = {
     "vortex_40": (lambda: inputs.vortex(40), 0.02),
+    # characteristic components (recon_vars = 1) on every boundary kind
+    "char_vortex_40": (lambda: inputs.vortex(40, recon_vars=1), 0.02),
+    "char_sod_strip_64x4": (lambda: inputs.sod_strip(64, 4, recon_vars=1), 0.002),
+    "char_walls_6_2_appD": (lambda: inputs.random_smooth(17, 11, seed=21, amp=0.1, bc=(3, 3, 2, 2), flux_variant=62,
+                                                         geno_variant=1, mu=0.002, Pr=0.7, tau_c1=0.02, tau_c2=1.0,
+                                                         recon_vars=1), 0.003),
     "sod_strip_64x4": (lambda: inputs.sod_strip(64, 4), 0.002),
     "viscous_tube_24x12": (lambda: inputs.viscous_shock_tube(24, 12), 2e-4),
     "walls_6_2_appD_readingA": (lambda: inputs.random_smooth(17, 11, seed=21, amp=0.1, bc=(3, 3, 2, 2),
@@ -167,6 +175,7 @@ STRONG = {
     "strong_shock_strip_100x2": lambda: (inputs.strong_shock_strip(100, 2), 12),
     # the viscous shock tube itself (no-slip walls, symmetry top) on a coarse grid
     "viscous_tube_24x12": lambda: (inputs.viscous_shock_tube(24, 12), 6),
+    "strong_shock_strip_char_100x2": lambda: (inputs.strong_shock_strip(100, 2, recon_vars=1), 12),
 }
 
 
@@ -351,3 +360,18 @@ def test_mixed_steps_within_stated_error(nsteps, bound_w, bound_g):
     w = max(v for k, v in errs.items() if k.startswith("W"))
     g = max(v for k, v in errs.items() if k.startswith("G"))
     assert w < bound_w and g < bound_g, errs
+
+
+def test_characteristic_reconstruction_is_single_context_only():
+    case = inputs.vortex(12, recon_vars=1)
+    with pytest.raises(fdcgks.FdcgksError) as e:
+        fdcgks.Ensemble.from_cases([case])
+    assert e.value.status == 1
+    with fdcgks.Solver.from_case(case) as s:
+        S0 = [torch.from_numpy(a).cuda() for a in case.initial_state()]
+        with pytest.raises(fdcgks.FdcgksError) as e:
+            s.vjp_steps(0.01, 1, S0, S0)
+        assert e.value.status == 1
+    with pytest.raises(fdcgks.FdcgksError) as e:
+        fdcgks.Solver(fdcgks.make_params(8, 8, recon_vars=2))
+    assert e.value.status == 1

@@ -156,3 +156,81 @@ def test_fourth_order_fallback_flux_exact_to_degree_3(deg):
 def test_second_order_fallback_is_interface_flux():
     Fi, Fn = np.array([1.0, 2.5, 7.0]), np.array([3.0, 4.0])
     assert oracle.compact_flux(62, 0.0, Fi, Fn) == 2.5
+
+
+# ---------------------------------------------------------------------------
+# characteristic components (recon_vars = 1)
+# ---------------------------------------------------------------------------
+def _euler_flux(W, normal, gamma=1.4):
+    """Textbook Euler flux along x (normal 0) or y (normal 1) of W = (rho, rho U, rho V, rho E)."""
+    rho, mx, my, E = W
+    u, v = mx / rho, my / rho
+    p = (gamma - 1.0) * (E - 0.5 * rho * (u * u + v * v))
+    un = u if normal == 0 else v
+    return np.array([rho * un, mx * un + (p if normal == 0 else 0.0), my * un + (p if normal == 1 else 0.0),
+                      (E + p) * un])
+
+
+@pytest.mark.parametrize("normal", [0, 1])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_characteristic_basis_diagonalises_the_flux_jacobian(normal, seed):
+    """L R = I and R diag(u_n - c, u_n, u_n, u_n + c) L = dF_n/dW at the mean state,
+    with the Jacobian taken by central differences of the Euler flux."""
+    rng = np.random.default_rng(seed)
+    g = 1.4
+
+    def state():
+        rho, u, v, p = rng.uniform(0.5, 2), rng.uniform(-1, 1), rng.uniform(-1, 1), rng.uniform(0.3, 2)
+        return np.array([rho, rho * u, rho * v, p / (g - 1) + 0.5 * rho * (u * u + v * v)])
+    Wa, Wb = state(), state()
+    L, R = oracle.char_basis(g, normal, Wa, Wb)
+    W = 0.5 * (Wa + Wb)
+    perm = [0, 1, 2, 3] if normal == 0 else [0, 2, 1, 3]       # (rho, m_n, m_t, E) order
+    P = np.eye(4)[perm]                                          # W_perm = P W
+    assert np.allclose(L @ R, np.eye(4), atol=1e-13)
+    A = np.zeros((4, 4))
+    for k in range(4):
+        e = np.zeros(4)
+        e[k] = 1e-6 * max(1.0, abs(W[k]))
+        A[:, k] = (_euler_flux(W + e, normal) - _euler_flux(W - e, normal)) / (2 * e[k])
+    rho, u, v = W[0], W[1] / W[0], W[2] / W[0]
+    p = (g - 1) * (W[3] - 0.5 * rho * (u * u + v * v))
+    c, un = np.sqrt(g * p / rho), (u if normal == 0 else v)
+    lam = np.diag([un - c, un, un, un + c])
+    assert np.allclose(P.T @ R @ lam @ L @ P, A, rtol=1e-7, atol=1e-7)
+
+
+@pytest.mark.parametrize("normal", [0, 1])
+def test_characteristic_reconstruction_equals_conservative_when_linear(normal):
+    """With the linear reconstruction (GENO variant 2) both are linear maps and the
+    projection is fixed per line, so characteristic and conservative
+    reconstruction agree to rounding on any data."""
+    rng = np.random.default_rng(5)
+    g = 1.4
+    for _ in range(20):
+        rho = rng.uniform(0.5, 2, 4)
+        u, v, p = rng.uniform(-1, 1, 4), rng.uniform(-1, 1, 4), rng.uniform(0.3, 2, 4)
+        Q = np.stack([rho, rho * u, rho * v, p / (g - 1) + 0.5 * rho * (u * u + v * v)], 1)   # [entry][field]
+        Qx = rng.normal(size=(4, 4))
+        a = oracle.recon_line(2, 1, g, normal, Q, Qx, 0.1)
+        b = oracle.recon_line(2, 0, g, normal, Q, Qx, 0.1)
+        for x, y in zip(a[:4], b[:4]):
+            assert np.allclose(x, y, rtol=1e-12, atol=1e-12)
+
+
+def test_characteristic_reconstruction_exact_to_degree_6():
+    """Polynomial data of degree 6 in every conservative variable, smooth enough that
+    GENO keeps the high-order stencil: the characteristic reconstruction is exact."""
+    g, h = 1.4, 0.05
+    x = np.array([-1.5, -0.5, 0.5, 1.5]) * h                     # entries around the interface at 0
+    base = np.array([1.0, 0.3, -0.2, 2.5])
+    cf = np.array([0.02, -0.01, 0.015, 0.03])
+
+    def f(t):
+        return base + cf * (t + t ** 2 + t ** 3 + t ** 4 + t ** 5 + t ** 6)
+
+    Q = np.array([f(t) for t in x])
+    Qx = np.array([(f(t + h / 2) - f(t - h / 2)) / h for t in x])     # exact averaged gradients
+    Wl, Wr, Wlx, Wrx, chi = oracle.recon_line(0, 1, g, 0, Q, Qx, h)
+    assert chi == pytest.approx(1.0)
+    assert np.allclose(Wl, f(0.0), atol=1e-12) and np.allclose(Wr, f(0.0), atol=1e-12)

@@ -216,12 +216,14 @@ def test_sod_tube_against_exact_riemann_solution():
     assert np.abs(u - ex[1]).mean() < 1.5e-2
 
 
-def test_strong_shock_tube_against_exact_riemann_solution():
+@pytest.mark.parametrize("recon_vars", [0, 1])
+def test_strong_shock_tube_against_exact_riemann_solution(recon_vars):
     """Density and pressure ratio 100 (the viscous shock tube's states, Sec. 5.8, inviscid),
     N = 200, t = 0.1, CFL 0.4: the run stays physical (the positivity safeguard replaces
     reconstructed interface states with non-positive pressure near the diaphragm in the
-    first steps) and converges to the exact solution."""
-    c = inputs.strong_shock_strip(200, 1)
+    first steps) and converges to the exact solution, with conservative and with
+    characteristic components."""
+    c = inputs.strong_shock_strip(200, 1, recon_vars=recon_vars)
     p = oracle.make_params(**c.oracle_kwargs())
     S = c.initial_state()
     t, T, g = 0.0, 0.1, c.gamma
