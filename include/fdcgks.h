@@ -56,7 +56,10 @@ typedef enum {
   FDCGKS_BC_PERIODIC = 0,
   FDCGKS_BC_TRANSMISSIVE = 1,
   FDCGKS_BC_SYMMETRY = 2,
-  FDCGKS_BC_NOSLIP = 3
+  FDCGKS_BC_NOSLIP = 3,
+  FDCGKS_BC_FIXED = 4          /* fixed state (inflow, or the state on either side of a tracked shock):
+                                  ghosts hold the given state with zero gradients; only through
+                                  fdcgks_set_sides */
 } fdcgks_bc;
 
 typedef enum { FDCGKS_FP64 = 0, FDCGKS_MIXED = 1 } fdcgks_precision;
@@ -147,6 +150,29 @@ fdcgks_status fdcgks_stage_operator(fdcgks_t ctx, double dt, double* Lp, double*
  * on this context. */
 fdcgks_status fdcgks_set_profiling(fdcgks_t ctx, int enable);
 fdcgks_status fdcgks_get_profile(fdcgks_t ctx, double* ms, int* count, long long* launches);
+
+/* Boundary sides beyond params.bc (the paper names inflow, outflow, reflecting
+ * walls starting part way along a side, and a top boundary that tracks an
+ * exact moving shock, Sec. 5 double Mach reflection, without describing their
+ * implementation).  Each side (x-low, x-high, y-low, y-high) is split at a
+ * point that moves along it, split0 + split_speed * t (x for the y-sides, y
+ * for the x-sides): ghost nodes whose coordinate along the side lies below
+ * the split take kind[0], the others kind[1].  FIXED parts hold prim[part] =
+ * (rho, U, V, p) in their ghosts with zero gradients.  The ghost fill of stage
+ * 1 uses the context time t, that of stage 2 t + dt/2; each step advances t
+ * by dt (fdcgks_set_time, fdcgks_get_time; fdcgks_set_state resets t to 0).
+ *   - sides == NULL restores params.bc.  A periodic direction stays periodic
+ *     on both sides and parts; a bounded side takes TRANSMISSIVE, SYMMETRY,
+ *     FIXED, or NOSLIP (NOSLIP only for an unsplit side, kind[0] == kind[1]).
+ *   - Single contexts only (the ensemble and the adjoint take params.bc). */
+typedef struct {
+  int kind[2];
+  double split0, split_speed;
+  double prim[2][4];
+} fdcgks_side;
+fdcgks_status fdcgks_set_sides(fdcgks_t ctx, const fdcgks_side* sides);
+fdcgks_status fdcgks_set_time(fdcgks_t ctx, double t);
+fdcgks_status fdcgks_get_time(fdcgks_t ctx, double* t);
 
 /* Batched kinetic interface solve (App. A1-A2, Eq. eq:W-model), normal 0 = x,
  * 1 = y, on device arrays: in [n][20] = Wl[4], Wr[4], normal derivatives

@@ -581,7 +581,7 @@ double compact_flux(int variant, double chi, const double Fi[3], const double Fn
 // ===========================================================================
 extern "C" {
 
-enum { OBC_PERIODIC = 0, OBC_TRANSMISSIVE = 1, OBC_SYMMETRY = 2, OBC_NOSLIP = 3 };
+enum { OBC_PERIODIC = 0, OBC_TRANSMISSIVE = 1, OBC_SYMMETRY = 2, OBC_NOSLIP = 3, OBC_FIXED = 4 };
 
 typedef struct {
   int nx, ny;
@@ -593,6 +593,18 @@ typedef struct {
   int grad_base;        // 0 reading B (re-evaluated), 1 reading A (stored)
   double tau_c1, tau_c2;
   int recon_vars;       // 0 conservative components, 1 characteristic components
+  // Split sides (Sec. 5, double Mach reflection: inflow, a wall that starts
+  // part way along the bottom, a top boundary that follows the exact moving
+  // shock).  With has_sides, ghost nodes of side k whose coordinate along the
+  // side lies below side_split0[k] + side_speed[k] * t take side_kind[k][0],
+  // the others side_kind[k][1]; OBC_FIXED parts hold side_prim[k][part] =
+  // (rho, U, V, p) with zero gradients.  t starts at t0; stage 1 of a step at
+  // t fills ghosts at t, stage 2 at t + dt/2.
+  int has_sides;
+  int side_kind[4][2];
+  double side_split0[4], side_speed[4];
+  double side_prim[4][2][4];
+  double t0;
 } oracle_params;
 
 }  // extern "C"
@@ -623,18 +635,26 @@ Grid make_grid(int nx, int ny, int perx, int pery) {
   return g;
 }
 
-// ghost fill of one grid; is_dual selects the mirror map (dual nodes lie on
-// bounded boundaries, primary nodes half a spacing inside)
-void fill_ghosts(Grid& g, const int bc[4], bool is_dual) {
+// ghost fill of one grid at time t; is_dual selects the mirror map (dual
+// nodes lie on bounded boundaries, primary nodes half a spacing inside)
+void fill_ghosts(Grid& g, const oracle_params& p, double hx, double hy, bool is_dual, double t) {
+  const double gm1 = p.gamma - 1.0;
   for (int dir = 0; dir < 2; ++dir) {
     int n = g.n[dir];
-    int lo = dir == 0 ? -G : -G;
     int tcount = dir == 0 ? g.n[1] : g.n[0] + 2 * G;   // x pass over interior rows, y pass over all columns
     int toff = dir == 0 ? 0 : -G;
     for (int side = 0; side < 2; ++side) {
-      int b = bc[2 * dir + side];
-      for (int t = 0; t < tcount; ++t) {
-        int tt = t + toff;
+      for (int t_ = 0; t_ < tcount; ++t_) {
+        int tt = t_ + toff;
+        // node coordinate along the side (primary nodes sit at cell centres,
+        // dual nodes at the primary cell corners) against the split point;
+        // both are single-rounded fused products so that a node lying on the
+        // split point is classified the same way by every implementation
+        const int sd = 2 * dir + side;
+        const double pos = tt + (is_dual ? 0.0 : 0.5);
+        const double coord = dir == 0 ? std::fma(pos, hy, p.y0) : std::fma(pos, hx, p.x0);
+        const int part = p.has_sides && !(coord < std::fma(p.side_speed[sd], t, p.side_split0[sd]));
+        const int b = p.has_sides ? p.side_kind[sd][part] : p.bc[sd];
         for (int k = 1; k <= G; ++k) {
           int ghost = side == 0 ? -k : n - 1 + k;
           int src;
@@ -644,6 +664,17 @@ void fill_ghosts(Grid& g, const int bc[4], bool is_dual) {
           else src = side == 0 ? k : n - 1 - k;
           int gi = dir == 0 ? ghost : tt, gj = dir == 0 ? tt : ghost;
           int si = dir == 0 ? src : tt, sj = dir == 0 ? tt : src;
+          if (b == OBC_FIXED) {
+            const double* pr = p.side_prim[sd][part];
+            const double W[4] = {pr[0], pr[0] * pr[1], pr[0] * pr[2],
+                                 pr[3] / gm1 + 0.5 * pr[0] * (pr[1] * pr[1] + pr[2] * pr[2])};
+            for (int c = 0; c < 4; ++c) {
+              g.at(c, gi, gj) = W[c];
+              g.at(4 + c, gi, gj) = 0.0;
+              g.at(8 + c, gi, gj) = 0.0;
+            }
+            continue;
+          }
           for (int c = 0; c < 4; ++c) {
             double sW = 1.0;
             if (b == OBC_SYMMETRY || b == OBC_NOSLIP) {
@@ -671,7 +702,6 @@ void fill_ghosts(Grid& g, const int bc[4], bool is_dual) {
         }
       }
     }
-    (void)lo;
   }
 }
 
@@ -895,10 +925,10 @@ void gather_line(const Grid& g, int i, int j, int dir, double Q[4][4], double Qn
   }
 }
 
-StageOut stage(const Scheme& S, Grid& P, Grid& D, double dt) {
+StageOut stage(const Scheme& S, Grid& P, Grid& D, double dt, double t) {
   const int nx = S.p.nx, ny = S.p.ny, nxd = S.nxd, nyd = S.nyd;
-  fill_ghosts(P, S.p.bc, false);
-  fill_ghosts(D, S.p.bc, true);
+  fill_ghosts(P, S.p, S.hx, S.hy, false, t);
+  fill_ghosts(D, S.p, S.hx, S.hy, true, t);
 
   // nodal reconstruction and flux (Sec. 4 item 2, Sec. 2.1)
   auto nodal = [&](Grid& g, int nxg, int nyg, Rect<NodeOut>& out) {
@@ -1021,6 +1051,14 @@ bool make_scheme(const oracle_params* p, Scheme& S) {
   }
   if ((p->bc[0] != OBC_PERIODIC && p->nx < 3) || (p->bc[2] != OBC_PERIODIC && p->ny < 3)) return false;
   if (p->recon_vars != 0 && p->recon_vars != 1) return false;
+  if (p->has_sides)
+    for (int k = 0; k < 4; ++k)
+      for (int q = 0; q < 2; ++q) {
+        int kind = p->side_kind[k][q];
+        if ((kind == OBC_PERIODIC) != (p->bc[k] == OBC_PERIODIC) || kind < 0 || kind > OBC_FIXED) return false;
+        if (kind == OBC_NOSLIP && p->side_kind[k][1 - q] != OBC_NOSLIP) return false;
+        if (kind == OBC_FIXED && !(p->side_prim[k][q][0] > 0.0 && p->side_prim[k][q][3] > 0.0)) return false;
+      }
   S.nxd = p->nx + (p->bc[0] == OBC_PERIODIC ? 0 : 1);
   S.nyd = p->ny + (p->bc[2] == OBC_PERIODIC ? 0 : 1);
   S.hx = (p->x1 - p->x0) / p->nx;
@@ -1061,7 +1099,11 @@ void store_grid(const Grid& g, double* W, double* Gr) {
 // velocity of dual nodes lying on a no-slip wall is set to zero (kinetic
 // energy removed, internal energy kept)
 void noslip_reset(const Scheme& S, Grid& D) {
-  const int* bc = S.p.bc;
+  // a split side is never a no-slip wall (a no-slip side is not split)
+  int bc[4];
+  for (int k = 0; k < 4; ++k)
+    bc[k] = !S.p.has_sides ? S.p.bc[k]
+                           : (S.p.side_kind[k][0] == S.p.side_kind[k][1] ? S.p.side_kind[k][0] : OBC_FIXED);
   for (int j = 0; j < S.nyd; ++j)
     for (int i = 0; i < S.nxd; ++i) {
       bool wall = (bc[0] == OBC_NOSLIP && i == 0) || (bc[1] == OBC_NOSLIP && i == S.nxd - 1) ||
@@ -1081,11 +1123,11 @@ void noslip_reset(const Scheme& S, Grid& D) {
 }
 
 // one S2O4 step (Eqs. eq-nodal-update, eq-interface-update)
-void s2o4_step(const Scheme& S, Grid& P, Grid& D, double dt) {
+void s2o4_step(const Scheme& S, Grid& P, Grid& D, double dt, double t) {
   Grid* grids[2] = {&P, &D};
   const bool readA = S.p.grad_base == 1;
   Grid P0 = P, D0 = D;   // state at t^n
-  StageOut s1 = stage(S, P, D, dt);
+  StageOut s1 = stage(S, P, D, dt, t);
   // stage 1 -> t^{n+1/2}
   const std::vector<double>* L1[2] = {&s1.Lp, &s1.Ld};
   const std::vector<double>* Lt1[2] = {&s1.Ltp, &s1.Ltd};
@@ -1111,7 +1153,7 @@ void s2o4_step(const Scheme& S, Grid& P, Grid& D, double dt) {
       }
   }
   noslip_reset(S, D);
-  StageOut s2 = stage(S, P, D, dt);
+  StageOut s2 = stage(S, P, D, dt, t + 0.5 * dt);
   const std::vector<double>* Lt2[2] = {&s2.Ltp, &s2.Ltd};
   const std::vector<double>* gt2[2] = {&s2.gtp, &s2.gtd};
   for (int gi = 0; gi < 2; ++gi) {
@@ -1160,7 +1202,11 @@ int oracle_steps(const oracle_params* p, double dt, int nsteps, double* Wp, doub
   Grid D = make_grid(S.nxd, S.nyd, p->bc[0] == OBC_PERIODIC, p->bc[2] == OBC_PERIODIC);
   load_grid(P, Wp, Gp);
   load_grid(D, Wd, Gd);
-  for (int s = 0; s < nsteps; ++s) s2o4_step(S, P, D, dt);
+  double t = p->t0;
+  for (int s = 0; s < nsteps; ++s) {
+    s2o4_step(S, P, D, dt, t);
+    t += dt;
+  }
   store_grid(P, Wp, Gp);
   store_grid(D, Wd, Gd);
   return 0;
@@ -1177,7 +1223,7 @@ int oracle_stage(const oracle_params* p, double dt, const double* Wp, const doub
   Grid D = make_grid(S.nxd, S.nyd, p->bc[0] == OBC_PERIODIC, p->bc[2] == OBC_PERIODIC);
   load_grid(P, Wp, Gp);
   load_grid(D, Wd, Gd);
-  StageOut o = stage(S, P, D, dt);
+  StageOut o = stage(S, P, D, dt, p->t0);
   std::memcpy(Lp, o.Lp.data(), o.Lp.size() * sizeof(double));
   std::memcpy(Ltp, o.Ltp.data(), o.Ltp.size() * sizeof(double));
   std::memcpy(gbp, o.gbp.data(), o.gbp.size() * sizeof(double));

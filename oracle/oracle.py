@@ -10,7 +10,7 @@ import numpy as np
 
 from .build import build_oracle
 
-BC_PERIODIC, BC_TRANSMISSIVE, BC_SYMMETRY, BC_NOSLIP = 0, 1, 2, 3
+BC_PERIODIC, BC_TRANSMISSIVE, BC_SYMMETRY, BC_NOSLIP, BC_FIXED = 0, 1, 2, 3, 4
 
 
 class OracleParams(ctypes.Structure):
@@ -25,6 +25,11 @@ class OracleParams(ctypes.Structure):
         ("grad_base", ctypes.c_int),
         ("tau_c1", ctypes.c_double), ("tau_c2", ctypes.c_double),
         ("recon_vars", ctypes.c_int),
+        ("has_sides", ctypes.c_int),
+        ("side_kind", (ctypes.c_int * 2) * 4),
+        ("side_split0", ctypes.c_double * 4), ("side_speed", ctypes.c_double * 4),
+        ("side_prim", ((ctypes.c_double * 4) * 2) * 4),
+        ("t0", ctypes.c_double),
     ]
 
 
@@ -44,7 +49,10 @@ def lib():
 
 def make_params(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, mu=0.0, Pr=1.0,
                 bc=(0, 0, 0, 0), flux_variant=64, geno_variant=0, grad_base=0,
-                tau_c1=0.0, tau_c2=0.0, recon_vars=0):
+                tau_c1=0.0, tau_c2=0.0, recon_vars=0, sides=None, t0=0.0):
+    """sides: None, or 4 dicts (x-low, x-high, y-low, y-high) with keys kind
+    (2 boundary kinds), split0, split_speed and prim (2 x (rho, U, V, p)); t0:
+    the time of the first step (moving split points)."""
     p = OracleParams()
     p.nx, p.ny = nx, ny
     p.x0, p.x1, p.y0, p.y1 = x0, x1, y0, y1
@@ -54,6 +62,15 @@ def make_params(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, mu=0.0, Pr=1.
     p.flux_variant, p.geno_variant, p.grad_base = flux_variant, geno_variant, grad_base
     p.tau_c1, p.tau_c2 = tau_c1, tau_c2
     p.recon_vars = recon_vars
+    p.has_sides = int(sides is not None)
+    for k, sd in enumerate(sides or ()):
+        p.side_kind[k][0], p.side_kind[k][1] = sd["kind"]
+        p.side_split0[k] = sd.get("split0", 0.0)
+        p.side_speed[k] = sd.get("split_speed", 0.0)
+        for q, prim in enumerate(sd.get("prim", ((0.0,) * 4,) * 2)):
+            for j in range(4):
+                p.side_prim[k][q][j] = prim[j]
+    p.t0 = t0
     return p
 
 

@@ -519,6 +519,7 @@ extern "C" fdcgks_status fdcgks_vjp_steps(fdcgks_t ctx, double dt, int nsteps, i
   if (w.v.p.precision != FDCGKS_FP64) return afail(ctx, FDCGKS_ERR_ARG, "the adjoint needs an FP64 context");
   if (w.v.p.recon_vars != 0)
     return afail(ctx, FDCGKS_ERR_ARG, "the adjoint reconstructs conservative components only");
+  if (w.v.has_sides) return afail(ctx, FDCGKS_ERR_ARG, "the adjoint takes the boundary kinds of params.bc only");
   if (!(dt > 0.0) || !std::isfinite(dt)) return afail(ctx, FDCGKS_ERR_ARG, "dt must be positive and finite");
   if (nsteps < 0 || checkpoint_every < 1) return afail(ctx, FDCGKS_ERR_ARG, "nsteps >= 0 and checkpoint_every >= 1");
   const void* ptrs[] = {Wp0, Gp0, Wd0, Gd0, aWp, aGp, aWd, aGd, gWp, gGp, gWd, gGd};

@@ -44,6 +44,10 @@ struct fdcgks_ctx {
   int ev_cap = 0, ev_used = 0;
   int* ev_class = nullptr;    // class of the interval that ends at event 2k+1
   long long launches = 0;     // kernels launched by the stepping path
+  // split sides (fdcgks_set_sides) and the context time they are evaluated at
+  bool has_sides = false;
+  fdcgks_side sides[4];
+  double t = 0.0;
   char err[512];
 };
 
@@ -60,6 +64,7 @@ bool fdk::ctx_view(fdcgks_t c, CtxView* v) {
   v->stream = c->stream;
   v->S = c->S;
   v->has_state = c->has_state;
+  v->has_sides = c->has_sides;
   return true;
 }
 
@@ -125,13 +130,50 @@ __global__ void ghost_kernel(T* S, Layout L, int bc0, int bc1, int dir) {
 }
 
 template <class T>
-static cudaError_t fill_ghosts(fdcgks_t c, T* S) {
+__global__ void ghost_sides_kernel(T* S, Layout L, GhostSides gs, int dir) {
+  ghost_body_sides(S, L, gs, dir, blockIdx.z, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// split sides evaluated at time t
+static GhostSides ghost_sides(fdcgks_t c, double t) {
+  GhostSides gs;
+  const double gm1 = c->p.gamma - 1.0;
+  for (int k = 0; k < 4; ++k) {
+    const fdcgks_side& sd = c->sides[k];
+    gs.split[k] = std::fma(sd.split_speed, t, sd.split0);
+    for (int q = 0; q < 2; ++q) {
+      gs.kind[k][q] = sd.kind[q];
+      const double* pr = sd.prim[q];
+      gs.W[k][q][0] = pr[0];
+      gs.W[k][q][1] = pr[0] * pr[1];
+      gs.W[k][q][2] = pr[0] * pr[2];
+      gs.W[k][q][3] = pr[3] / gm1 + 0.5 * pr[0] * (pr[1] * pr[1] + pr[2] * pr[2]);
+    }
+  }
+  gs.x0 = c->p.x0;
+  gs.y0 = c->p.y0;
+  gs.hx = c->hx;
+  gs.hy = c->hy;
+  return gs;
+}
+
+// ghost layers at stage time t (t matters only for split sides)
+template <class T>
+static cudaError_t fill_ghosts(fdcgks_t c, T* S, double t) {
   const Layout& L = c->L;
   int tx = (L.ny > L.nyd ? L.ny : L.nyd) * 2 * GH;
+  int ty = ((L.nx > L.nxd ? L.nx : L.nxd) + 2 * GH) * 2 * GH;
+  if (c->has_sides) {
+    const GhostSides gs = ghost_sides(c, t);
+    ghost_sides_kernel<T><<<dim3((tx + 127) / 128, 1, 2), 128, 0, c->stream>>>(S, L, gs, 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ghost_sides_kernel<T><<<dim3((ty + 127) / 128, 1, 2), 128, 0, c->stream>>>(S, L, gs, 1);
+    return cudaGetLastError();
+  }
   ghost_kernel<T><<<dim3((tx + 127) / 128, 1, 2), 128, 0, c->stream>>>(S, L, c->p.bc[0], c->p.bc[1], 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  int ty = ((L.nx > L.nxd ? L.nx : L.nxd) + 2 * GH) * 2 * GH;
   ghost_kernel<T><<<dim3((ty + 127) / 128, 1, 2), 128, 0, c->stream>>>(S, L, c->p.bc[2], c->p.bc[3], 1);
   return cudaGetLastError();
 }
@@ -270,7 +312,10 @@ static KArgs<R> make_args(fdcgks_t c, double dt, const double* S, double* Sout, 
   a.ihd[0] = 1.0 / c->hx; a.ihd[1] = 1.0 / c->hy;
   a.h[0] = (R)c->hx; a.h[1] = (R)c->hy;
   a.ih[0] = (R)(1.0 / c->hx); a.ih[1] = (R)(1.0 / c->hy);
-  for (int k = 0; k < 4; ++k) a.bc[k] = c->p.bc[k];
+  // the no-slip wall reset reads bc: an unsplit side's kind, else a non-wall kind
+  for (int k = 0; k < 4; ++k)
+    a.bc[k] = !c->has_sides ? c->p.bc[k]
+                            : (c->sides[k].kind[0] == c->sides[k].kind[1] ? c->sides[k].kind[0] : FDCGKS_BC_FIXED);
   a.flux_variant = c->p.flux_variant;
   a.grad_base = c->p.grad_base;
   a.recon_vars = c->p.recon_vars;
@@ -303,7 +348,7 @@ static fdcgks_status run_stage(fdcgks_t c, double dt, int mode, double* const* o
   KArgs<R> a = make_args<R>(c, dt, nullptr, nullptr, mode != UPD_STAGE2);
   stage_state(c, mode, a);
   CUDA_TRY(c, prof_mark(c, KC_GHOST, true));
-  CUDA_TRY(c, fill_ghosts(c, const_cast<R*>(a.Sr)));
+  CUDA_TRY(c, fill_ghosts(c, const_cast<R*>(a.Sr), mode == UPD_STAGE2 ? c->t + 0.5 * dt : c->t));
   CUDA_TRY(c, prof_mark(c, KC_GHOST, false));
   if (op)
     for (int k = 0; k < 8; ++k) a.op[k] = op[k];
@@ -324,7 +369,9 @@ template <class R>
 static fdcgks_status run_step(fdcgks_t c, double dt) {
   fdcgks_status s = run_stage<R>(c, dt, UPD_STAGE1, nullptr);
   if (s != FDCGKS_OK) return s;
-  return run_stage<R>(c, dt, UPD_STAGE2, nullptr);
+  s = run_stage<R>(c, dt, UPD_STAGE2, nullptr);
+  if (s == FDCGKS_OK) c->t += dt;
+  return s;
 }
 
 // ---------------------------------------------------------------------------
@@ -473,6 +520,7 @@ fdcgks_status fdcgks_set_state(fdcgks_t c, const double* Wp, const double* Gp, c
     return fail(c, FDCGKS_ERR_NONPHYSICAL, "state has non-positive or non-finite density/pressure");
   }
   c->has_state = true;
+  c->t = 0.0;
   return FDCGKS_OK;
 }
 
@@ -561,6 +609,50 @@ fdcgks_status fdcgks_stage_operator(fdcgks_t c, double dt, double* Lp, double* L
     if (!q) return fail(c, FDCGKS_ERR_ARG, "NULL output pointer");
   return c->p.precision == FDCGKS_MIXED ? run_stage<float>(c, dt, UPD_OPERATOR, op)
                                         : run_stage<double>(c, dt, UPD_OPERATOR, op);
+}
+
+fdcgks_status fdcgks_set_sides(fdcgks_t c, const fdcgks_side* sides) {
+  if (!c) return fail(nullptr, FDCGKS_ERR_ARG, "ctx is NULL");
+  if (!sides) {
+    c->has_sides = false;
+    return FDCGKS_OK;
+  }
+  for (int k = 0; k < 4; ++k) {
+    const fdcgks_side& sd = sides[k];
+    const bool periodic = c->p.bc[k] == FDCGKS_BC_PERIODIC;
+    for (int q = 0; q < 2; ++q) {
+      const int kind = sd.kind[q];
+      if (periodic != (kind == FDCGKS_BC_PERIODIC))
+        return fail(c, FDCGKS_ERR_ARG, "side %d: a periodic direction stays periodic, a bounded one bounded", k);
+      if (kind < 0 || kind > FDCGKS_BC_FIXED) return fail(c, FDCGKS_ERR_ARG, "side %d: unknown kind %d", k, kind);
+      if (kind == FDCGKS_BC_NOSLIP && sd.kind[1 - q] != FDCGKS_BC_NOSLIP)
+        return fail(c, FDCGKS_ERR_ARG, "side %d: a no-slip wall cannot be split", k);
+      if (kind == FDCGKS_BC_FIXED) {
+        const double* pr = sd.prim[q];
+        if (!(pr[0] > 0.0) || !(pr[3] > 0.0) || !std::isfinite(pr[1]) || !std::isfinite(pr[2]) ||
+            !std::isfinite(pr[0]) || !std::isfinite(pr[3]))
+          return fail(c, FDCGKS_ERR_ARG, "side %d: fixed state needs positive finite density and pressure", k);
+      }
+    }
+    if (!std::isfinite(sd.split0) || !std::isfinite(sd.split_speed))
+      return fail(c, FDCGKS_ERR_ARG, "side %d: split must be finite", k);
+  }
+  for (int k = 0; k < 4; ++k) c->sides[k] = sides[k];
+  c->has_sides = true;
+  return FDCGKS_OK;
+}
+
+fdcgks_status fdcgks_set_time(fdcgks_t c, double t) {
+  if (!c) return fail(nullptr, FDCGKS_ERR_ARG, "ctx is NULL");
+  if (!std::isfinite(t)) return fail(c, FDCGKS_ERR_ARG, "t must be finite");
+  c->t = t;
+  return FDCGKS_OK;
+}
+
+fdcgks_status fdcgks_get_time(fdcgks_t c, double* t) {
+  if (!c || !t) return fail(c, FDCGKS_ERR_ARG, "NULL argument");
+  *t = c->t;
+  return FDCGKS_OK;
 }
 
 fdcgks_status fdcgks_set_profiling(fdcgks_t c, int enable) {

@@ -140,12 +140,9 @@ FD_HD void ghost_sign(int b, int dir, int c, int& sW, int& sgx, int& sgy) {
   sgy = dir == 1 ? -sW : sW;
 }
 
+// copy the source node into the ghost node with the parities of kind b
 template <class T>
-__device__ __forceinline__ void ghost_body(T* S, const Layout& L, int bc0, int bc1, int dir, int g, int idx) {
-  long gc, sc;
-  int b;
-  if (!ghost_map(L, bc0, bc1, dir, g, idx, gc, sc, b)) return;
-  T* Sg = S + (long)g * NFLD * L.plane;
+__device__ __forceinline__ void ghost_apply(T* Sg, const Layout& L, int b, int dir, long gc, long sc) {
   for (int c = 0; c < 4; ++c) {
     int sW, sgx, sgy;
     ghost_sign(b, dir, c, sW, sgx, sgy);
@@ -166,6 +163,55 @@ __device__ __forceinline__ void ghost_body(T* S, const Layout& L, int bc0, int b
   }
 }
 
+template <class T>
+__device__ __forceinline__ void ghost_body(T* S, const Layout& L, int bc0, int bc1, int dir, int g, int idx) {
+  long gc, sc;
+  int b;
+  if (!ghost_map(L, bc0, bc1, dir, g, idx, gc, sc, b)) return;
+  ghost_apply(S + (long)g * NFLD * L.plane, L, b, dir, gc, sc);
+}
+
+// Split sides (fdcgks_set_sides), at one stage time: kind of each part, the
+// split position along the side, the fixed conservative states, the node
+// geometry for the coordinate along the side.
+struct GhostSides {
+  int kind[4][2];
+  double split[4];
+  double W[4][2][4];
+  double x0, y0, hx, hy;
+};
+
+template <class T>
+__device__ __forceinline__ void ghost_body_sides(T* S, const Layout& L, const GhostSides& gs, int dir, int g,
+                                                 int idx) {
+  const int nxg = g == 0 ? L.nx : L.nxd, nyg = g == 0 ? L.ny : L.nyd;
+  const int tcount = dir == 0 ? nyg : nxg + 2 * GH;
+  if (idx < 0 || idx >= tcount * 2 * GH) return;
+  const int side = (idx / GH) % 2;
+  const int t = idx / (2 * GH) + (dir == 0 ? 0 : -GH);
+  const int sd = 2 * dir + side;
+  // coordinate along the side of the ghost's row (x sides) or column (y
+  // sides), a single-rounded fused product like the split point, so that a
+  // node lying on the split is classified independently of contraction
+  const double pos = t + (g == 0 ? 0.5 : 0.0);
+  const double coord = dir == 0 ? fma(pos, gs.hy, gs.y0) : fma(pos, gs.hx, gs.x0);
+  const int part = coord < gs.split[sd] ? 0 : 1;
+  const int kind = gs.kind[sd][part];
+  long gc, sc;
+  int b;
+  if (!ghost_map(L, kind, kind, dir, g, idx, gc, sc, b)) return;
+  T* Sg = S + (long)g * NFLD * L.plane;
+  if (kind == 4) {   // FIXED
+    for (int c = 0; c < 4; ++c) {
+      Sg[(long)c * L.plane + gc] = (T)gs.W[sd][part][c];
+      Sg[(long)(4 + c) * L.plane + gc] = 0;
+      Sg[(long)(8 + c) * L.plane + gc] = 0;
+    }
+    return;
+  }
+  ghost_apply(Sg, L, b, dir, gc, sc);
+}
+
 enum { UPD_STAGE1 = 0, UPD_STAGE2 = 1, UPD_OPERATOR = 2 };
 
 // message returned by fdcgks_last_error(NULL)
@@ -179,6 +225,7 @@ struct CtxView {
   cudaStream_t stream;
   double* S;        // FP64 state [2][12][plane] (the state itself on the FP64 path)
   bool has_state;
+  bool has_sides;   // fdcgks_set_sides in force
 };
 bool ctx_view(fdcgks_t c, CtxView* v);
 void ctx_set_error(fdcgks_t c, const char* msg);

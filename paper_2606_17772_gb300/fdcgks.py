@@ -12,7 +12,7 @@ import numpy as np
 
 from . import build as _build
 
-BC_PERIODIC, BC_TRANSMISSIVE, BC_SYMMETRY, BC_NOSLIP = 0, 1, 2, 3
+BC_PERIODIC, BC_TRANSMISSIVE, BC_SYMMETRY, BC_NOSLIP, BC_FIXED = 0, 1, 2, 3, 4
 FP64, MIXED = 0, 1
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "non-physical state", 4: "no state loaded",
@@ -25,7 +25,7 @@ EXPORTS = ["fdcgks_create", "fdcgks_destroy", "fdcgks_dims", "fdcgks_set_state",
            "fdcgks_ens_create", "fdcgks_ens_destroy", "fdcgks_ens_set_state", "fdcgks_ens_get_state",
            "fdcgks_ens_run", "fdcgks_ens_status", "fdcgks_ens_set_tiles", "fdcgks_ens_get_tiles",
            "fdcgks_ens_tune", "fdcgks_ens_profile", "fdcgks_ens_info", "fdcgks_ens_last_error",
-           "fdcgks_vjp_steps"]
+           "fdcgks_vjp_steps", "fdcgks_set_sides", "fdcgks_set_time", "fdcgks_get_time"]
 
 ENS_NONPHYSICAL, ENS_NO_WAVE_SPEED, ENS_FROZEN = 1, 2, 4
 
@@ -45,6 +45,31 @@ class Params(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("recon_vars", ctypes.c_int),
     ]
+
+
+class Side(ctypes.Structure):
+    """One boundary side split at split0 + split_speed * t (fdcgks_side)."""
+    _fields_ = [
+        ("kind", ctypes.c_int * 2),
+        ("split0", ctypes.c_double), ("split_speed", ctypes.c_double),
+        ("prim", (ctypes.c_double * 4) * 2),
+    ]
+
+
+def make_sides(sides):
+    """Four fdcgks_side structs from a sequence of 4 dicts with keys kind
+    (2 ints), split0, split_speed (default 0) and prim (2 x 4 floats, default
+    zeros)."""
+    arr = (Side * 4)()
+    for k, sd in enumerate(sides):
+        arr[k].kind[0], arr[k].kind[1] = sd["kind"]
+        arr[k].split0 = sd.get("split0", 0.0)
+        arr[k].split_speed = sd.get("split_speed", 0.0)
+        prim = sd.get("prim", ((0.0,) * 4,) * 2)
+        for q in range(2):
+            for j in range(4):
+                arr[k].prim[q][j] = prim[q][j]
+    return arr
 
 
 class FdcgksError(RuntimeError):
@@ -104,6 +129,9 @@ def load(path=None):
     lib.fdcgks_ens_info.argtypes = [_VP, ctypes.POINTER(_VP), ctypes.POINTER(ctypes.c_longlong),
                                     ctypes.POINTER(ctypes.c_longlong)]
     lib.fdcgks_vjp_steps.argtypes = [_VP, ctypes.c_double, ctypes.c_int, ctypes.c_int] + [_VP] * 12
+    lib.fdcgks_set_sides.argtypes = [_VP, _VP]
+    lib.fdcgks_set_time.argtypes = [_VP, ctypes.c_double]
+    lib.fdcgks_get_time.argtypes = [_VP, ctypes.POINTER(ctypes.c_double)]
     lib.fdcgks_ens_last_error.argtypes = [_VP]
     lib.fdcgks_ens_last_error.restype = ctypes.c_char_p
     lib.fdcgks_last_error.argtypes = [_VP]
@@ -115,7 +143,8 @@ def load(path=None):
                  "fdcgks_nodal_batch", "fdcgks_recon_batch", "fdcgks_set_profiling", "fdcgks_get_profile",
                  "fdcgks_cfl_dt_noalloc", "fdcgks_ens_create", "fdcgks_ens_set_state", "fdcgks_ens_get_state",
                  "fdcgks_ens_run", "fdcgks_ens_status", "fdcgks_ens_set_tiles", "fdcgks_ens_get_tiles",
-                 "fdcgks_ens_tune", "fdcgks_ens_profile", "fdcgks_ens_info", "fdcgks_vjp_steps"):
+                 "fdcgks_ens_tune", "fdcgks_ens_profile", "fdcgks_ens_info", "fdcgks_vjp_steps",
+                 "fdcgks_set_sides", "fdcgks_set_time", "fdcgks_get_time"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -197,7 +226,23 @@ class Solver:
 
     @classmethod
     def from_case(cls, case, precision=FP64):
-        return cls(params_for_case(case, precision))
+        s = cls(params_for_case(case, precision))
+        if getattr(case, "sides", None) is not None:
+            s.set_sides(case.sides)
+        return s
+
+    def set_sides(self, sides):
+        """Split boundary sides (see make_sides); None restores params.bc."""
+        arr = None if sides is None else make_sides(sides)
+        _check(load().fdcgks_set_sides(self._h, arr), self._h)
+
+    def set_time(self, t):
+        _check(load().fdcgks_set_time(self._h, ctypes.c_double(t)), self._h)
+
+    def get_time(self):
+        out = ctypes.c_double()
+        _check(load().fdcgks_get_time(self._h, ctypes.byref(out)), self._h)
+        return out.value
 
     def close(self):
         if getattr(self, "_h", None):

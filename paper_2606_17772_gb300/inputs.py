@@ -13,6 +13,9 @@ Workloads (paper Sec. 5 and the throughput workloads):
   * Sod tube (Sec. 5.2) on a y-periodic strip with transmissive x ends;
   * isentropic vortex on [0, 10]^2 periodic (standard closed form, strength 5);
   * viscous shock tube (Sec. 5.8) on [0, 1] x [0, 0.5] with walls/symmetry;
+  * Woodward-Colella blast waves (Sec. 5.3) between reflecting walls;
+  * double Mach reflection (Sec. 5.5) on [0, 4] x [0, 1] with inflow, outflow,
+    a wall from x = 1/6 and a top boundary following the exact Mach 10 shock;
   * a seeded random smooth perturbation used by the parity tests.
 
 Node placement: primary nodes at cell centres x0 + (i + 1/2) h, dual nodes at
@@ -23,7 +26,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-BC_PERIODIC, BC_TRANSMISSIVE, BC_SYMMETRY, BC_NOSLIP = 0, 1, 2, 3
+BC_PERIODIC, BC_TRANSMISSIVE, BC_SYMMETRY, BC_NOSLIP, BC_FIXED = 0, 1, 2, 3, 4
 
 
 @dataclass
@@ -47,6 +50,7 @@ class Case:
     grad_base: int = 0
     recon_vars: int = 0          # 0 conservative, 1 characteristic components
     prim: object = None          # callable (x, y) -> (rho, U, V, p) arrays
+    sides: object = None         # None, or 4 split-side dicts (kind, split0, split_speed, prim)
     extra: dict = field(default_factory=dict)
 
     @property
@@ -103,7 +107,7 @@ class Case:
                     gamma=self.gamma, mu=self.mu, Pr=self.Pr, bc=tuple(self.bc),
                     flux_variant=self.flux_variant, geno_variant=self.geno_variant,
                     grad_base=self.grad_base, tau_c1=self.tau_c1, tau_c2=self.tau_c2,
-                    recon_vars=self.recon_vars)
+                    recon_vars=self.recon_vars, sides=self.sides)
 
 
 # ---------------------------------------------------------------------------
@@ -180,6 +184,51 @@ def strong_shock_strip(nx=200, ny=1, gamma=1.4, **kw):
         return rho, 0.0, 0.0, rho / gamma
     kw.setdefault("tau_c2", 1.0)
     return Case("strong_shock_strip", nx, ny, 0.0, 1.0, 0.0, ny * h, (1, 1, 0, 0), gamma=gamma, prim=prim, **kw)
+
+
+def woodward_colella(nx=400, ny=1, gamma=1.4, **kw):
+    """Sec. 5.3 interacting blast waves on [0, 1] between reflecting (symmetry) walls,
+    a y-periodic strip of ny rows: (rho, U, p) = (1, 0, 1000) for x < 0.1, (1, 0, 0.01)
+    for 0.1 <= x < 0.9, (1, 0, 100) for x >= 0.9; final time 0.038."""
+    h = 1.0 / nx
+
+    def prim(x, y):
+        p = np.where(x < 0.1, 1000.0, np.where(x < 0.9, 0.01, 100.0))
+        return 1.0, 0.0, 0.0, p
+    kw.setdefault("tau_c1", 0.05)
+    kw.setdefault("tau_c2", 1.0)
+    return Case("woodward_colella", nx, ny, 0.0, 1.0, 0.0, ny * h, (BC_SYMMETRY, BC_SYMMETRY, 0, 0),
+                gamma=gamma, prim=prim, **kw)
+
+
+DMR_POST = (8.0, 4.125 * math.sqrt(3.0), -4.125, 116.5)
+DMR_PRE = (1.4, 0.0, 0.0, 1.0)
+
+
+def double_mach(nx=960, ny=240, **kw):
+    """Sec. 5.5 double Mach reflection on [0, 4] x [0, 1], gamma 1.4, final time 0.2.
+
+    A Mach 10 shock through (1/6, 0) at 60 degrees to the x-axis, post-shock
+    (8, 4.125 sqrt 3, -4.125, 116.5) to its left, pre-shock (1.4, 0, 0, 1) to its
+    right; the shock line x = 1/6 + (y + 20 t)/sqrt 3.  Sides: inflow (post-shock
+    state) at x = 0, outflow (transmissive) at x = 4, outflow below x = 1/6 and a
+    reflecting wall from x = 1/6 on at y = 0, and at y = 1 the exact shock's
+    states, split where the shock meets y = 1 (speed 20/sqrt 3 along x)."""
+    r3 = math.sqrt(3.0)
+
+    def prim(x, y):
+        post = x < 1.0 / 6.0 + y / r3
+        return tuple(np.where(post, a, b) for a, b in zip(DMR_POST, DMR_PRE))
+    fixed_post = dict(kind=(BC_FIXED, BC_FIXED), prim=(DMR_POST, DMR_POST))
+    sides = (fixed_post,
+             dict(kind=(BC_TRANSMISSIVE, BC_TRANSMISSIVE)),
+             dict(kind=(BC_TRANSMISSIVE, BC_SYMMETRY), split0=1.0 / 6.0),
+             dict(kind=(BC_FIXED, BC_FIXED), split0=1.0 / 6.0 + 1.0 / r3, split_speed=20.0 / r3,
+                  prim=(DMR_POST, DMR_PRE)))
+    kw.setdefault("tau_c1", 0.05)
+    kw.setdefault("tau_c2", 1.0)
+    return Case("double_mach", nx, ny, 0.0, 4.0, 0.0, 1.0,
+                (BC_TRANSMISSIVE, BC_TRANSMISSIVE, BC_SYMMETRY, BC_TRANSMISSIVE), prim=prim, sides=sides, **kw)
 
 
 def viscous_shock_tube(nx=1000, ny=500, gamma=1.4, mu=0.005, Pr=0.73, **kw):
