@@ -41,6 +41,13 @@
 //     corners; n dual nodes per periodic direction, n+1 per bounded one.
 //     Ghost layers by periodic wrap, mirror (symmetry / no-slip wall) or
 //     constant extrapolation (transmissive).
+//   * Split boundary sides (Sec. 5.5 names inflow, outflow, a reflecting wall
+//     from x = 1/6 and a top boundary following the exact shock, without
+//     their implementation): each side may be split at a point moving at a
+//     constant speed; ghost nodes take the part their coordinate along the
+//     side falls in; a fixed part holds a given state with zero gradients;
+//     stage 1 of a step fills ghosts at the step's time t, stage 2 at
+//     t + dt/2.
 //   * Positivity safeguard (the paper describes none): a reconstructed
 //     interface state with non-positive density or pressure falls back to the
 //     adjacent node's state with zero normal slope, and chi = 0 there.
@@ -48,7 +55,10 @@
 // Parity unpinned: the form and constants of the collision time tau and the
 // choice tau_0 = tau are exercised by no number the paper prints (its
 // accuracy tables use tau = 0); the no-slip wall treatment is pinned only by
-// symmetry, free-stream and conservation-bound tests.  Dual nodes on a no-slip wall
+// symmetry, free-stream and conservation-bound tests; split sides are pinned
+// by reduction to the unsplit kinds, free streams and the exact speed of a
+// tracked oblique Mach 10 shock, not by a number the paper prints (its
+// double Mach reflection results are figures).  Dual nodes on a no-slip wall
 //     have their velocity, and the averaged momentum gradients along the
 //     wall, set to zero after each stage.
 #include <cmath>

@@ -179,8 +179,11 @@ def make_params(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, mu=0.0, Pr=1.
 
 
 def params_for_case(case, precision=FP64, stream=None):
-    """Params from a paper_2606_17772_gb300.inputs.Case."""
-    return make_params(precision=precision, stream=stream, **case.oracle_kwargs())
+    """Params from a paper_2606_17772_gb300.inputs.Case (its split sides, if
+    any, go through Solver.set_sides, which Solver.from_case calls)."""
+    kw = case.oracle_kwargs()
+    kw.pop("sides", None)
+    return make_params(precision=precision, stream=stream, **kw)
 
 
 def _dptr(t, numel=None):
@@ -435,6 +438,8 @@ class Ensemble:
 
     @classmethod
     def from_cases(cls, cases, precision=FP64):
+        if any(getattr(c, "sides", None) is not None for c in cases):
+            raise ValueError("ensemble members take the boundary kinds of params.bc only (no split sides)")
         return cls([params_for_case(c, precision) for c in cases])
 
     def close(self):

@@ -2,11 +2,18 @@
 
 Host-side driving only (time-step choice, final-step clipping, periodic
 positivity checks); every step runs in the library's kernels.  The module
-entry point runs the viscous shock tube (Sec. 5.8) to its final time and
-prints a JSON summary with the density along the bottom wall and along
-y = 0.075, the two profiles the paper plots.
+entry point runs one of the paper's long runs to its final time and prints a
+JSON summary:
 
-    python -m paper_2606_17772_gb300.runs --nx 1000 --ny 500 --precision mixed --t-end 1.0
+  * viscous shock tube (Sec. 5.8): density along the bottom wall and along
+    y = 0.075, the two profiles the paper plots;
+  * double Mach reflection (Sec. 5.5) to t = 0.2: density extrema and the
+    density on the wall and along y = 0.5 (the figure is a contour plot);
+  * Woodward-Colella blast waves (Sec. 5.3) to t = 0.038: density and
+    pressure along the tube.
+
+    python -m paper_2606_17772_gb300.runs --case viscous_tube --nx 1000 --ny 500 --precision mixed
+    python -m paper_2606_17772_gb300.runs --case double_mach --nx 960 --ny 240 --precision fp64
 """
 import argparse
 import json
@@ -64,18 +71,74 @@ def viscous_shock_tube(nx=1000, ny=500, precision=fdcgks.MIXED, t_end=1.0, cfl=0
     }
 
 
+def _timed_run(case, precision, t_end, cfl):
+    with fdcgks.Solver.from_case(case, precision) as s:
+        s.set_state(*case.initial_state())
+        w0 = time.perf_counter()
+        t, n = advance(s, t_end, cfl)
+        state = s.get_state(device=False)
+        wall = time.perf_counter() - w0
+        t_ctx = s.get_time()
+    return state, t, n, wall, t_ctx
+
+
+def double_mach(nx=960, ny=240, precision=fdcgks.FP64, t_end=0.2, cfl=0.4, flux_variant=62, recon_vars=1):
+    """Run Sec. 5.5's double Mach reflection; returns a summary dict."""
+    case = inputs.double_mach(nx, ny, flux_variant=flux_variant, recon_vars=recon_vars)
+    (Wp, Gp, Wd, Gd), t, n, wall, t_ctx = _timed_run(case, precision, t_end, cfl)
+    xp, yp = case.node_xy(False)
+    xd, _ = case.node_xy(True)
+    k = min(max(int(np.searchsorted(yp[:, 0], 0.5)) - 1, 0), ny - 2)
+    return {
+        "case": "double Mach reflection, %d x %d, FD-CGKS(6-%d), %s reconstruction, %s, CFL %.2f" % (
+            nx, ny, 2 if flux_variant == 62 else 4, "characteristic" if recon_vars else "conservative",
+            "mixed" if precision == fdcgks.MIXED else "fp64", cfl),
+        "t": t, "t_context": t_ctx, "steps": n, "wall_seconds": wall,
+        "node_updates_per_s": n * (nx * ny + case.nxd * case.nyd) / wall,
+        "rho_min": float(min(Wp[0].min(), Wd[0].min())), "rho_max": float(max(Wp[0].max(), Wd[0].max())),
+        "x_wall": xd[0].tolist(), "rho_wall": Wd[0, 0].tolist(),
+        "x_line": xp[0].tolist(), "rho_y05": Wp[0, k].tolist(),
+    }
+
+
+def woodward_colella(nx=400, precision=fdcgks.FP64, t_end=0.038, cfl=0.4, flux_variant=62, recon_vars=0):
+    """Run Sec. 5.3's interacting blast waves; returns a summary dict."""
+    case = inputs.woodward_colella(nx, flux_variant=flux_variant, recon_vars=recon_vars)
+    (Wp, Gp, Wd, Gd), t, n, wall, _ = _timed_run(case, precision, t_end, cfl)
+    xp, _ = case.node_xy(False)
+    rho = Wp[0, 0]
+    p = (case.gamma - 1.0) * (Wp[3, 0] - 0.5 * (Wp[1, 0] ** 2 + Wp[2, 0] ** 2) / rho)
+    return {
+        "case": "Woodward-Colella blast waves, N = %d, FD-CGKS(6-%d), %s, CFL %.2f" % (
+            nx, 2 if flux_variant == 62 else 4, "mixed" if precision == fdcgks.MIXED else "fp64", cfl),
+        "t": t, "steps": n, "wall_seconds": wall,
+        "rho_min": float(rho.min()), "rho_max": float(rho.max()), "p_min": float(p.min()),
+        "x": xp[0].tolist(), "rho": rho.tolist(), "p": p.tolist(),
+    }
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
-    ap.add_argument("--nx", type=int, default=1000)
-    ap.add_argument("--ny", type=int, default=500)
+    ap.add_argument("--case", choices=["viscous_tube", "double_mach", "woodward_colella"], default="viscous_tube")
+    ap.add_argument("--nx", type=int, default=None)
+    ap.add_argument("--ny", type=int, default=None)
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
-    ap.add_argument("--t-end", type=float, default=1.0)
+    ap.add_argument("--t-end", type=float, default=None)
     ap.add_argument("--cfl", type=float, default=0.4)
+    ap.add_argument("--flux", type=int, choices=[62, 64], default=None)
+    ap.add_argument("--recon-vars", type=int, choices=[0, 1], default=None)
     ap.add_argument("--out", default=None, help="write the JSON summary here (default: stdout)")
     a = ap.parse_args()
     from . import build
     build.build()
-    res = viscous_shock_tube(a.nx, a.ny, fdcgks.MIXED if a.precision == "mixed" else fdcgks.FP64, a.t_end, a.cfl)
+    prec = fdcgks.MIXED if a.precision == "mixed" else fdcgks.FP64
+    opt = {k: v for k, v in (("flux_variant", a.flux), ("recon_vars", a.recon_vars)) if v is not None}
+    if a.case == "viscous_tube":
+        res = viscous_shock_tube(a.nx or 1000, a.ny or 500, prec, a.t_end or 1.0, a.cfl)
+    elif a.case == "double_mach":
+        res = double_mach(a.nx or 960, a.ny or 240, prec, a.t_end or 0.2, a.cfl, **opt)
+    else:
+        res = woodward_colella(a.nx or 400, prec, a.t_end or 0.038, a.cfl, **opt)
     text = json.dumps(res)
     if a.out:
         with open(a.out, "w") as f:

@@ -59,6 +59,43 @@ int main(void) {
                     P.tau_c2.offset, P.stream.offset]
 
 
+def test_side_struct_layout_matches_header():
+    src = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "fdcgks.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %d\n", sizeof(fdcgks_side), offsetof(fdcgks_side, kind),
+         offsetof(fdcgks_side, split0), offsetof(fdcgks_side, split_speed), offsetof(fdcgks_side, prim),
+         (int)FDCGKS_BC_FIXED);
+  return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "t")
+        subprocess.run(["gcc", "-I", os.path.dirname(HEADER), c, "-o", exe], check=True)
+        vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
+    S = fdcgks.Side
+    assert vals == [ctypes.sizeof(S), S.kind.offset, S.split0.offset, S.split_speed.offset, S.prim.offset,
+                    fdcgks.BC_FIXED]
+
+
+def test_case_sides_marshalling():
+    from paper_2606_17772_gb300 import inputs
+    case = inputs.double_mach(16, 4)
+    p = fdcgks.params_for_case(case)
+    assert list(p.bc) == list(case.bc)
+    arr = fdcgks.make_sides(case.sides)
+    assert list(arr[3].kind) == [fdcgks.BC_FIXED, fdcgks.BC_FIXED]
+    assert arr[3].split0 == case.sides[3]["split0"] and arr[3].split_speed == case.sides[3]["split_speed"]
+    assert list(arr[3].prim[1]) == list(inputs.DMR_PRE) and list(arr[0].prim[0]) == list(inputs.DMR_POST)
+    assert list(arr[2].kind) == [fdcgks.BC_TRANSMISSIVE, fdcgks.BC_SYMMETRY] and arr[2].split0 == 1.0 / 6.0
+    with pytest.raises(ValueError):
+        fdcgks.Ensemble.from_cases([case])
+
+
 @pytest.mark.parametrize("bad", [dict(nx=0), dict(ny=-3), dict(gamma=1.0), dict(Pr=0.0), dict(mu=-1.0),
                                  dict(bc=(0, 1, 0, 0)), dict(flux_variant=63), dict(geno_variant=5),
                                  dict(precision=7), dict(grad_base=2), dict(x1=-1.0), dict(bc=(9, 9, 0, 0))])
@@ -84,5 +121,8 @@ def test_batch_argument_validation(lib):
 def test_null_context_calls(lib):
     assert lib.fdcgks_step(None, ctypes.c_double(0.1)) == 1
     assert lib.fdcgks_dims(None, None, None, None, None) == 1
+    assert lib.fdcgks_set_sides(None, None) == 1
+    assert lib.fdcgks_set_time(None, ctypes.c_double(0.0)) == 1
+    assert lib.fdcgks_get_time(None, None) == 1
     lib.fdcgks_destroy(None)
     assert lib.fdcgks_status_string(3).decode() == "non-physical state"
