@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--ens-no-tune", action="store_true", help="default tiles (profiling runs)")
     ap.add_argument("--no-viscous-tube", action="store_true")
     ap.add_argument("--vt-steps", type=int, default=100, help="timed steps of the viscous shock tube window")
+    ap.add_argument("--no-double-mach", action="store_true")
+    ap.add_argument("--dmr-steps", type=int, default=100, help="timed FP64 steps of the double Mach window")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--adj-steps", type=int, default=20, help="steps of the adjoint window")
     ap.add_argument("--ensemble-only", action="store_true",
@@ -344,6 +346,47 @@ def run_viscous_tube(args, world):
     return out
 
 
+def run_double_mach(args, world):
+    """Double Mach reflection (Sec. 5.5) at 960 x 240 and 1440 x 360: split
+    sides (inflow, outflow, the wall from x = 1/6, the tracked top shock)
+    evaluated at each stage's time.  Throughput of a window of steps after 20
+    CFL steps (dt held at the CFL value at the window's start), FP64 and
+    mixed; FD-CGKS(6-2) with characteristic reconstruction."""
+    import torch
+    from paper_2606_17772_gb300 import fdcgks, inputs
+    out = {}
+    for nx, ny in ((960, 240), (1440, 360)):
+        case = inputs.double_mach(nx, ny, flux_variant=62, recon_vars=1)
+        nodes = case.nx * case.ny + case.nxd * case.nyd
+        res = {"config": {"workload": "double Mach reflection, [0,4]x[0,1], %dx%d (+%dx%d dual), Mach 10, "
+                                      "FD-CGKS(6-2), characteristic reconstruction; window after 20 CFL-0.4 steps"
+                                      % (nx, ny, case.nxd, case.nyd), "node_updates_per_step": nodes}}
+        for name, prec, k in (("fp64", fdcgks.FP64, args.dmr_steps), ("mixed", fdcgks.MIXED, 4 * args.dmr_steps)):
+            with fdcgks.Solver.from_case(case, prec) as s:
+                s.set_state(*case.initial_state())
+                for _ in range(20):
+                    s.step(s.cfl_dt(0.4))
+                dt = s.cfl_dt(0.4)
+                torch.cuda.synchronize()
+                barrier(world)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                s.steps(dt, k)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = max_over_ranks(e0.elapsed_time(e1), world)
+                bad = s.check()
+                t_end = s.get_time()
+            res[name] = {"value": nodes * k * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / k, "steps": k,
+                         "dt": dt, "t_end": t_end, "nonphysical": bool(bad)}
+        out["%dx%d" % (nx, ny)] = res
+    # the blast waves run to their final time (host-driven CFL loop, one strip row)
+    from paper_2606_17772_gb300 import runs
+    wc = runs.woodward_colella(400, fdcgks.FP64)
+    out["woodward_colella"] = {k: wc[k] for k in ("case", "t", "steps", "wall_seconds", "rho_max", "p_min")}
+    return out
+
+
 def run_adjoint(args, world):
     """Gradient of a density misfit after a window of steps of the 256^2 vortex
     (strength 5) with respect to the primary initial state: forward and
@@ -534,6 +577,8 @@ def main():
         line["ensemble"] = run_ensemble(args, world, rank, local)
     if not args.no_viscous_tube:
         line["viscous_tube"] = run_viscous_tube(args, world)
+    if not args.no_double_mach:
+        line["double_mach"] = run_double_mach(args, world)
     if not args.no_adjoint:
         line["adjoint"] = run_adjoint(args, world)
 

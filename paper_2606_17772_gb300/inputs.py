@@ -10,7 +10,7 @@ CUDA path and the CPU oracle both take their inputs from here.
 Workloads (paper Sec. 5 and the throughput workloads):
   * density wave (Sec. 5.1): rho = 1 + 0.2 sin(pi (x + y)), U = V = 1, p = 1 on
     [0, 2]^2 periodic; its 1-D form on a y-periodic strip;
-  * Sod tube (Sec. 5.2) on a y-periodic strip with transmissive x ends;
+  * Sod and Lax tubes (Sec. 5.2) on a y-periodic strip with transmissive x ends;
   * isentropic vortex on [0, 10]^2 periodic (standard closed form, strength 5);
   * viscous shock tube (Sec. 5.8) on [0, 1] x [0, 0.5] with walls/symmetry;
   * Woodward-Colella blast waves (Sec. 5.3) between reflecting walls;
@@ -170,6 +170,21 @@ def sod_strip(nx=200, ny=4, **kw):
     kw.setdefault("tau_c1", 0.05)
     kw.setdefault("tau_c2", 1.0)
     return Case("sod_strip", nx, ny, 0.0, 1.0, 0.0, ny * h, (1, 1, 0, 0), prim=prim, **kw)
+
+
+def lax_strip(nx=100, ny=1, **kw):
+    """Sec. 5.2 Lax tube on [0,1], y-periodic strip of ny rows, transmissive x ends:
+    (rho, U, p) = (0.445, 0.698, 3.528) for x < 0.5 and (0.5, 0, 0.571) for x >= 0.5;
+    final time 0.16."""
+    h = 1.0 / nx
+
+    def prim(x, y):
+        right = x >= 0.5
+        return (np.where(right, 0.5, 0.445), np.where(right, 0.0, 0.698), 0.0,
+                np.where(right, 0.571, 3.528))
+    kw.setdefault("tau_c1", 0.05)
+    kw.setdefault("tau_c2", 1.0)
+    return Case("lax_strip", nx, ny, 0.0, 1.0, 0.0, ny * h, (1, 1, 0, 0), prim=prim, **kw)
 
 
 def strong_shock_strip(nx=200, ny=1, gamma=1.4, **kw):

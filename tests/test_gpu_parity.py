@@ -176,6 +176,9 @@ STRONG = {
     # the viscous shock tube itself (no-slip walls, symmetry top) on a coarse grid
     "viscous_tube_24x12": lambda: (inputs.viscous_shock_tube(24, 12), 6),
     "strong_shock_strip_char_100x2": lambda: (inputs.strong_shock_strip(100, 2, recon_vars=1), 12),
+    # Sec. 5.2 Lax tube (a moving initial state), 6-4 and 6-2 fluxes
+    "lax_strip_100x2": lambda: (inputs.lax_strip(100, 2), 20),
+    "lax_strip_62_100x2": lambda: (inputs.lax_strip(100, 2, flux_variant=62), 20),
 }
 
 
