@@ -48,6 +48,9 @@
 //     side falls in; a fixed part holds a given state with zero gradients;
 //     stage 1 of a step fills ghosts at the step's time t, stage 2 at
 //     t + dt/2.
+//   * One-dimensional scheme (Sec. 2): nodes at cell centres, the 1-D BGK
+//     gas as the 2-D one with V = 0 and no y-variation, the gradient update
+//     from the interface solve's own W^(l,r); reflecting ends mirror U.
 //   * Positivity safeguard (the paper describes none): a reconstructed
 //     interface state with non-positive density or pressure falls back to the
 //     adjacent node's state with zero normal slope, and chi = 0 there.
@@ -1188,6 +1191,236 @@ void s2o4_step(const Scheme& S, Grid& P, Grid& D, double dt, double t) {
 }
 
 }  // namespace
+
+// ===========================================================================
+// The paper's one-dimensional scheme (Sec. 2 with the reconstruction of
+// Sec. 3): one grid of n nodes at x0 + (j + 1/2) h carrying W = (rho, rho U,
+// rho E) and the averaged gradient W_x over [x_{j-1/2}, x_{j+1/2}].  The
+// one-dimensional BGK gas is the two-dimensional one with V = 0 and no
+// y-variation (K + 1 = (3 - gamma)/(gamma - 1) internal degrees of freedom
+// then take up the y-velocity), so the kinetic solves are the 2-D ones with
+// those inputs.  The interface values that update the averaged gradient
+// (Eq. define-averaged-gradient) are the solve's own W^(l,r) of Eq. eq:W-model:
+// there is no second direction to average with.
+// ===========================================================================
+namespace {
+
+struct Line1 {
+  int n;
+  std::vector<double> f;   // 6 fields (W 3, W_x 3), each n + 2G entries
+  double& at(int field, int j) { return f[(size_t)field * (n + 2 * G) + (j + G)]; }
+};
+
+// ghost nodes: periodic wrap, constant extrapolation with zero gradient
+// (transmissive), or mirror about the end (reflecting: U odd, and each
+// gradient with the opposite parity of its field)
+void fill_ghosts_1d(Line1& L, const int bc[2]) {
+  for (int side = 0; side < 2; ++side) {
+    const int b = bc[side];
+    for (int k = 1; k <= G; ++k) {
+      const int ghost = side == 0 ? -k : L.n - 1 + k;
+      int src;
+      if (b == OBC_PERIODIC) src = ((ghost % L.n) + L.n) % L.n;
+      else if (b == OBC_TRANSMISSIVE) src = side == 0 ? 0 : L.n - 1;
+      else src = side == 0 ? k - 1 : L.n - k;
+      for (int c = 0; c < 3; ++c) {
+        double w = L.at(c, src), gx = L.at(3 + c, src);
+        if (b == OBC_TRANSMISSIVE) {
+          gx = 0.0;
+        } else if (b == OBC_SYMMETRY) {
+          const double s = c == 1 ? -1.0 : 1.0;
+          w *= s;
+          gx *= -s;
+        }
+        L.at(c, ghost) = w;
+        L.at(3 + c, ghost) = gx;
+      }
+    }
+  }
+}
+
+// (rho, rho U, rho E) <-> (rho, rho U, rho V = 0, rho E)
+const int C4[3] = {0, 1, 3};
+
+struct Stage1D {
+  std::vector<double> L, Lt, gb, gt;   // [3][n] each
+};
+
+Stage1D stage_1d(const Scheme& S, Line1& Ln, double dt) {
+  const int n = Ln.n;
+  const double h = S.hx;
+  fill_ghosts_1d(Ln, S.p.bc);
+  // interfaces k + 1/2, k = -2..n: reconstruction from nodes k-1..k+2, safeguard, kinetic solve
+  std::vector<IfaceOut> I(n + 3);
+  std::vector<double> chi(n + 3);
+  const double zero[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k = -2; k <= n; ++k) {
+    double Q[4][4] = {}, Qx[4][4] = {};
+    for (int m = 0; m < 4; ++m)
+      for (int c = 0; c < 3; ++c) {
+        Q[m][C4[c]] = Ln.at(c, k - 1 + m);
+        Qx[m][C4[c]] = Ln.at(3 + c, k - 1 + m);
+      }
+    double Wl[4], Wr[4], Wln[4], Wrn[4], ch;
+    if (S.p.recon_vars == 1) recon_line_char(S.gc, S.gas.gamma, 0, Q, Qx, h, Wl, Wr, Wln, Wrn, &ch);
+    else recon_line(S.gc, Q, Qx, h, Wl, Wr, Wln, Wrn, &ch);
+    positivity_fallback(Q, Wl, Wr, Wln, Wrn, &ch);
+    I[k + 2] = iface_solve(S.gas, 0, dt, Wl, Wr, Wln, Wrn, zero);
+    chi[k + 2] = ch;
+  }
+  // nodal fluxes at nodes -1..n (Sec. 2.1), from the node value and its GENO derivative
+  std::vector<double> NF((size_t)(n + 2) * 8);   // F[4], F_t[4] per node
+  for (int j = -1; j <= n; ++j) {
+    double W[4] = {}, Wx[4] = {};
+    for (int c = 0; c < 3; ++c) {
+      const double q[3] = {Ln.at(c, j - 1), Ln.at(c, j), Ln.at(c, j + 1)};
+      const double g[3] = {Ln.at(3 + c, j - 1), Ln.at(3 + c, j), Ln.at(3 + c, j + 1)};
+      double chin;
+      W[C4[c]] = q[1];
+      recon_node(S.gc, q, g, h, &Wx[C4[c]], &chin);
+    }
+    double o[16];
+    nodal_flux(S.gas, dt, W, Wx, zero, o);
+    for (int c = 0; c < 4; ++c) {
+      NF[(size_t)(j + 1) * 8 + c] = o[c];
+      NF[(size_t)(j + 1) * 8 + 4 + c] = o[8 + c];
+    }
+  }
+  // node operator (Eqs. fd-conservative-form, fd-conservative-flux*, define-averaged-gradient)
+  Stage1D so;
+  so.L.assign((size_t)3 * n, 0.0);
+  so.Lt = so.L;
+  so.gb = so.L;
+  so.gt = so.L;
+  const int fv = S.p.flux_variant;
+  auto flux = [&](int k, int c4, bool t) {   // compact flux at interface k + 1/2
+    double Fi[3], Fn[2];
+    for (int m = 0; m < 3; ++m) Fi[m] = t ? I[k + 1 + m].Fht[c4] : I[k + 1 + m].Fh[c4];
+    Fn[0] = NF[(size_t)(k + 1) * 8 + (t ? 4 : 0) + c4];
+    Fn[1] = NF[(size_t)(k + 2) * 8 + (t ? 4 : 0) + c4];
+    return compact_flux(fv, chi[k + 2], Fi, Fn);
+  };
+  for (int j = 0; j < n; ++j)
+    for (int c = 0; c < 3; ++c) {
+      const int c4 = C4[c];
+      const size_t o = (size_t)c * n + j;
+      so.L[o] = -(flux(j, c4, false) - flux(j - 1, c4, false)) / h;
+      so.Lt[o] = -(flux(j, c4, true) - flux(j - 1, c4, true)) / h;
+      so.gb[o] = (I[j + 2].Whl[c4] - I[j + 1].Whr[c4]) / h;
+      so.gt[o] = (I[j + 2].Whlt[c4] - I[j + 1].Whrt[c4]) / h;
+    }
+  return so;
+}
+
+bool make_scheme_1d(const oracle_params* p, Scheme& S) {
+  S.p = *p;
+  if (p->nx < 1) return false;
+  const bool a = p->bc[0] == OBC_PERIODIC, b = p->bc[1] == OBC_PERIODIC;
+  if (a != b) return false;
+  for (int k = 0; k < 2; ++k)
+    if (p->bc[k] < OBC_PERIODIC || p->bc[k] > OBC_SYMMETRY) return false;
+  if (!a && p->nx < 3) return false;
+  if (p->recon_vars != 0 && p->recon_vars != 1) return false;
+  S.nxd = S.nyd = 0;
+  S.hx = (p->x1 - p->x0) / p->nx;
+  S.hy = S.hx;
+  S.gas.gamma = p->gamma;
+  S.gas.K = (4.0 - 2.0 * p->gamma) / (p->gamma - 1.0);
+  S.gas.mu = p->mu;
+  S.gas.Pr = p->Pr;
+  S.gas.c1 = p->tau_c1;
+  S.gas.c2 = p->tau_c2;
+  S.gc = geno_const(p->geno_variant);
+  return true;
+}
+
+Line1 load_line(int n, const double* W, const double* Gx) {
+  Line1 L;
+  L.n = n;
+  L.f.assign((size_t)6 * (n + 2 * G), 0.0);
+  for (int c = 0; c < 3; ++c)
+    for (int j = 0; j < n; ++j) {
+      L.at(c, j) = W[(size_t)c * n + j];
+      L.at(3 + c, j) = Gx[(size_t)c * n + j];
+    }
+  return L;
+}
+
+// one S2O4 step (Eqs. eq-nodal-update, eq-interface-update) of the line
+void s2o4_step_1d(const Scheme& S, Line1& Ln, double dt) {
+  const int n = Ln.n;
+  const bool readA = S.p.grad_base == 1;
+  Line1 L0 = Ln;
+  Stage1D s1 = stage_1d(S, Ln, dt);
+  for (int c = 0; c < 3; ++c)
+    for (int j = 0; j < n; ++j) {
+      const size_t o = (size_t)c * n + j;
+      Ln.at(c, j) = L0.at(c, j) + 0.5 * dt * s1.L[o] + 0.125 * dt * dt * s1.Lt[o];
+      const double base = readA ? L0.at(3 + c, j) : s1.gb[o];
+      Ln.at(3 + c, j) = base + 0.5 * dt * s1.gt[o];
+    }
+  Stage1D s2 = stage_1d(S, Ln, dt);
+  for (int c = 0; c < 3; ++c)
+    for (int j = 0; j < n; ++j) {
+      const size_t o = (size_t)c * n + j;
+      Ln.at(c, j) = L0.at(c, j) + dt * s1.L[o] + 0.5 * dt * dt * s1.Lt[o] + dt * dt / 3.0 * (s2.Lt[o] - s1.Lt[o]);
+      const double base = readA ? L0.at(3 + c, j) : s1.gb[o];
+      Ln.at(3 + c, j) = base + dt * s2.gt[o];
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+// nsteps S2O4 steps of the one-dimensional scheme; W, Gx: [3][n] in place
+int oracle_steps_1d(const oracle_params* p, double dt, int nsteps, double* W, double* Gx) {
+  Scheme S;
+  if (!make_scheme_1d(p, S)) return 1;
+  Line1 L = load_line(p->nx, W, Gx);
+  for (int s = 0; s < nsteps; ++s) s2o4_step_1d(S, L, dt);
+  for (int c = 0; c < 3; ++c)
+    for (int j = 0; j < p->nx; ++j) {
+      W[(size_t)c * p->nx + j] = L.at(c, j);
+      Gx[(size_t)c * p->nx + j] = L.at(3 + c, j);
+    }
+  return 0;
+}
+
+// one stage's operator of the one-dimensional scheme: L, L_t, re-evaluated
+// averaged gradient and its time derivative, [3][n] each
+int oracle_stage_1d(const oracle_params* p, double dt, const double* W, const double* Gx, double* L, double* Lt,
+                    double* gb, double* gt) {
+  Scheme S;
+  if (!make_scheme_1d(p, S)) return 1;
+  Line1 Ln = load_line(p->nx, W, Gx);
+  Stage1D o = stage_1d(S, Ln, dt);
+  std::memcpy(L, o.L.data(), o.L.size() * sizeof(double));
+  std::memcpy(Lt, o.Lt.data(), o.Lt.size() * sizeof(double));
+  std::memcpy(gb, o.gb.data(), o.gb.size() * sizeof(double));
+  std::memcpy(gt, o.gt.data(), o.gt.size() * sizeof(double));
+  return 0;
+}
+
+// CFL time step of the line: CFL min h/(|U| + c), and CFL h^2/(8 nu_max) with viscosity
+double oracle_cfl_dt_1d(const oracle_params* p, double cfl, const double* W) {
+  Scheme S;
+  if (!make_scheme_1d(p, S)) return -1.0;
+  const int n = p->nx;
+  double best = 1e300, numax = 0.0;
+  for (int j = 0; j < n; ++j) {
+    const double rho = W[j], U = W[n + j] / rho;
+    const double pr = (p->gamma - 1.0) * (W[2 * n + j] - 0.5 * rho * U * U);
+    const double c = std::sqrt(p->gamma * pr / rho);
+    best = std::fmin(best, S.hx / (std::fabs(U) + c));
+    numax = std::fmax(numax, p->mu / rho);
+  }
+  double dt = cfl * best;
+  if (numax > 0.0) dt = std::fmin(dt, cfl * S.hx * S.hx / (8.0 * numax));
+  return dt;
+}
+
+}  // extern "C"
 
 // ===========================================================================
 // C entry points (used by tests through ctypes)

@@ -44,6 +44,7 @@ def lib():
         _lib.oracle_cfl_dt.restype = ctypes.c_double
         _lib.oracle_maxwell_moment.restype = ctypes.c_double
         _lib.oracle_compact_flux.restype = ctypes.c_double
+        _lib.oracle_cfl_dt_1d.restype = ctypes.c_double
     return _lib
 
 
@@ -105,6 +106,33 @@ def steps(p, dt, nsteps, Wp, Gp, Wd, Gd):
     if rc != 0:
         raise ValueError("oracle_steps failed")
     return Wp, Gp, Wd, Gd
+
+
+def steps_1d(p, dt, nsteps, W, Gx):
+    """The one-dimensional scheme (Sec. 2): ``nsteps`` S2O4 steps of the line of
+    p.nx nodes (bc[0], bc[1] at its ends); W, Gx: [3][n] (rho, rho U, rho E) and
+    their averaged gradients.  Returns new arrays."""
+    n = p.nx
+    W = _arr(W, 3 * n).copy().reshape(3, n)
+    Gx = _arr(Gx, 3 * n).copy().reshape(3, n)
+    if lib().oracle_steps_1d(ctypes.byref(p), ctypes.c_double(dt), ctypes.c_int(nsteps), _ptr(W), _ptr(Gx)) != 0:
+        raise ValueError("oracle_steps_1d failed")
+    return W, Gx
+
+
+def stage_1d(p, dt, W, Gx):
+    """One stage's operator of the line: dict L, Lt, gb, gt ([3][n] each)."""
+    n = p.nx
+    out = {k: np.zeros((3, n)) for k in ("L", "Lt", "gb", "gt")}
+    rc = lib().oracle_stage_1d(ctypes.byref(p), ctypes.c_double(dt), _ptr(_arr(W, 3 * n)), _ptr(_arr(Gx, 3 * n)),
+                               *(_ptr(out[k]) for k in ("L", "Lt", "gb", "gt")))
+    if rc != 0:
+        raise ValueError("oracle_stage_1d failed")
+    return out
+
+
+def cfl_dt_1d(p, cfl, W):
+    return lib().oracle_cfl_dt_1d(ctypes.byref(p), ctypes.c_double(cfl), _ptr(_arr(W, 3 * p.nx)))
 
 
 def stage(p, dt, Wp, Gp, Wd, Gd):

@@ -110,6 +110,15 @@ class Case:
                     recon_vars=self.recon_vars, sides=self.sides)
 
 
+def line_state(case):
+    """Initial data of the one-dimensional scheme (Sec. 2) from a strip case:
+    (W [3][n], Wx [3][n]), the first primary row's (rho, rho U, rho E) and
+    their averaged x-gradients."""
+    Wp, Gp, _, _ = case.initial_state()
+    idx = [0, 1, 3]
+    return np.ascontiguousarray(Wp[idx, 0, :]), np.ascontiguousarray(Gp[0][idx][:, 0, :])
+
+
 # ---------------------------------------------------------------------------
 # analytic initial conditions
 # ---------------------------------------------------------------------------
