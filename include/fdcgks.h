@@ -338,6 +338,65 @@ fdcgks_status fdcgks_ens_info(fdcgks_ens_t ens, void** stream, long long* launch
 /* Message of the last failed call on ens (NULL: as fdcgks_last_error(NULL)). */
 const char* fdcgks_ens_last_error(fdcgks_ens_t ens);
 
+/* ---- The paper's one-dimensional scheme (Sec. 2) on a batch of lines ----
+ * Each line is one grid of n nodes at x0 + (j + 1/2) h, h = (x1 - x0) / n,
+ * carrying W = (rho, rho U, rho E) and the averaged gradient W_x over
+ * [x_{j-1/2}, x_{j+1/2}] (Eq. define-averaged-gradient).  A stage
+ * reconstructs the interface states (Sec. 3, GENO, the same options as the
+ * 2-D scheme), solves the BGK interface problem (App. A; the 1-D gas is the
+ * 2-D one with V = 0 and no y-variation), forms the nodal fluxes and the
+ * compact flux (Eqs. fd-conservative-flux*) and updates W and W_x with
+ * S2O4 (Eqs. eq-nodal-update, eq-interface-update); the interface values
+ * of the gradient update are the solve's own W^(l,r) (Eq. eq:W-model).
+ * The lines share grid, gas and options and evolve independently: one
+ * thread block advances one line through whole steps, so a call is one
+ * kernel launch whatever the number of steps.  FP64 only.
+ *   - bc[0], bc[1]: PERIODIC (both ends), TRANSMISSIVE or SYMMETRY
+ *     (a reflecting wall); n >= 3 (bounded) or >= 1 (periodic); batch >= 1.
+ *   - State arrays W [batch][3][n] and Wx [batch][3][n], row-major; host or
+ *     device (on_device) memory owned by the caller.
+ *   - Each line keeps its own time (0 after set_state), advanced by every
+ *     step of fdcgks_line_steps and fdcgks_line_run.
+ *   - Errors: FDCGKS_ERR_ARG for invalid arguments (nothing changed),
+ *     FDCGKS_ERR_CUDA for a failed allocation, copy or launch; messages via
+ *     fdcgks_line_last_error (fdcgks_last_error(NULL) for a failed create). */
+typedef struct {
+  int n, batch;
+  double x0, x1;
+  double gamma, mu, Pr;
+  int bc[2];
+  int flux_variant, geno_variant, grad_base;
+  double tau_c1, tau_c2;
+  int recon_vars;
+  void* stream;                /* cudaStream_t, NULL = default stream */
+} fdcgks_line_params;
+typedef struct fdcgks_line_ctx* fdcgks_line_t;
+fdcgks_status fdcgks_line_create(const fdcgks_line_params* params, fdcgks_line_t* out);
+void fdcgks_line_destroy(fdcgks_line_t ctx);
+fdcgks_status fdcgks_line_set_state(fdcgks_line_t ctx, const double* W, const double* Wx, int on_device);
+fdcgks_status fdcgks_line_get_state(fdcgks_line_t ctx, double* W, double* Wx, int on_device);
+/* nsteps steps of size dt > 0 on every line (one launch, asynchronous). */
+fdcgks_status fdcgks_line_steps(fdcgks_line_t ctx, double dt, int nsteps);
+/* Each line advances from its own time to t_end with its own CFL steps,
+ * dt = cfl min h/(|U| + c) (and cfl h^2/(8 nu_max) when mu > 0), the last
+ * one clipped to land on t_end, at most max_steps steps; a line whose time
+ * step is not positive and finite stops and sets status bit 1, a line with
+ * a non-physical node after a step stops there (bit 0).  One launch;
+ * waits for it.  t[batch] and steps[batch] (host, either may be NULL)
+ * receive each line's time and the number of steps it took. */
+fdcgks_status fdcgks_line_run(fdcgks_line_t ctx, double t_end, double cfl, int max_steps, double* t, int* steps);
+/* One stage's operator of the current state with time step dt: L, dL/dt,
+ * the averaged gradient re-evaluated from the interface solution and its
+ * time derivative, [batch][3][n] device arrays each. */
+fdcgks_status fdcgks_line_stage_operator(fdcgks_line_t ctx, double dt, double* L, double* Lt, double* gb,
+                                         double* gt);
+/* Status bits of each line since set_state (bit 0: a node left the physical
+ * states after a stage; bit 1: no positive finite CFL time step): flags
+ * [batch] (host, may be NULL) and their OR in *any (may be NULL).  Waits. */
+fdcgks_status fdcgks_line_check(fdcgks_line_t ctx, int* flags, int* any);
+/* Message of the last failed call on ctx (NULL: as fdcgks_last_error(NULL)). */
+const char* fdcgks_line_last_error(fdcgks_line_t ctx);
+
 /* Message of the last failed call on ctx (or of the last failed
  * context-free call when ctx is NULL). */
 const char* fdcgks_last_error(fdcgks_t ctx);

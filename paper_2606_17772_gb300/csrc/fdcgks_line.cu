@@ -1,0 +1,541 @@
+// The paper's one-dimensional scheme (Sec. 2, with the reconstruction of
+// Sec. 3) on a batch of independent lines.
+//
+// One line is one grid of n nodes carrying W = (rho, rho U, rho E) and the
+// averaged gradient W_x (Eq. define-averaged-gradient).  One thread block
+// owns one line for a whole call: a step is
+//
+//   stage 1: ghosts(S) -> interface solves + nodal fluxes -> update S -> T
+//   stage 2: ghosts(T) -> interface solves + nodal fluxes -> update T -> S
+//
+// with block barriers between the phases, so a call runs any number of
+// steps (fixed dt, or each line's own CFL dt found by a block reduction)
+// in a single launch, and the lines of a batch run side by side on the
+// SMs.  The line's working arrays stay in global memory (L2-resident for
+// the line sizes of Sec. 5); the per-node device functions are the 2-D
+// path's: the line reconstruction of the 2-D interface points with the
+// y-momentum set to zero, the x-normal kinetic solve with V = 0 and no
+// tangential variation (the 1-D BGK gas is the 2-D one restricted so), and
+// the nodal solve with W_y = 0.  FP64.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/fdcgks.h"
+#include "fdcgks_kernels.cuh"
+
+using namespace fdk;
+
+namespace {
+
+constexpr int LT = 128;    // threads per line block
+constexpr int NPF = 19;    // interface outputs: F, F_t, W^l, W^r, W^l_t, W^r_t (3 each), chi
+
+enum { LINE_STEPS = 0, LINE_RUN = 1, LINE_OPERATOR = 2 };
+
+struct LineArgs {
+  int n, np;                 // nodes; padded length n + 2 GH
+  int bc0, bc1, fv, grad_base, recon_vars;
+  double h, ih, gamma, mu;
+  GenoK<double> geno;
+  GasK<double> gas;          // the time-step fields are set per step
+  double* S;                 // [batch][6][np] state (W 3, W_x 3)
+  double* T;                 // [batch][6][np] stage-1 state
+  double* P;                 // [batch][NPF][n + 3] interfaces k + 1/2, k = -2..n
+  double* NF;                // [batch][6][n + 2] nodal F, F_t at nodes -1..n
+  double* A;                 // [batch][6][n] S2O4 accumulator and gradient base
+  double* tl;                // [batch] line time
+  int* ns;                   // [batch] steps taken by the last run
+  int* flag;                 // [batch] status bits
+  double* op[4];             // LINE_OPERATOR outputs [batch][3][n]
+};
+
+// conservative component c (0..2) of a line <-> slot of the 2-D 4-vector
+__device__ __forceinline__ int slot4(int c) { return c == 2 ? 3 : c; }
+
+// ghost nodes of buffer B: periodic wrap, constant extrapolation with zero
+// gradient (transmissive), mirror with U odd and each gradient of the
+// opposite parity to its field (reflecting)
+__device__ void line_ghosts(const LineArgs& a, double* B) {
+  for (int idx = threadIdx.x; idx < 2 * GH; idx += blockDim.x) {
+    const int side = idx / GH, k = 1 + idx % GH;
+    const int b = side == 0 ? a.bc0 : a.bc1;
+    const int ghost = side == 0 ? -k : a.n - 1 + k;
+    int src;
+    if (b == FDCGKS_BC_PERIODIC) src = ((ghost % a.n) + a.n) % a.n;
+    else if (b == FDCGKS_BC_TRANSMISSIVE) src = side == 0 ? 0 : a.n - 1;
+    else src = side == 0 ? k - 1 : a.n - k;
+    for (int c = 0; c < 3; ++c) {
+      double w = B[c * a.np + GH + src], gx = B[(3 + c) * a.np + GH + src];
+      if (b == FDCGKS_BC_TRANSMISSIVE) {
+        gx = 0.0;
+      } else if (b == FDCGKS_BC_SYMMETRY) {
+        const double s = c == 1 ? -1.0 : 1.0;
+        w *= s;
+        gx *= -s;
+      }
+      B[c * a.np + GH + ghost] = w;
+      B[(3 + c) * a.np + GH + ghost] = gx;
+    }
+  }
+}
+
+// interface solves (k = -2..n) and nodal fluxes (j = -1..n) of buffer B
+__device__ void line_fluxes(const LineArgs& a, const GasK<double>& gas, const double* B, double* P, double* NF) {
+  const int ni = a.n + 3, nn = a.n + 2;
+  for (int idx = threadIdx.x; idx < ni + nn; idx += blockDim.x) {
+    if (idx < ni) {
+      const int k = idx - 2;   // interface k + 1/2 from nodes k-1..k+2
+      auto ld = [&](int, int e, int f) -> double {
+        const int s = f & 3;
+        if (s == 2) return 0.0;                       // rho V
+        const int c = s == 3 ? 2 : s;
+        return B[((f < 4 ? 0 : 3) + c) * a.np + GH + (k - 1 + e)];
+      };
+      double vl[4], dl[4], vr[4], dr[4], chi;
+      if (a.recon_vars) recon_line_char(a.geno, gas.gm1, 0, ld, 0, a.h, a.ih, vl, dl, vr, dr, chi);
+      else recon_line_ld(a.geno, ld, 0, a.h, a.ih, vl, dl, vr, dr, chi);
+      const double zero[4] = {0.0, 0.0, 0.0, 0.0};
+      IfaceOut<double> o;
+      iface_solve(gas, 0, vl, vr, dl, dr, zero, true, o);
+      double* q = P + idx;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int s = slot4(c);
+        q[(0 + c) * ni] = o.F[s];
+        q[(3 + c) * ni] = o.Ft[s];
+        q[(6 + c) * ni] = o.Wl[s];
+        q[(9 + c) * ni] = o.Wr[s];
+        q[(12 + c) * ni] = o.Wlt[s];
+        q[(15 + c) * ni] = o.Wrt[s];
+      }
+      q[18 * ni] = chi;
+    } else {
+      const int j = idx - ni - 1;   // node j: value and GENO x-derivative
+      double W[4] = {0.0, 0.0, 0.0, 0.0}, Wx[4] = {0.0, 0.0, 0.0, 0.0}, Wy[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double* w = B + c * a.np + GH + j;
+        const double* g = B + (3 + c) * a.np + GH + j;
+        const double q[3] = {w[-1], w[0], w[1]}, gx[3] = {g[-1], g[0], g[1]};
+        W[slot4(c)] = w[0];
+        Wx[slot4(c)] = recon_node(a.geno, q, gx, a.h, a.ih);
+      }
+      double F[4], G[4], Ft[4], Gt[4];
+      nodal_flux(gas, W, Wx, Wy, F, G, Ft, Gt);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        NF[c * nn + j + 1] = F[slot4(c)];
+        NF[(3 + c) * nn + j + 1] = Ft[slot4(c)];
+      }
+    }
+  }
+}
+
+// node operator (Eqs. fd-conservative-form, fd-conservative-flux*,
+// define-averaged-gradient) and the S2O4 stage update Bin -> Bout
+__device__ void line_update(const LineArgs& a, int mode, int stage, double dt, const double* P, const double* NF,
+                            const double* Bin, double* Bout, double* A, int line, int* flag) {
+  const int ni = a.n + 3, nn = a.n + 2;
+  for (int j = threadIdx.x; j < a.n; j += blockDim.x) {
+    const double chip = P[18 * ni + j + 2], chim = P[18 * ni + j + 1];
+    double L[3], Lt[3], gb[3], gt[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double* F = P + c * ni;
+      const double* Ft = P + (3 + c) * ni;
+      const double* nF = NF + c * nn;
+      const double* nFt = NF + (3 + c) * nn;
+      // interface k + 1/2 sits at P index k + 2, node k at NF index k + 1
+      const double fp = compact_flux(a.fv, chip, F[j + 1], F[j + 2], F[j + 3], nF[j + 1], nF[j + 2]);
+      const double fm = compact_flux(a.fv, chim, F[j], F[j + 1], F[j + 2], nF[j], nF[j + 1]);
+      const double ftp = compact_flux(a.fv, chip, Ft[j + 1], Ft[j + 2], Ft[j + 3], nFt[j + 1], nFt[j + 2]);
+      const double ftm = compact_flux(a.fv, chim, Ft[j], Ft[j + 1], Ft[j + 2], nFt[j], nFt[j + 1]);
+      L[c] = -(fp - fm) * a.ih;
+      Lt[c] = -(ftp - ftm) * a.ih;
+      gb[c] = (P[(6 + c) * ni + j + 2] - P[(9 + c) * ni + j + 1]) * a.ih;
+      gt[c] = (P[(12 + c) * ni + j + 2] - P[(15 + c) * ni + j + 1]) * a.ih;
+    }
+    if (mode == LINE_OPERATOR) {
+      const long o = (long)line * 3 * a.n + j;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        a.op[0][o + c * a.n] = L[c];
+        a.op[1][o + c * a.n] = Lt[c];
+        a.op[2][o + c * a.n] = gb[c];
+        a.op[3][o + c * a.n] = gt[c];
+      }
+      continue;
+    }
+    double W[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (stage == 0) {
+        const double Wn = Bin[c * a.np + GH + j];
+        W[c] = Wn + 0.5 * dt * L[c] + 0.125 * dt * dt * Lt[c];
+        A[c * a.n + j] = Wn + dt * L[c] + dt * dt / 6.0 * Lt[c];
+        const double base = a.grad_base ? Bin[(3 + c) * a.np + GH + j] : gb[c];
+        A[(3 + c) * a.n + j] = base;
+        Bout[(3 + c) * a.np + GH + j] = base + 0.5 * dt * gt[c];
+      } else {
+        W[c] = A[c * a.n + j] + dt * dt / 3.0 * Lt[c];
+        Bout[(3 + c) * a.np + GH + j] = A[(3 + c) * a.n + j] + dt * gt[c];
+      }
+      Bout[c * a.np + GH + j] = W[c];
+    }
+    const double p = W[2] - 0.5 * W[1] * W[1] / W[0];
+    if (!(W[0] > 0.0) || !(p > 0.0)) atomicOr(flag, 1);
+  }
+}
+
+// the line's CFL time step (the same in every thread of the block)
+__device__ double line_cfl(const LineArgs& a, const double* B, double cfl) {
+  __shared__ double sr[LT / 32], sn[LT / 32];
+  double rate = 0.0, numax = 0.0;
+  for (int j = threadIdx.x; j < a.n; j += blockDim.x)
+    cfl_rates(B[GH + j], B[a.np + GH + j], 0.0, B[2 * a.np + GH + j], a.gamma, a.mu, a.ih, 0.0, rate, numax);
+  for (int o = 16; o > 0; o >>= 1) {
+    rate = fmax(rate, __shfl_xor_sync(0xffffffffu, rate, o));
+    numax = fmax(numax, __shfl_xor_sync(0xffffffffu, numax, o));
+  }
+  if (threadIdx.x % 32 == 0) {
+    sr[threadIdx.x / 32] = rate;
+    sn[threadIdx.x / 32] = numax;
+  }
+  __syncthreads();
+  rate = 0.0;
+  numax = 0.0;
+  for (int w = 0; w < LT / 32; ++w) {
+    rate = fmax(rate, sr[w]);
+    numax = fmax(numax, sn[w]);
+  }
+  __syncthreads();   // sr, sn are rewritten by the next call
+  double dt = cfl / rate;
+  if (numax > 0.0) dt = fmin(dt, cfl * a.h * a.h / (8.0 * numax));
+  return dt;
+}
+
+__device__ void line_stage(const LineArgs& a, const GasK<double>& gas, int mode, int stage, double dt,
+                           double* Bin, double* Bout, double* P, double* NF, double* A, int line, int* flag) {
+  line_ghosts(a, Bin);
+  __syncthreads();
+  line_fluxes(a, gas, Bin, P, NF);
+  __syncthreads();
+  line_update(a, mode, stage, dt, P, NF, Bin, Bout, A, line, flag);
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(LT) line_kernel(LineArgs a, int mode, double dt_fixed, int nsteps, double t_end,
+                                                  double cfl, int max_steps) {
+  const int b = blockIdx.x;
+  const long pad = 6L * a.np;
+  double* S = a.S + b * pad;
+  double* T = a.T + b * pad;
+  double* P = a.P + (long)b * NPF * (a.n + 3);
+  double* NF = a.NF + (long)b * 6 * (a.n + 2);
+  double* A = a.A + (long)b * 6 * a.n;
+  int* flag = a.flag + b;
+  GasK<double> gas = a.gas;
+  if (mode == LINE_OPERATOR) {
+    gas.dt = gas.dt_r = dt_fixed;
+    gas.inv_dt = gas.inv_dt_r = 1.0 / dt_fixed;
+    line_stage(a, gas, mode, 0, dt_fixed, S, T, P, NF, A, b, flag);
+    return;
+  }
+  double t = a.tl[b];
+  int k = 0;
+  // every thread runs the same sequence of time steps, so the loop and its
+  // barriers are uniform over the block
+  while (mode == LINE_STEPS ? k < nsteps : (k < max_steps && t < t_end * (1.0 - 1e-14))) {
+    double dt = dt_fixed;
+    if (mode == LINE_RUN) {
+      dt = fmin(line_cfl(a, S, cfl), t_end - t);
+      if (!(dt > 0.0) || !(dt < INFINITY)) {
+        if (threadIdx.x == 0) atomicOr(flag, 2);
+        break;
+      }
+    }
+    gas.dt = gas.dt_r = dt;
+    gas.inv_dt = gas.inv_dt_r = 1.0 / dt;
+    line_stage(a, gas, mode, 0, dt, S, T, P, NF, A, b, flag);
+    line_stage(a, gas, mode, 1, dt, T, S, P, NF, A, b, flag);
+    t += dt;
+    ++k;
+    // a run stops a line that left the physical states (the flag is read
+    // after the stage's closing barrier, so every thread sees the same value)
+    if (mode == LINE_RUN && (*(volatile int*)flag & 1)) break;
+  }
+  if (threadIdx.x == 0) {
+    a.tl[b] = t;
+    a.ns[b] = k;
+  }
+}
+
+// W, W_x [batch][3][n] <-> the padded state (set_state / get_state)
+__global__ void line_scatter_kernel(const double* W, const double* Wx, double* S, int n, int np, long total) {
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const long b = t / (3L * n);
+    const int c = (int)((t / n) % 3), j = (int)(t % n);
+    S[b * 6 * np + (long)c * np + GH + j] = W[t];
+    S[b * 6 * np + (long)(3 + c) * np + GH + j] = Wx[t];
+  }
+}
+__global__ void line_gather_kernel(const double* S, double* W, double* Wx, int n, int np, long total) {
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const long b = t / (3L * n);
+    const int c = (int)((t / n) % 3), j = (int)(t % n);
+    W[t] = S[b * 6 * np + (long)c * np + GH + j];
+    Wx[t] = S[b * 6 * np + (long)(3 + c) * np + GH + j];
+  }
+}
+
+}  // namespace
+
+struct fdcgks_line_ctx {
+  fdcgks_line_params p;
+  LineArgs a;
+  cudaStream_t stream;
+  void* mem = nullptr;       // one allocation for every array
+  double* stage = nullptr;   // [2][batch][3][n] host-copy staging
+  long long launches = 0;
+  char err[512];
+};
+
+namespace {
+
+fdcgks_status lfail(fdcgks_line_t c, fdcgks_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) snprintf(c->err, sizeof(c->err), "%s", buf);
+  else set_global_error(buf);
+  return s;
+}
+
+#define LINE_TRY(c, expr)                                                                          \
+  do {                                                                                             \
+    cudaError_t e_ = (expr);                                                                       \
+    if (e_ != cudaSuccess) return lfail((c), FDCGKS_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+const char* check_line_params(const fdcgks_line_params* p) {
+  if (!p) return "params is NULL";
+  if (p->n < 1 || p->n > (1 << 20)) return "n must be in [1, 2^20]";
+  if (p->batch < 1 || p->batch > (1 << 20)) return "batch must be in [1, 2^20]";
+  if ((long long)p->n * p->batch > (1LL << 28)) return "n * batch too large";
+  for (int k = 0; k < 2; ++k)
+    if (p->bc[k] != FDCGKS_BC_PERIODIC && p->bc[k] != FDCGKS_BC_TRANSMISSIVE && p->bc[k] != FDCGKS_BC_SYMMETRY)
+      return "line ends take PERIODIC, TRANSMISSIVE or SYMMETRY";
+  if ((p->bc[0] == FDCGKS_BC_PERIODIC) != (p->bc[1] == FDCGKS_BC_PERIODIC))
+    return "a periodic line is periodic at both ends";
+  if (p->bc[0] != FDCGKS_BC_PERIODIC && p->n < 3) return "a bounded line needs n >= 3";
+  // the remaining options are those of the 2-D scheme
+  fdcgks_params q;
+  std::memset(&q, 0, sizeof(q));
+  q.nx = p->n;
+  q.ny = 1;
+  q.x0 = p->x0;
+  q.x1 = p->x1;
+  q.y0 = 0.0;
+  q.y1 = 1.0;
+  q.gamma = p->gamma;
+  q.mu = p->mu;
+  q.Pr = p->Pr;
+  q.bc[0] = p->bc[0];
+  q.bc[1] = p->bc[1];
+  q.flux_variant = p->flux_variant;
+  q.geno_variant = p->geno_variant;
+  q.grad_base = p->grad_base;
+  q.precision = FDCGKS_FP64;
+  q.tau_c1 = p->tau_c1;
+  q.tau_c2 = p->tau_c2;
+  q.recon_vars = p->recon_vars;
+  return check_params(&q);
+}
+
+fdcgks_status launch_line(fdcgks_line_t c, int mode, double dt, int nsteps, double t_end, double cfl, int max_steps) {
+  line_kernel<<<c->p.batch, LT, 0, c->stream>>>(c->a, mode, dt, nsteps, t_end, cfl, max_steps);
+  LINE_TRY(c, cudaGetLastError());
+  ++c->launches;
+  return FDCGKS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fdcgks_status fdcgks_line_create(const fdcgks_line_params* p, fdcgks_line_t* out) {
+  if (!out) return lfail(nullptr, FDCGKS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (const char* m = check_line_params(p)) return lfail(nullptr, FDCGKS_ERR_ARG, "%s", m);
+  fdcgks_line_t c = new (std::nothrow) fdcgks_line_ctx();
+  if (!c) return lfail(nullptr, FDCGKS_ERR_CUDA, "out of host memory");
+  c->p = *p;
+  c->err[0] = 0;
+  c->stream = (cudaStream_t)p->stream;
+  const int n = p->n, B = p->batch, np = n + 2 * GH;
+  LineArgs& a = c->a;
+  a.n = n;
+  a.np = np;
+  a.bc0 = p->bc[0];
+  a.bc1 = p->bc[1];
+  a.fv = p->flux_variant;
+  a.grad_base = p->grad_base;
+  a.recon_vars = p->recon_vars;
+  a.h = (p->x1 - p->x0) / n;
+  a.ih = 1.0 / a.h;
+  a.gamma = p->gamma;
+  a.mu = p->mu;
+  a.geno = make_geno<double>(p->geno_variant);
+  fdcgks_params q;
+  std::memset(&q, 0, sizeof(q));
+  q.gamma = p->gamma;
+  q.mu = p->mu;
+  q.Pr = p->Pr;
+  q.tau_c1 = p->tau_c1;
+  q.tau_c2 = p->tau_c2;
+  a.gas = make_gas<double>(q, 1.0);
+  // doubles: S, T, P, NF, A, tl, staging; ints: ns, flag
+  const size_t nS = (size_t)B * 6 * np, nP = (size_t)B * NPF * (n + 3), nN = (size_t)B * 6 * (n + 2),
+               nA = (size_t)B * 6 * n, nStage = (size_t)B * 6 * n;
+  const size_t nd = 2 * nS + nP + nN + nA + B + nStage;
+  const size_t bytes = nd * sizeof(double) + 2 * (size_t)B * sizeof(int);
+  cudaError_t e = cudaMalloc(&c->mem, bytes);
+  if (e != cudaSuccess) {
+    delete c;
+    return lfail(nullptr, FDCGKS_ERR_CUDA, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  double* d = (double*)c->mem;
+  a.S = d;
+  d += nS;
+  a.T = d;
+  d += nS;
+  a.P = d;
+  d += nP;
+  a.NF = d;
+  d += nN;
+  a.A = d;
+  d += nA;
+  a.tl = d;
+  d += B;
+  c->stage = d;
+  d += nStage;
+  a.ns = (int*)d;
+  a.flag = a.ns + B;
+  for (int k = 0; k < 4; ++k) a.op[k] = nullptr;
+  e = cudaMemsetAsync(c->mem, 0, bytes, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    cudaFree(c->mem);
+    delete c;
+    return lfail(nullptr, FDCGKS_ERR_CUDA, "initialisation: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  return FDCGKS_OK;
+}
+
+void fdcgks_line_destroy(fdcgks_line_t c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  cudaFree(c->mem);
+  delete c;
+}
+
+fdcgks_status fdcgks_line_set_state(fdcgks_line_t c, const double* W, const double* Wx, int on_device) {
+  if (!c) return lfail(nullptr, FDCGKS_ERR_ARG, "ctx is NULL");
+  if (!W || !Wx) return lfail(c, FDCGKS_ERR_ARG, "W or Wx is NULL");
+  const long total = 3L * c->p.n * c->p.batch;
+  const double *w = W, *wx = Wx;
+  if (!on_device) {
+    LINE_TRY(c, cudaMemcpyAsync(c->stage, W, total * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    LINE_TRY(c, cudaMemcpyAsync(c->stage + total, Wx, total * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    w = c->stage;
+    wx = c->stage + total;
+  }
+  const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+  line_scatter_kernel<<<blocks, 256, 0, c->stream>>>(w, wx, c->a.S, c->p.n, c->a.np, total);
+  LINE_TRY(c, cudaGetLastError());
+  LINE_TRY(c, cudaMemsetAsync(c->a.tl, 0, c->p.batch * sizeof(double), c->stream));
+  LINE_TRY(c, cudaMemsetAsync(c->a.flag, 0, c->p.batch * sizeof(int), c->stream));
+  if (!on_device) LINE_TRY(c, cudaStreamSynchronize(c->stream));
+  return FDCGKS_OK;
+}
+
+fdcgks_status fdcgks_line_get_state(fdcgks_line_t c, double* W, double* Wx, int on_device) {
+  if (!c) return lfail(nullptr, FDCGKS_ERR_ARG, "ctx is NULL");
+  if (!W || !Wx) return lfail(c, FDCGKS_ERR_ARG, "W or Wx is NULL");
+  const long total = 3L * c->p.n * c->p.batch;
+  double* w = on_device ? W : c->stage;
+  double* wx = on_device ? Wx : c->stage + total;
+  const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+  line_gather_kernel<<<blocks, 256, 0, c->stream>>>(c->a.S, w, wx, c->p.n, c->a.np, total);
+  LINE_TRY(c, cudaGetLastError());
+  if (!on_device) {
+    LINE_TRY(c, cudaMemcpyAsync(W, w, total * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LINE_TRY(c, cudaMemcpyAsync(Wx, wx, total * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LINE_TRY(c, cudaStreamSynchronize(c->stream));
+  }
+  return FDCGKS_OK;
+}
+
+fdcgks_status fdcgks_line_steps(fdcgks_line_t c, double dt, int nsteps) {
+  if (!c) return lfail(nullptr, FDCGKS_ERR_ARG, "ctx is NULL");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return lfail(c, FDCGKS_ERR_ARG, "dt must be positive and finite");
+  if (nsteps < 0) return lfail(c, FDCGKS_ERR_ARG, "nsteps must be >= 0");
+  if (nsteps == 0) return FDCGKS_OK;
+  return launch_line(c, LINE_STEPS, dt, nsteps, 0.0, 0.0, 0);
+}
+
+fdcgks_status fdcgks_line_run(fdcgks_line_t c, double t_end, double cfl, int max_steps, double* t, int* steps) {
+  if (!c) return lfail(nullptr, FDCGKS_ERR_ARG, "ctx is NULL");
+  if (!std::isfinite(t_end)) return lfail(c, FDCGKS_ERR_ARG, "t_end must be finite");
+  if (!(cfl > 0.0) || !std::isfinite(cfl)) return lfail(c, FDCGKS_ERR_ARG, "cfl must be positive and finite");
+  if (max_steps < 0) return lfail(c, FDCGKS_ERR_ARG, "max_steps must be >= 0");
+  fdcgks_status s = launch_line(c, LINE_RUN, 0.0, 0, t_end, cfl, max_steps);
+  if (s != FDCGKS_OK) return s;
+  if (t) LINE_TRY(c, cudaMemcpyAsync(t, c->a.tl, c->p.batch * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (steps) LINE_TRY(c, cudaMemcpyAsync(steps, c->a.ns, c->p.batch * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  LINE_TRY(c, cudaStreamSynchronize(c->stream));
+  return FDCGKS_OK;
+}
+
+fdcgks_status fdcgks_line_stage_operator(fdcgks_line_t c, double dt, double* L, double* Lt, double* gb, double* gt) {
+  if (!c) return lfail(nullptr, FDCGKS_ERR_ARG, "ctx is NULL");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return lfail(c, FDCGKS_ERR_ARG, "dt must be positive and finite");
+  if (!L || !Lt || !gb || !gt) return lfail(c, FDCGKS_ERR_ARG, "output pointer is NULL");
+  LineArgs keep = c->a;
+  c->a.op[0] = L;
+  c->a.op[1] = Lt;
+  c->a.op[2] = gb;
+  c->a.op[3] = gt;
+  fdcgks_status s = launch_line(c, LINE_OPERATOR, dt, 0, 0.0, 0.0, 0);
+  c->a = keep;
+  return s;
+}
+
+fdcgks_status fdcgks_line_check(fdcgks_line_t c, int* flags, int* any) {
+  if (!c) return lfail(nullptr, FDCGKS_ERR_ARG, "ctx is NULL");
+  const int B = c->p.batch;
+  int* h = new (std::nothrow) int[B];
+  if (!h) return lfail(c, FDCGKS_ERR_CUDA, "out of host memory");
+  cudaError_t e = cudaMemcpyAsync(h, c->a.flag, B * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    delete[] h;
+    return lfail(c, FDCGKS_ERR_CUDA, "flag read: %s", cudaGetErrorString(e));
+  }
+  int o = 0;
+  for (int b = 0; b < B; ++b) o |= h[b];
+  if (flags) std::memcpy(flags, h, B * sizeof(int));
+  if (any) *any = o;
+  delete[] h;
+  return FDCGKS_OK;
+}
+
+const char* fdcgks_line_last_error(fdcgks_line_t c) { return c ? c->err : fdcgks_last_error(nullptr); }
+
+}  // extern "C"

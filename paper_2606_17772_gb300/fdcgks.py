@@ -25,7 +25,10 @@ EXPORTS = ["fdcgks_create", "fdcgks_destroy", "fdcgks_dims", "fdcgks_set_state",
            "fdcgks_ens_create", "fdcgks_ens_destroy", "fdcgks_ens_set_state", "fdcgks_ens_get_state",
            "fdcgks_ens_run", "fdcgks_ens_status", "fdcgks_ens_set_tiles", "fdcgks_ens_get_tiles",
            "fdcgks_ens_tune", "fdcgks_ens_profile", "fdcgks_ens_info", "fdcgks_ens_last_error",
-           "fdcgks_vjp_steps", "fdcgks_set_sides", "fdcgks_set_time", "fdcgks_get_time"]
+           "fdcgks_vjp_steps", "fdcgks_set_sides", "fdcgks_set_time", "fdcgks_get_time",
+           "fdcgks_line_create", "fdcgks_line_destroy", "fdcgks_line_set_state", "fdcgks_line_get_state",
+           "fdcgks_line_steps", "fdcgks_line_run", "fdcgks_line_stage_operator", "fdcgks_line_check",
+           "fdcgks_line_last_error"]
 
 ENS_NONPHYSICAL, ENS_NO_WAVE_SPEED, ENS_FROZEN = 1, 2, 4
 
@@ -45,6 +48,39 @@ class Params(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("recon_vars", ctypes.c_int),
     ]
+
+
+class LineParams(ctypes.Structure):
+    """fdcgks_line_params: a batch of lines of the one-dimensional scheme."""
+    _fields_ = [
+        ("n", ctypes.c_int), ("batch", ctypes.c_int),
+        ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("mu", ctypes.c_double), ("Pr", ctypes.c_double),
+        ("bc", ctypes.c_int * 2),
+        ("flux_variant", ctypes.c_int), ("geno_variant", ctypes.c_int), ("grad_base", ctypes.c_int),
+        ("tau_c1", ctypes.c_double), ("tau_c2", ctypes.c_double),
+        ("recon_vars", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+def line_params(n, batch=1, x0=0.0, x1=1.0, gamma=1.4, mu=0.0, Pr=1.0, bc=(1, 1), flux_variant=64,
+                geno_variant=0, grad_base=0, tau_c1=0.0, tau_c2=0.0, recon_vars=0, stream=None):
+    p = LineParams()
+    p.n, p.batch, p.x0, p.x1 = n, batch, x0, x1
+    p.gamma, p.mu, p.Pr = gamma, mu, Pr
+    p.bc[0], p.bc[1] = bc
+    p.flux_variant, p.geno_variant, p.grad_base = flux_variant, geno_variant, grad_base
+    p.tau_c1, p.tau_c2, p.recon_vars = tau_c1, tau_c2, recon_vars
+    p.stream = stream
+    return p
+
+
+def line_params_for_case(case, batch=1, stream=None):
+    """LineParams of a strip case (inputs.Case; its x extent, gas, x-ends and options)."""
+    return line_params(case.nx, batch, case.x0, case.x1, case.gamma, case.mu, case.Pr, tuple(case.bc[:2]),
+                       case.flux_variant, case.geno_variant, case.grad_base, case.tau_c1, case.tau_c2,
+                       case.recon_vars, stream)
 
 
 class Side(ctypes.Structure):
@@ -132,6 +168,17 @@ def load(path=None):
     lib.fdcgks_set_sides.argtypes = [_VP, _VP]
     lib.fdcgks_set_time.argtypes = [_VP, ctypes.c_double]
     lib.fdcgks_get_time.argtypes = [_VP, ctypes.POINTER(ctypes.c_double)]
+    lib.fdcgks_line_create.argtypes = [ctypes.POINTER(LineParams), ctypes.POINTER(_VP)]
+    lib.fdcgks_line_destroy.argtypes = [_VP]
+    lib.fdcgks_line_destroy.restype = None
+    lib.fdcgks_line_set_state.argtypes = [_VP, _VP, _VP, ctypes.c_int]
+    lib.fdcgks_line_get_state.argtypes = [_VP, _VP, _VP, ctypes.c_int]
+    lib.fdcgks_line_steps.argtypes = [_VP, ctypes.c_double, ctypes.c_int]
+    lib.fdcgks_line_run.argtypes = [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_int, _VP, _VP]
+    lib.fdcgks_line_stage_operator.argtypes = [_VP, ctypes.c_double, _VP, _VP, _VP, _VP]
+    lib.fdcgks_line_check.argtypes = [_VP, _VP, ctypes.POINTER(ctypes.c_int)]
+    lib.fdcgks_line_last_error.argtypes = [_VP]
+    lib.fdcgks_line_last_error.restype = ctypes.c_char_p
     lib.fdcgks_ens_last_error.argtypes = [_VP]
     lib.fdcgks_ens_last_error.restype = ctypes.c_char_p
     lib.fdcgks_last_error.argtypes = [_VP]
@@ -144,7 +191,9 @@ def load(path=None):
                  "fdcgks_cfl_dt_noalloc", "fdcgks_ens_create", "fdcgks_ens_set_state", "fdcgks_ens_get_state",
                  "fdcgks_ens_run", "fdcgks_ens_status", "fdcgks_ens_set_tiles", "fdcgks_ens_get_tiles",
                  "fdcgks_ens_tune", "fdcgks_ens_profile", "fdcgks_ens_info", "fdcgks_vjp_steps",
-                 "fdcgks_set_sides", "fdcgks_set_time", "fdcgks_get_time"):
+                 "fdcgks_set_sides", "fdcgks_set_time", "fdcgks_get_time", "fdcgks_line_create",
+                 "fdcgks_line_set_state", "fdcgks_line_get_state", "fdcgks_line_steps", "fdcgks_line_run",
+                 "fdcgks_line_stage_operator", "fdcgks_line_check"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -539,6 +588,94 @@ class Ensemble:
     def synchronize(self):
         import torch
         torch.cuda.ExternalStream(self.stream).synchronize()
+
+
+def _lcheck(status, lines):
+    if status != 0:
+        raise FdcgksError(status, load().fdcgks_line_last_error(lines).decode())
+
+
+class Lines:
+    """A batch of lines of the one-dimensional scheme (fdcgks_line_*).
+    State arrays: W [batch][3][n] (rho, rho U, rho E) and Wx [batch][3][n]."""
+
+    def __init__(self, params):
+        lib = load()
+        self._p = params
+        if params.stream is None:
+            params.stream = _stream().value
+        h = _VP()
+        _lcheck(lib.fdcgks_line_create(ctypes.byref(params), ctypes.byref(h)), None)
+        self._h = h
+        self.n, self.batch = params.n, params.batch
+
+    @classmethod
+    def from_case(cls, case, batch=1):
+        return cls(line_params_for_case(case, batch))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().fdcgks_line_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def shape(self):
+        return (self.batch, 3, self.n)
+
+    def set_state(self, W, Wx):
+        """CUDA float64 tensors or host arrays of shape (batch, 3, n) (or (3, n) for one line)."""
+        import torch
+        on_device = isinstance(W, torch.Tensor) and W.is_cuda
+        n = self.batch * 3 * self.n
+        conv = _dptr if on_device else _hptr
+        _lcheck(load().fdcgks_line_set_state(self._h, conv(W, n), conv(Wx, n), int(on_device)), self._h)
+
+    def get_state(self, device=True):
+        import torch
+        if device:
+            out = [torch.empty(self.shape(), dtype=torch.float64, device="cuda") for _ in range(2)]
+            ptrs = [_dptr(t) for t in out]
+        else:
+            out = [np.empty(self.shape()) for _ in range(2)]
+            ptrs = [_hptr(a) for a in out]
+        _lcheck(load().fdcgks_line_get_state(self._h, *ptrs, int(device)), self._h)
+        return tuple(out)
+
+    def steps(self, dt, n):
+        _lcheck(load().fdcgks_line_steps(self._h, ctypes.c_double(dt), int(n)), self._h)
+
+    def run(self, t_end, cfl=0.4, max_steps=1 << 30):
+        """Each line to t_end with its own CFL steps; returns (t [batch], steps [batch])."""
+        t = np.zeros(self.batch)
+        k = np.zeros(self.batch, dtype=np.int32)
+        _lcheck(load().fdcgks_line_run(self._h, ctypes.c_double(t_end), ctypes.c_double(cfl), int(max_steps),
+                                       t.ctypes.data, k.ctypes.data), self._h)
+        return t, k
+
+    def stage_operator(self, dt):
+        import torch
+        out = {k: torch.empty(self.shape(), dtype=torch.float64, device="cuda") for k in ("L", "Lt", "gb", "gt")}
+        _lcheck(load().fdcgks_line_stage_operator(self._h, ctypes.c_double(dt),
+                                                  *(_dptr(out[k]) for k in ("L", "Lt", "gb", "gt"))), self._h)
+        return out
+
+    def check(self):
+        """(per-line status bits, their OR): bit 0 non-physical node, bit 1 no CFL time step."""
+        flags = np.zeros(self.batch, dtype=np.int32)
+        anyf = ctypes.c_int()
+        _lcheck(load().fdcgks_line_check(self._h, flags.ctypes.data, ctypes.byref(anyf)), self._h)
+        return flags, anyf.value
 
 
 def _steps_function():

@@ -82,6 +82,41 @@ int main(void) {
                     fdcgks.BC_FIXED]
 
 
+def test_line_params_struct_layout_matches_header():
+    src = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "fdcgks.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(fdcgks_line_params), offsetof(fdcgks_line_params, bc),
+         offsetof(fdcgks_line_params, flux_variant), offsetof(fdcgks_line_params, tau_c1),
+         offsetof(fdcgks_line_params, recon_vars), offsetof(fdcgks_line_params, stream));
+  return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "t")
+        subprocess.run(["gcc", "-I", os.path.dirname(HEADER), c, "-o", exe], check=True)
+        vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
+    P = fdcgks.LineParams
+    assert vals == [ctypes.sizeof(P), P.bc.offset, P.flux_variant.offset, P.tau_c1.offset, P.recon_vars.offset,
+                    P.stream.offset]
+
+
+@pytest.mark.parametrize("bad", [dict(n=2), dict(n=0), dict(batch=0), dict(bc=(0, 1)), dict(bc=(3, 3)),
+                                 dict(flux_variant=63), dict(gamma=1.0), dict(recon_vars=2)])
+def test_invalid_line_parameters_are_rejected_before_device_work(lib, bad):
+    kw = dict(n=20, batch=1, bc=(1, 1))
+    kw.update(bad)
+    p = fdcgks.line_params(**kw)
+    h = ctypes.c_void_p()
+    assert lib.fdcgks_line_create(ctypes.byref(p), ctypes.byref(h)) == 1
+    assert h.value is None
+    assert lib.fdcgks_line_last_error(None).decode()
+
+
 def test_case_sides_marshalling():
     from paper_2606_17772_gb300 import inputs
     case = inputs.double_mach(16, 4)
@@ -124,5 +159,8 @@ def test_null_context_calls(lib):
     assert lib.fdcgks_set_sides(None, None) == 1
     assert lib.fdcgks_set_time(None, ctypes.c_double(0.0)) == 1
     assert lib.fdcgks_get_time(None, None) == 1
+    assert lib.fdcgks_line_steps(None, ctypes.c_double(0.1), 1) == 1
+    assert lib.fdcgks_line_check(None, None, None) == 1
+    lib.fdcgks_line_destroy(None)
     lib.fdcgks_destroy(None)
     assert lib.fdcgks_status_string(3).decode() == "non-physical state"
