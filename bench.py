@@ -81,6 +81,7 @@ def parse():
     ap.add_argument("--no-viscous-tube", action="store_true")
     ap.add_argument("--vt-steps", type=int, default=100, help="timed steps of the viscous shock tube window")
     ap.add_argument("--no-double-mach", action="store_true")
+    ap.add_argument("--no-lines", action="store_true")
     ap.add_argument("--dmr-steps", type=int, default=100, help="timed FP64 steps of the double Mach window")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--adj-steps", type=int, default=20, help="steps of the adjoint window")
@@ -380,10 +381,43 @@ def run_double_mach(args, world):
             res[name] = {"value": nodes * k * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / k, "steps": k,
                          "dt": dt, "t_end": t_end, "nonphysical": bool(bad)}
         out["%dx%d" % (nx, ny)] = res
-    # the blast waves run to their final time (host-driven CFL loop, one strip row)
-    from paper_2606_17772_gb300 import runs
-    wc = runs.woodward_colella(400, fdcgks.FP64)
-    out["woodward_colella"] = {k: wc[k] for k in ("case", "t", "steps", "wall_seconds", "rho_max", "p_min")}
+    return out
+
+
+def run_lines(args, world):
+    """The one-dimensional scheme (Sec. 2) on Woodward-Colella blast-wave lines
+    (Sec. 5.3), N = 400, FD-CGKS(6-2) with App. D's GENO constants, run to
+    t = 0.038 with each line's own CFL steps inside one launch: one line (the
+    time to solution of the paper's run) and a batch of 4 lines per SM
+    (throughput); and the Sod and Lax tubes (Sec. 5.2, N = 100) as single
+    lines."""
+    import numpy as np
+    import torch
+    from paper_2606_17772_gb300 import fdcgks, inputs
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    wc = inputs.woodward_colella(400, flux_variant=62, geno_variant=1)
+    out = {"config": {"workload": "Woodward-Colella blast waves, [0,1], N = 400, reflecting ends, "
+                                  "FD-CGKS(6-2), GENO App. D, CFL 0.4, to t = 0.038, one thread block per line; "
+                                  "Sod (t = 0.2) and Lax (t = 0.16) tubes, N = 100"}}
+    for name, case, t_end, batch in (("one_line", wc, 0.038, 1), ("batch", wc, 0.038, 4 * sms),
+                                     ("sod", inputs.sod_strip(100, 1), 0.2, 1),
+                                     ("lax", inputs.lax_strip(100, 1), 0.16, 1)):
+        W, G = inputs.line_state(case)
+        with fdcgks.Lines.from_case(case, batch) as L:
+            L.set_state(np.ascontiguousarray(np.broadcast_to(W, (batch,) + W.shape)),
+                        np.ascontiguousarray(np.broadcast_to(G, (batch,) + G.shape)))
+            torch.cuda.synchronize()
+            barrier(world)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            tt, kk = L.run(t_end, 0.4)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = max_over_ranks(e0.elapsed_time(e1), world)
+            _, bad = L.check()
+        updates = float(kk.sum()) * case.nx
+        out[name] = {"lines": batch, "steps": int(kk.max()), "t": float(tt.min()), "ms": ms,
+                     "value": updates * world / (ms / 1e3), "unit": UNIT, "launches": 1, "nonphysical": bool(bad)}
     return out
 
 
@@ -579,6 +613,8 @@ def main():
         line["viscous_tube"] = run_viscous_tube(args, world)
     if not args.no_double_mach:
         line["double_mach"] = run_double_mach(args, world)
+    if not args.no_lines:
+        line["lines_1d"] = run_lines(args, world)
     if not args.no_adjoint:
         line["adjoint"] = run_adjoint(args, world)
 

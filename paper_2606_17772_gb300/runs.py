@@ -9,8 +9,8 @@ JSON summary:
     y = 0.075, the two profiles the paper plots;
   * double Mach reflection (Sec. 5.5) to t = 0.2: density extrema and the
     density on the wall and along y = 0.5 (the figure is a contour plot);
-  * Woodward-Colella blast waves (Sec. 5.3) to t = 0.038: density and
-    pressure along the tube.
+  * Woodward-Colella blast waves (Sec. 5.3) to t = 0.038 with the
+    one-dimensional scheme: density and pressure along the tube.
 
     python -m paper_2606_17772_gb300.runs --case viscous_tube --nx 1000 --ny 500 --precision mixed
     python -m paper_2606_17772_gb300.runs --case double_mach --nx 960 --ny 240 --precision fp64
@@ -101,17 +101,31 @@ def double_mach(nx=960, ny=240, precision=fdcgks.FP64, t_end=0.2, cfl=0.4, flux_
     }
 
 
-def woodward_colella(nx=400, precision=fdcgks.FP64, t_end=0.038, cfl=0.4, flux_variant=62, recon_vars=0):
-    """Run Sec. 5.3's interacting blast waves; returns a summary dict."""
-    case = inputs.woodward_colella(nx, flux_variant=flux_variant, recon_vars=recon_vars)
-    (Wp, Gp, Wd, Gd), t, n, wall, _ = _timed_run(case, precision, t_end, cfl)
+def woodward_colella(nx=400, t_end=0.038, cfl=0.4, flux_variant=62, recon_vars=0, geno_variant=1):
+    """Run Sec. 5.3's interacting blast waves with the one-dimensional scheme
+    (one launch: the line's own CFL steps run inside the kernel); returns a
+    summary dict.  FP64.  Defaults: FD-CGKS(6-2) with App. D's GENO constants
+    (with the Sec. 3.2 constants and tau_c2 = 1 the line loses positivity at
+    t = 0.027)."""
+    case = inputs.woodward_colella(nx, flux_variant=flux_variant, recon_vars=recon_vars, geno_variant=geno_variant)
+    W, G = inputs.line_state(case)
+    with fdcgks.Lines.from_case(case) as L:
+        L.set_state(W, G)
+        w0 = time.perf_counter()
+        tt, kk = L.run(t_end, cfl)
+        wall = time.perf_counter() - w0
+        flags, _ = L.check()
+        Wf, _ = L.get_state(device=False)
+    if flags[0]:
+        raise RuntimeError("non-physical state at t = %.6g after %d steps" % (tt[0], kk[0]))
     xp, _ = case.node_xy(False)
-    rho = Wp[0, 0]
-    p = (case.gamma - 1.0) * (Wp[3, 0] - 0.5 * (Wp[1, 0] ** 2 + Wp[2, 0] ** 2) / rho)
+    rho = Wf[0, 0]
+    p = (case.gamma - 1.0) * (Wf[0, 2] - 0.5 * Wf[0, 1] ** 2 / rho)
     return {
-        "case": "Woodward-Colella blast waves, N = %d, FD-CGKS(6-%d), %s, CFL %.2f" % (
-            nx, 2 if flux_variant == 62 else 4, "mixed" if precision == fdcgks.MIXED else "fp64", cfl),
-        "t": t, "steps": n, "wall_seconds": wall,
+        "case": "Woodward-Colella blast waves, N = %d, one-dimensional FD-CGKS(6-%d), GENO variant %d, %s, "
+                "CFL %.2f, fp64" % (nx, 2 if flux_variant == 62 else 4, geno_variant,
+                                    "characteristic" if recon_vars else "conservative", cfl),
+        "t": float(tt[0]), "steps": int(kk[0]), "wall_seconds": wall,
         "rho_min": float(rho.min()), "rho_max": float(rho.max()), "p_min": float(p.min()),
         "x": xp[0].tolist(), "rho": rho.tolist(), "p": p.tolist(),
     }
@@ -138,7 +152,7 @@ def main():
     elif a.case == "double_mach":
         res = double_mach(a.nx or 960, a.ny or 240, prec, a.t_end or 0.2, a.cfl, **opt)
     else:
-        res = woodward_colella(a.nx or 400, prec, a.t_end or 0.038, a.cfl, **opt)
+        res = woodward_colella(a.nx or 400, a.t_end or 0.038, a.cfl, **opt)
     text = json.dumps(res)
     if a.out:
         with open(a.out, "w") as f:

@@ -164,17 +164,29 @@ def test_density_wave_table_1_on_the_gpu():
 
 def test_cfl_run_reaches_the_final_time_like_the_oracle():
     """fdcgks_line_run: each line's own CFL steps in one launch, the last one
-    clipped.  Against the oracle's CFL loop: the same number of steps and a
-    state equal to rounding (the two reduce h / (|U| + c) differently)."""
+    clipped.  Against the oracle's CFL loop: the same number of steps and the
+    same state up to the scheme's amplification of rounding over ~190 steps
+    of a shock tube (the two reduce h / (|U| + c) differently, so their time
+    steps differ in the last bits): 100 times the oracle's own response to a
+    1e-15 relative perturbation of the initial data (about 1e-5 measured:
+    GENO's weights in the nearly uniform states next to the waves amplify
+    perturbations, see the adjoint tests)."""
     case = inputs.sod_strip(100, 1)
     p = oracle.make_params(**case.oracle_kwargs())
     W, G = inputs.line_state(case)
-    t, k, ref = 0.0, 0, (W, G)
-    while t < 0.2 * (1 - 1e-14):
-        dt = min(oracle.cfl_dt_1d(p, 0.4, ref[0]), 0.2 - t)
-        ref = oracle.steps_1d(p, dt, 1, *ref)
-        t += dt
-        k += 1
+
+    def oracle_run(state):
+        t, k = 0.0, 0
+        while t < 0.2 * (1 - 1e-14):
+            dt = min(oracle.cfl_dt_1d(p, 0.4, state[0]), 0.2 - t)
+            state = oracle.steps_1d(p, dt, 1, *state)
+            t += dt
+            k += 1
+        return state, k
+    ref, k = oracle_run((W, G))
+    rng = np.random.default_rng(1)
+    pert, _ = oracle_run((W * (1 + 1e-15 * rng.standard_normal(W.shape)), G))
+    spread = max(errs(pert, ref))
     other = inputs.lax_strip(100, 1)          # a second line with other data
     Wl, Gl = inputs.line_state(other)
     with fdcgks.Lines.from_case(case, batch=2) as L:
@@ -185,7 +197,28 @@ def test_cfl_run_reaches_the_final_time_like_the_oracle():
     assert anyf == 0
     assert tt[0] == pytest.approx(0.2, rel=1e-14) and tt[1] == pytest.approx(0.2, rel=1e-14)
     assert kk[0] == k
-    assert max(errs((gw[0], gg[0]), ref)) < 1e-9
+    assert max(errs((gw[0], gg[0]), ref)) < max(1e-9, 100 * spread), spread
+
+
+def test_cfl_run_on_smooth_data_matches_the_oracle_loop():
+    """On smooth data rounding is not amplified: the in-kernel CFL loop and the
+    oracle's host loop take the same steps and agree to 1e-10."""
+    case = random_line(40, 7, 1, mu=0.005, Pr=0.72)
+    p = oracle.make_params(**case.oracle_kwargs())
+    W, G = inputs.line_state(case)
+    t, k, ref = 0.0, 0, (W, G)
+    while t < 0.1 * (1 - 1e-14):
+        dt = min(oracle.cfl_dt_1d(p, 0.4, ref[0]), 0.1 - t)
+        ref = oracle.steps_1d(p, dt, 1, *ref)
+        t += dt
+        k += 1
+    with fdcgks.Lines.from_case(case) as L:
+        L.set_state(W, G)
+        tt, kk = L.run(0.1, 0.4)
+        gw, gg = L.get_state(device=False)
+    assert kk[0] == k and k >= 15
+    assert tt[0] == pytest.approx(0.1, rel=1e-14)
+    assert max(errs((gw[0], gg[0]), ref)) < 1e-10
 
 
 def test_nonphysical_line_is_flagged_and_stops():
