@@ -14,7 +14,10 @@
 //                  nodal kernels (the FP64 kernels are FP64-pipe bound and
 //                  are left uncapped)
 // FDK_SOLVE_NOINLINE  1: the kinetic solve is an out-of-line function called
-//                  twice (one code copy per kernel), 0: inlined twice
+//                  twice (one code copy per kernel), 0: inlined twice.  With the
+//                  reconstruction also out of line (below) the smaller code
+//                  runs 3.6 % (mixed) and 0.8 % (FP64) faster per step on the
+//                  1024^2 vortex than both inlined
 #ifndef FDK_POINT_MINB_F64
 #define FDK_POINT_MINB_F64 1
 #endif
@@ -28,10 +31,19 @@
 #define FDK_NODAL_MINB_F32 8
 #endif
 #ifndef FDK_SOLVE_NOINLINE_F64
-#define FDK_SOLVE_NOINLINE_F64 0
+#define FDK_SOLVE_NOINLINE_F64 1
 #endif
 #ifndef FDK_SOLVE_NOINLINE_F32
-#define FDK_SOLVE_NOINLINE_F32 0
+#define FDK_SOLVE_NOINLINE_F32 1
+#endif
+// FDK_RECON_NOINLINE_F32 / _F64  1: the per-component interface reconstruction
+//                  of the point kernels is an out-of-line function (one code copy
+//                  instead of eight inlined ones), 0: inlined
+#ifndef FDK_RECON_NOINLINE_F32
+#define FDK_RECON_NOINLINE_F32 1
+#endif
+#ifndef FDK_RECON_NOINLINE_F64
+#define FDK_RECON_NOINLINE_F64 1
 #endif
 
 namespace fdk {
@@ -49,6 +61,37 @@ template <> struct PointTune<float> {
   static constexpr int nodal_minb = FDK_NODAL_MINB_F32;
   static constexpr bool noinline = FDK_SOLVE_NOINLINE_F32;
 };
+
+// interface reconstruction of one component, inlined or out of line (the
+// adjoint's dual numbers always inline)
+template <class R> struct ReconCall { static constexpr bool noinline = false; };
+template <> struct ReconCall<float> { static constexpr bool noinline = FDK_RECON_NOINLINE_F32; };
+template <> struct ReconCall<double> { static constexpr bool noinline = FDK_RECON_NOINLINE_F64; };
+
+template <class R>
+struct ReconOne { R vl, dl, cl, vr, dr, cr; };
+
+template <class R>
+__device__ __noinline__ ReconOne<R> recon_interface_call(const GenoK<R>& g, R q0, R q1, R q2, R q3, R x0, R x1, R x2,
+                                                         R x3, R h, R ih) {
+  const R Q[4] = {q0, q1, q2, q3}, Qx[4] = {x0, x1, x2, x3};
+  ReconOne<R> o;
+  recon_interface(g, Q, Qx, h, ih, o.vl, o.dl, o.cl, o.vr, o.dr, o.cr);
+  return o;
+}
+
+template <class R>
+FD_HD void recon_interface_sel(const GenoK<R>& g, const R Q[4], const R Qx[4], R h, R ih, R& vl, R& dl, R& cl, R& vr,
+                               R& dr, R& cr) {
+#ifdef __CUDA_ARCH__
+  if constexpr (ReconCall<R>::noinline) {
+    const ReconOne<R> o = recon_interface_call(g, Q[0], Q[1], Q[2], Q[3], Qx[0], Qx[1], Qx[2], Qx[3], h, ih);
+    vl = o.vl; dl = o.dl; cl = o.cl; vr = o.vr; dr = o.dr; cr = o.cr;
+    return;
+  }
+#endif
+  recon_interface(g, Q, Qx, h, ih, vl, dl, cl, vr, dr, cr);
+}
 
 template <class R>
 __device__ __noinline__ void iface_solve_call(const GasK<R>& gas, int normal, const R* Wl, const R* Wr, const R* Wln,
@@ -156,7 +199,7 @@ FD_HD void recon_line_ld(const GenoK<R>& geno, LD ld, int l, R h, R ih, R vl[4],
     R Q[4] = {ld(l, 0, c), ld(l, 1, c), ld(l, 2, c), ld(l, 3, c)};
     R Qx[4] = {ld(l, 0, 4 + c), ld(l, 1, 4 + c), ld(l, 2, 4 + c), ld(l, 3, 4 + c)};
     R cl, cr;
-    recon_interface(geno, Q, Qx, h, ih, vl[c], dl[c], cl, vr[c], dr[c], cr);
+    recon_interface_sel(geno, Q, Qx, h, ih, vl[c], dl[c], cl, vr[c], dr[c], cr);
     if (c == 0) chi = s_min(cl, cr);   // chi_{j+1/2} = min(chi^{l,rho}, chi^{r,rho})
   }
   positivity_fix(ld, l, vl, dl, vr, dr, chi);
@@ -210,7 +253,7 @@ FD_HD void recon_line_char(const GenoK<R>& geno, R gm1, int normal, LD ld, int l
       Q[m] = a;
       Qx[m] = b;
     }
-    recon_interface(geno, Q, Qx, h, ih, cvl[k], cdl[k], cl[k], cvr[k], cdr[k], cr[k]);
+    recon_interface_sel(geno, Q, Qx, h, ih, cvl[k], cdl[k], cl[k], cvr[k], cdr[k], cr[k]);
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
