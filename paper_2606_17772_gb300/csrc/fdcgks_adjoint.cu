@@ -46,11 +46,24 @@ using namespace fdk;
 
 namespace {
 
-// tangent lanes per dual-number pass: one.  The local Jacobian then takes one
-// pass per input (64 per point, 44 per node); wider lanes cut the passes but
-// make the device compiler's optimisation of these kernels take minutes.
+// tangent lanes per dual-number pass: one (wider lanes make the device
+// compiler's optimisation of these kernels take minutes).
 const int AN = 1;
 typedef Dual<AN> DN;
+
+// The local maps are differentiated piece by piece, each piece's Jacobian
+// taken column by column with dual numbers and contracted with the adjoint
+// of its outputs (reverse order of the forward):
+//   point: W~ assembly (linear) <- two kinetic solves (20 inputs each: W^l,
+//          W^r, their normal derivatives, the tangential derivative) <- the
+//          tangential derivatives (means of the other line's derivatives) <-
+//          two line reconstructions, whose components are independent of one
+//          another, so one pass seeds the same (entry, value/gradient) input
+//          of every component of both lines (8 passes);
+//   node:  nodal flux (12 inputs) <- eight node-derivative reconstructions
+//          (independent; 6 passes seed all of them).
+// Branches (GENO saturation, the positivity safeguard) follow the values, so
+// every piece differentiates the branch the forward took.
 
 // ---------------------------------------------------------------------------
 // point map adjoint: inputs are the 64 values (2 lines x 4 entries x (4 W +
@@ -79,30 +92,100 @@ __global__ void __launch_bounds__(128) point_vjp_kernel(KArgs<double> a, const d
   };
   double x[64];
   for (int s = 0; s < 64; ++s) x[s] = a.Sr[addr(s)];
-  const GenoK<DN> geno = dual_geno<AN>(a.geno);
-  const GasK<DN> gas = dual_gas<AN>(a.gas);
-  const DN h[2] = {DN(a.h[0]), DN(a.h[1])}, ih[2] = {DN(a.ih[0]), DN(a.ih[1])};
   const bool wn = a.want_n != 0;
-#pragma unroll 1
-  for (int k0 = 0; k0 < 64; k0 += AN) {
-    double acc[AN];
-    for (int t = 0; t < AN; ++t) acc[t] = 0.0;
-    point_compute<DN, TYPE>(
-        geno, gas, h, ih, wn,
-        [&](int l, int e, int f) -> DN {
-          const int s = l * 32 + e * 8 + f;
-          DN r(x[s]);
-          const int t = s - k0;
-          if (t >= 0 && t < AN) r.d[t] = 1.0;
-          return r;
-        },
-        [&](int k, const DN& v) {
-#pragma unroll
-          for (int t = 0; t < AN; ++t) acc[t] += v.d[t] * ah[k];
-        });
-    for (int t = 0; t < AN; ++t)
-      if (acc[t] != 0.0) atomicAdd(Sa + addr(k0 + t), acc[t]);
+  const int n0 = TYPE;                                  // normal of solve 0 (primary line); solve 1: 1 - n0
+  const double hl[2] = {a.h[n0], a.h[1 - n0]}, ihl[2] = {a.ih[n0], a.ih[1 - n0]};
+
+  // forward values of the reconstructions and tangential derivatives
+  double v[2][4][4], chi[2];                            // v[line][vl, dl, vr, dr][component]
+  for (int l = 0; l < 2; ++l)
+    recon_line_ld(a.geno, [&](int ll, int e, int f) -> double { return x[ll * 32 + e * 8 + f]; }, l, hl[l], ihl[l],
+                  v[l][0], v[l][1], v[l][2], v[l][3], chi[l]);
+  double tg[2][4];
+  for (int c = 0; c < 4; ++c) {
+    tg[0][c] = 0.5 * (v[1][1][c] + v[1][3][c]);
+    tg[1][c] = 0.5 * (v[0][1][c] + v[0][3][c]);
   }
+
+  // adjoints of the solves' outputs from the point outputs (W~ of Eq. eq:W-model-2d)
+  double ao[2][6][4];                                   // [solve][F, Ft, Wl, Wr, Wlt, Wrt][component]
+  for (int sv = 0; sv < 2; ++sv) {
+    const int b = sv * NPS, o = (1 - sv) * NPS;
+    for (int c = 0; c < 4; ++c) {
+      ao[sv][0][c] = wn ? ah[b + PO_F + c] : 0.0;
+      ao[sv][1][c] = ah[b + PO_FT + c];
+      ao[sv][2][c] = wn ? 0.5 * ah[b + PO_WL + c] + 0.25 * (ah[o + PO_WL + c] + ah[o + PO_WR + c]) : 0.0;
+      ao[sv][3][c] = wn ? 0.5 * ah[b + PO_WR + c] + 0.25 * (ah[o + PO_WL + c] + ah[o + PO_WR + c]) : 0.0;
+      ao[sv][4][c] = 0.5 * ah[b + PO_WLT + c] + 0.25 * (ah[o + PO_WLT + c] + ah[o + PO_WRT + c]);
+      ao[sv][5][c] = 0.5 * ah[b + PO_WRT + c] + 0.25 * (ah[o + PO_WLT + c] + ah[o + PO_WRT + c]);
+    }
+  }
+
+  // solves: adjoint of their 20 inputs, one dual pass per input
+  const GasK<DN> gas = dual_gas<AN>(a.gas);
+  double av[2][4][4] = {}, at[2][4];
+  for (int sv = 0; sv < 2; ++sv) {
+#pragma unroll 1
+    for (int m = 0; m < 20; ++m) {
+      DN in[5][4];
+      for (int q = 0; q < 4; ++q) {
+        in[0][q] = DN(v[sv][0][q]);
+        in[1][q] = DN(v[sv][2][q]);
+        in[2][q] = DN(v[sv][1][q]);
+        in[3][q] = DN(v[sv][3][q]);
+        in[4][q] = DN(tg[sv][q]);
+      }
+      in[m / 4][m % 4].d[0] = 1.0;
+      IfaceOut<DN> out;
+      iface_solve_call(gas, sv == 0 ? n0 : 1 - n0, in[0], in[1], in[2], in[3], in[4], wn, out);
+      double acc = 0.0;
+      for (int c = 0; c < 4; ++c) {
+        acc += out.Ft[c].d[0] * ao[sv][1][c] + out.Wlt[c].d[0] * ao[sv][4][c] + out.Wrt[c].d[0] * ao[sv][5][c];
+        if (wn) acc += out.F[c].d[0] * ao[sv][0][c] + out.Wl[c].d[0] * ao[sv][2][c] + out.Wr[c].d[0] * ao[sv][3][c];
+      }
+      const int grp = m / 4, c = m % 4;                 // Wl, Wr, Wln, Wrn, Wt
+      if (grp == 0) av[sv][0][c] += acc;
+      else if (grp == 1) av[sv][2][c] += acc;
+      else if (grp == 2) av[sv][1][c] += acc;
+      else if (grp == 3) av[sv][3][c] += acc;
+      else at[sv][c] = acc;
+    }
+  }
+  // the tangential derivative of each solve is the mean of the other line's derivatives
+  for (int c = 0; c < 4; ++c) {
+    av[1][1][c] += 0.5 * at[0][c];
+    av[1][3][c] += 0.5 * at[0][c];
+    av[0][1][c] += 0.5 * at[1][c];
+    av[0][3][c] += 0.5 * at[1][c];
+  }
+  const double achi[2] = {ah[PO_CHI], ah[NPS + PO_CHI]};
+
+  // line reconstructions: pass q seeds entry q % 4, value (q < 4) or gradient, of every component
+  const GenoK<DN> geno = dual_geno<AN>(a.geno);
+  double ax[64] = {};
+#pragma unroll 1
+  for (int q = 0; q < 8; ++q) {
+    const int es = q % 4, kind = q / 4;
+    for (int l = 0; l < 2; ++l) {
+      DN vl[4], dl[4], vr[4], dr[4], ch;
+      recon_line_ld(
+          geno,
+          [&](int ll, int e, int f) -> DN {
+            DN r(x[ll * 32 + e * 8 + f]);
+            if (e == es && (f >= 4) == (kind == 1)) r.d[0] = 1.0;
+            return r;
+          },
+          l, DN(hl[l]), DN(ihl[l]), vl, dl, vr, dr, ch);
+      for (int c = 0; c < 4; ++c) {
+        double g = vl[c].d[0] * av[l][0][c] + dl[c].d[0] * av[l][1][c] + vr[c].d[0] * av[l][2][c] +
+                   dr[c].d[0] * av[l][3][c];
+        if (c == 0) g += ch.d[0] * achi[l];
+        ax[l * 32 + es * 8 + (kind == 0 ? c : 4 + c)] += g;
+      }
+    }
+  }
+  for (int s = 0; s < 64; ++s)
+    if (ax[s] != 0.0) atomicAdd(Sa + addr(s), ax[s]);
 }
 
 // ---------------------------------------------------------------------------
@@ -151,29 +234,60 @@ __global__ void __launch_bounds__(128) nodal_vjp_kernel(KArgs<double> a, const d
   };
   double x[NODAL_IN];
   for (int s = 0; s < NODAL_IN; ++s) x[s] = a.Sr[addr(s)];
-  const GenoK<DN> geno = dual_geno<AN>(a.geno);
-  const GasK<DN> gas = dual_gas<AN>(a.gas);
-  const DN h[2] = {DN(a.h[0]), DN(a.h[1])}, ih[2] = {DN(a.ih[0]), DN(a.ih[1])};
-#pragma unroll 1
-  for (int k0 = 0; k0 < NODAL_IN; k0 += AN) {
-    double acc[AN];
-    for (int t = 0; t < AN; ++t) acc[t] = 0.0;
-    nodal_compute<DN>(
-        geno, gas, h, ih,
-        [&](int e, int f) -> DN {
-          const int s = nodal_slot(e, f);
-          DN r(x[s]);
-          const int t = s - k0;
-          if (t >= 0 && t < AN) r.d[t] = 1.0;
-          return r;
-        },
-        [&](int k, const DN& v) {
-#pragma unroll
-          for (int t = 0; t < AN; ++t) acc[t] += v.d[t] * ah[k];
-        });
-    for (int t = 0; t < AN && k0 + t < NODAL_IN; ++t)
-      if (acc[t] != 0.0) atomicAdd(Sa + addr(k0 + t), acc[t]);
+  auto X = [&](int e, int f) { return x[nodal_slot(e, f)]; };
+  // forward values of the node derivatives (dir 0: x with neighbours 1, 2; dir 1: y with 3, 4)
+  double W[4], D[2][4];
+  for (int c = 0; c < 4; ++c) {
+    W[c] = X(0, c);
+    for (int d = 0; d < 2; ++d) {
+      const int em = 1 + 2 * d, ep = 2 + 2 * d, gf = 4 + 4 * d + c;
+      const double q[3] = {X(em, c), W[c], X(ep, c)}, gq[3] = {X(em, gf), X(0, gf), X(ep, gf)};
+      D[d][c] = recon_node(a.geno, q, gq, a.h[d], a.ih[d]);
+    }
   }
+  // nodal flux: adjoint of its 12 inputs (W, W_x, W_y), one pass each
+  const GasK<DN> gas = dual_gas<AN>(a.gas);
+  double aW[4], aD[2][4];
+#pragma unroll 1
+  for (int m = 0; m < 12; ++m) {
+    DN w[4], dx[4], dy[4];
+    for (int c = 0; c < 4; ++c) {
+      w[c] = DN(W[c]);
+      dx[c] = DN(D[0][c]);
+      dy[c] = DN(D[1][c]);
+    }
+    (m < 4 ? w[m] : m < 8 ? dx[m - 4] : dy[m - 8]).d[0] = 1.0;
+    DN F[4], G[4], Ft[4], Gt[4];
+    nodal_flux(gas, w, dx, dy, F, G, Ft, Gt);
+    double acc = 0.0;
+    for (int c = 0; c < 4; ++c)
+      acc += F[c].d[0] * ah[c] + G[c].d[0] * ah[4 + c] + Ft[c].d[0] * ah[8 + c] + Gt[c].d[0] * ah[12 + c];
+    if (m < 4) aW[m] = acc;
+    else aD[(m - 4) / 4][m % 4] = acc;
+  }
+  // node derivatives: pass q seeds stencil entry q % 3, value (q < 3) or gradient, of all eight
+  const GenoK<DN> geno = dual_geno<AN>(a.geno);
+  double ax[NODAL_IN] = {};
+  for (int c = 0; c < 4; ++c) ax[nodal_slot(0, c)] += aW[c];
+#pragma unroll 1
+  for (int q = 0; q < 6; ++q) {
+    const int es = q % 3, kind = q / 3;
+    for (int d = 0; d < 2; ++d)
+      for (int c = 0; c < 4; ++c) {
+        const int em = 1 + 2 * d, ep = 2 + 2 * d, gf = 4 + 4 * d + c;
+        const int ent[3] = {em, 0, ep};
+        DN qv[3], gv[3];
+        for (int t = 0; t < 3; ++t) {
+          qv[t] = DN(X(ent[t], c));
+          gv[t] = DN(X(ent[t], gf));
+        }
+        (kind == 0 ? qv[es] : gv[es]).d[0] = 1.0;
+        const DN r = recon_node(geno, qv, gv, DN(a.h[d]), DN(a.ih[d]));
+        ax[nodal_slot(ent[es], kind == 0 ? c : gf)] += r.d[0] * aD[d][c];
+      }
+  }
+  for (int s = 0; s < NODAL_IN; ++s)
+    if (ax[s] != 0.0) atomicAdd(Sa + addr(s), ax[s]);
 }
 
 // ---------------------------------------------------------------------------
