@@ -407,7 +407,8 @@ def run_lines(args, world):
     """The one-dimensional scheme (Sec. 2) on Woodward-Colella blast-wave lines
     (Sec. 5.3), N = 400, FD-CGKS(6-2) with App. D's GENO constants, run to
     t = 0.038 with each line's own CFL steps inside one launch: one line (the
-    time to solution of the paper's run) and a batch of 4 lines per SM
+    time to solution of the paper's run; spread over a thread-block cluster by
+    default, and on one block for comparison) and a batch of 4 lines per SM
     (throughput); and the Sod and Lax tubes (Sec. 5.2, N = 100) as single
     lines."""
     import numpy as np
@@ -418,11 +419,12 @@ def run_lines(args, world):
     out = {"config": {"workload": "Woodward-Colella blast waves, [0,1], N = 400, reflecting ends, "
                                   "FD-CGKS(6-2), GENO App. D, CFL 0.4, to t = 0.038, one thread block per line; "
                                   "Sod (t = 0.2) and Lax (t = 0.16) tubes, N = 100"}}
-    for name, case, t_end, batch in (("one_line", wc, 0.038, 1), ("batch", wc, 0.038, 4 * sms),
-                                     ("sod", inputs.sod_strip(100, 1), 0.2, 1),
-                                     ("lax", inputs.lax_strip(100, 1), 0.16, 1)):
+    for name, case, t_end, batch, cs in (("one_line", wc, 0.038, 1, 0), ("one_line_one_block", wc, 0.038, 1, 1),
+                                         ("batch", wc, 0.038, 4 * sms, 0),
+                                         ("sod", inputs.sod_strip(100, 1), 0.2, 1, 0),
+                                         ("lax", inputs.lax_strip(100, 1), 0.16, 1, 0)):
         W, G = inputs.line_state(case)
-        with fdcgks.Lines.from_case(case, batch) as L:
+        with fdcgks.Lines.from_case(case, batch, cluster=cs) as L:
             L.set_state(np.ascontiguousarray(np.broadcast_to(W, (batch,) + W.shape)),
                         np.ascontiguousarray(np.broadcast_to(G, (batch,) + G.shape)))
             torch.cuda.synchronize()
@@ -435,7 +437,8 @@ def run_lines(args, world):
             ms = max_over_ranks(e0.elapsed_time(e1), world)
             _, bad = L.check()
         updates = float(kk.sum()) * case.nx
-        out[name] = {"lines": batch, "steps": int(kk.max()), "t": float(tt.min()), "ms": ms,
+        out[name] = {"lines": batch, "blocks_per_line": cs or "auto", "steps": int(kk.max()), "t": float(tt.min()),
+                     "ms": ms,
                      "value": updates * world / (ms / 1e3), "unit": UNIT, "launches": 1, "nonphysical": bool(bad)}
     return out
 

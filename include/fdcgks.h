@@ -349,8 +349,9 @@ const char* fdcgks_ens_last_error(fdcgks_ens_t ens);
  * S2O4 (Eqs. eq-nodal-update, eq-interface-update); the interface values
  * of the gradient update are the solve's own W^(l,r) (Eq. eq:W-model).
  * The lines share grid, gas and options and evolve independently: one
- * thread block advances one line through whole steps, so a call is one
- * kernel launch whatever the number of steps.  FP64 only.
+ * thread block (or a cluster of blocks, see cluster) advances one line
+ * through whole steps, so a call is one kernel launch whatever the number of
+ * steps.  FP64 only.
  *   - bc[0], bc[1]: PERIODIC (both ends), TRANSMISSIVE or SYMMETRY
  *     (a reflecting wall); n >= 3 (bounded) or >= 1 (periodic); batch >= 1.
  *   - State arrays W [batch][3][n] and Wx [batch][3][n], row-major; host or
@@ -369,6 +370,10 @@ typedef struct {
   double tau_c1, tau_c2;
   int recon_vars;
   void* stream;                /* cudaStream_t, NULL = default stream */
+  int cluster;                 /* blocks per line: 1, 2, 4 or 8 (a thread-block cluster
+                                  on as many SMs), or 0: automatic (clusters while the
+                                  batch leaves SMs idle, >= 32 nodes per block).  The
+                                  results do not depend on it. */
 } fdcgks_line_params;
 typedef struct fdcgks_line_ctx* fdcgks_line_t;
 fdcgks_status fdcgks_line_create(const fdcgks_line_params* params, fdcgks_line_t* out);

@@ -8,10 +8,14 @@
 //   stage 1: ghosts(S) -> interface solves + nodal fluxes -> update S -> T
 //   stage 2: ghosts(T) -> interface solves + nodal fluxes -> update T -> S
 //
-// with block barriers between the phases, so a call runs any number of
-// steps (fixed dt, or each line's own CFL dt found by a block reduction)
-// in a single launch, and the lines of a batch run side by side on the
-// SMs.  The line's working arrays stay in global memory (L2-resident for
+// with barriers between the phases, so a call runs any number of steps
+// (fixed dt, or each line's own CFL dt found by a reduction) in a single
+// launch, and the lines of a batch run side by side on the SMs.  A line can
+// also be spread over a thread-block cluster of 2, 4 or 8 blocks (on as many
+// SMs): the phases' work items are dealt out over the cluster's threads and
+// the phases are separated by cluster barriers, whose release/acquire
+// ordering makes each block's global-memory writes visible to the others.
+// A single line then runs at the FP64 rate of several SMs instead of one.  The line's working arrays stay in global memory (L2-resident for
 // the line sizes of Sec. 5); the per-node device functions are the 2-D
 // path's: the line reconstruction of the 2-D interface points with the
 // y-momentum set to zero, the x-normal kinetic solve with V = 0 and no
@@ -23,8 +27,12 @@
 #include <cstring>
 #include <new>
 
+#include <cooperative_groups.h>
+
 #include "../../include/fdcgks.h"
 #include "fdcgks_kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 using namespace fdk;
 
@@ -37,6 +45,7 @@ enum { LINE_STEPS = 0, LINE_RUN = 1, LINE_OPERATOR = 2 };
 
 struct LineArgs {
   int n, np;                 // nodes; padded length n + 2 GH
+  int cs;                    // blocks per line (a cluster when > 1)
   int bc0, bc1, fv, grad_base, recon_vars;
   double h, ih, gamma, mu;
   GenoK<double> geno;
@@ -49,8 +58,19 @@ struct LineArgs {
   double* tl;                // [batch] line time
   int* ns;                   // [batch] steps taken by the last run
   int* flag;                 // [batch] status bits
+  double* part;              // [batch][cs][2] per-block CFL maxima
   double* op[4];             // LINE_OPERATOR outputs [batch][3][n]
 };
+
+// this thread's index among the line's threads, and their number
+__device__ __forceinline__ int lt_index(const LineArgs& a) { return (blockIdx.x % a.cs) * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int lt_count(const LineArgs& a) { return a.cs * blockDim.x; }
+
+// barrier over the line's threads (block or cluster), ordering their memory accesses
+__device__ __forceinline__ void line_sync(const LineArgs& a) {
+  if (a.cs == 1) __syncthreads();
+  else cg::this_cluster().sync();
+}
 
 // conservative component c (0..2) of a line <-> slot of the 2-D 4-vector
 __device__ __forceinline__ int slot4(int c) { return c == 2 ? 3 : c; }
@@ -59,7 +79,7 @@ __device__ __forceinline__ int slot4(int c) { return c == 2 ? 3 : c; }
 // gradient (transmissive), mirror with U odd and each gradient of the
 // opposite parity to its field (reflecting)
 __device__ void line_ghosts(const LineArgs& a, double* B) {
-  for (int idx = threadIdx.x; idx < 2 * GH; idx += blockDim.x) {
+  for (int idx = lt_index(a); idx < 2 * GH; idx += lt_count(a)) {
     const int side = idx / GH, k = 1 + idx % GH;
     const int b = side == 0 ? a.bc0 : a.bc1;
     const int ghost = side == 0 ? -k : a.n - 1 + k;
@@ -85,7 +105,7 @@ __device__ void line_ghosts(const LineArgs& a, double* B) {
 // interface solves (k = -2..n) and nodal fluxes (j = -1..n) of buffer B
 __device__ void line_fluxes(const LineArgs& a, const GasK<double>& gas, const double* B, double* P, double* NF) {
   const int ni = a.n + 3, nn = a.n + 2;
-  for (int idx = threadIdx.x; idx < ni + nn; idx += blockDim.x) {
+  for (int idx = lt_index(a); idx < ni + nn; idx += lt_count(a)) {
     if (idx < ni) {
       const int k = idx - 2;   // interface k + 1/2 from nodes k-1..k+2
       auto ld = [&](int, int e, int f) -> double {
@@ -139,7 +159,7 @@ __device__ void line_fluxes(const LineArgs& a, const GasK<double>& gas, const do
 __device__ void line_update(const LineArgs& a, int mode, int stage, double dt, const double* P, const double* NF,
                             const double* Bin, double* Bout, double* A, int line, int* flag) {
   const int ni = a.n + 3, nn = a.n + 2;
-  for (int j = threadIdx.x; j < a.n; j += blockDim.x) {
+  for (int j = lt_index(a); j < a.n; j += lt_count(a)) {
     const double chip = P[18 * ni + j + 2], chim = P[18 * ni + j + 1];
     double L[3], Lt[3], gb[3], gt[3];
 #pragma unroll
@@ -190,11 +210,13 @@ __device__ void line_update(const LineArgs& a, int mode, int stage, double dt, c
   }
 }
 
-// the line's CFL time step (the same in every thread of the block)
-__device__ double line_cfl(const LineArgs& a, const double* B, double cfl) {
+// the line's CFL time step (the same in every thread of the line): block
+// maxima of (|U| + c)/h and nu, then across the cluster through global memory
+// (k alternates the partial buffer between consecutive steps)
+__device__ double line_cfl(const LineArgs& a, const double* B, double cfl, int line, int k) {
   __shared__ double sr[LT / 32], sn[LT / 32];
   double rate = 0.0, numax = 0.0;
-  for (int j = threadIdx.x; j < a.n; j += blockDim.x)
+  for (int j = lt_index(a); j < a.n; j += lt_count(a))
     cfl_rates(B[GH + j], B[a.np + GH + j], 0.0, B[2 * a.np + GH + j], a.gamma, a.mu, a.ih, 0.0, rate, numax);
   for (int o = 16; o > 0; o >>= 1) {
     rate = fmax(rate, __shfl_xor_sync(0xffffffffu, rate, o));
@@ -212,6 +234,18 @@ __device__ double line_cfl(const LineArgs& a, const double* B, double cfl) {
     numax = fmax(numax, sn[w]);
   }
   __syncthreads();   // sr, sn are rewritten by the next call
+  if (a.cs > 1) {
+    double* part = a.part + ((long)line * 2 + (k & 1)) * a.cs * 2;
+    if (threadIdx.x == 0) {
+      part[2 * (blockIdx.x % a.cs)] = rate;
+      part[2 * (blockIdx.x % a.cs) + 1] = numax;
+    }
+    line_sync(a);
+    for (int r = 0; r < a.cs; ++r) {
+      rate = fmax(rate, part[2 * r]);
+      numax = fmax(numax, part[2 * r + 1]);
+    }
+  }
   double dt = cfl / rate;
   if (numax > 0.0) dt = fmin(dt, cfl * a.h * a.h / (8.0 * numax));
   return dt;
@@ -220,16 +254,17 @@ __device__ double line_cfl(const LineArgs& a, const double* B, double cfl) {
 __device__ void line_stage(const LineArgs& a, const GasK<double>& gas, int mode, int stage, double dt,
                            double* Bin, double* Bout, double* P, double* NF, double* A, int line, int* flag) {
   line_ghosts(a, Bin);
-  __syncthreads();
+  line_sync(a);
   line_fluxes(a, gas, Bin, P, NF);
-  __syncthreads();
+  line_sync(a);
   line_update(a, mode, stage, dt, P, NF, Bin, Bout, A, line, flag);
-  __syncthreads();
+  line_sync(a);
 }
 
 __global__ void __launch_bounds__(LT) line_kernel(LineArgs a, int mode, double dt_fixed, int nsteps, double t_end,
                                                   double cfl, int max_steps) {
-  const int b = blockIdx.x;
+  const int b = blockIdx.x / a.cs;
+  const bool lead = blockIdx.x % a.cs == 0 && threadIdx.x == 0;
   const long pad = 6L * a.np;
   double* S = a.S + b * pad;
   double* T = a.T + b * pad;
@@ -251,9 +286,9 @@ __global__ void __launch_bounds__(LT) line_kernel(LineArgs a, int mode, double d
   while (mode == LINE_STEPS ? k < nsteps : (k < max_steps && t < t_end * (1.0 - 1e-14))) {
     double dt = dt_fixed;
     if (mode == LINE_RUN) {
-      dt = fmin(line_cfl(a, S, cfl), t_end - t);
+      dt = fmin(line_cfl(a, S, cfl, b, k), t_end - t);
       if (!(dt > 0.0) || !(dt < INFINITY)) {
-        if (threadIdx.x == 0) atomicOr(flag, 2);
+        if (lead) atomicOr(flag, 2);
         break;
       }
     }
@@ -264,10 +299,11 @@ __global__ void __launch_bounds__(LT) line_kernel(LineArgs a, int mode, double d
     t += dt;
     ++k;
     // a run stops a line that left the physical states (the flag is read
-    // after the stage's closing barrier, so every thread sees the same value)
+    // after the stage's closing barrier, so every thread of the line sees the
+    // same value and the line's blocks leave the loop together)
     if (mode == LINE_RUN && (*(volatile int*)flag & 1)) break;
   }
-  if (threadIdx.x == 0) {
+  if (lead) {
     a.tl[b] = t;
     a.ns[b] = k;
   }
@@ -333,6 +369,8 @@ const char* check_line_params(const fdcgks_line_params* p) {
   if ((p->bc[0] == FDCGKS_BC_PERIODIC) != (p->bc[1] == FDCGKS_BC_PERIODIC))
     return "a periodic line is periodic at both ends";
   if (p->bc[0] != FDCGKS_BC_PERIODIC && p->n < 3) return "a bounded line needs n >= 3";
+  if (p->cluster != 0 && p->cluster != 1 && p->cluster != 2 && p->cluster != 4 && p->cluster != 8)
+    return "cluster must be 0 (automatic), 1, 2, 4 or 8";
   // the remaining options are those of the 2-D scheme
   fdcgks_params q;
   std::memset(&q, 0, sizeof(q));
@@ -358,8 +396,19 @@ const char* check_line_params(const fdcgks_line_params* p) {
 }
 
 fdcgks_status launch_line(fdcgks_line_t c, int mode, double dt, int nsteps, double t_end, double cfl, int max_steps) {
-  line_kernel<<<c->p.batch, LT, 0, c->stream>>>(c->a, mode, dt, nsteps, t_end, cfl, max_steps);
-  LINE_TRY(c, cudaGetLastError());
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3((unsigned)(c->p.batch * c->a.cs));
+  cfg.blockDim = dim3(LT);
+  cfg.stream = c->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)c->a.cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  LINE_TRY(c, cudaLaunchKernelEx(&cfg, line_kernel, c->a, mode, dt, nsteps, t_end, cfl, max_steps));
   ++c->launches;
   return FDCGKS_OK;
 }
@@ -381,6 +430,17 @@ fdcgks_status fdcgks_line_create(const fdcgks_line_params* p, fdcgks_line_t* out
   LineArgs& a = c->a;
   a.n = n;
   a.np = np;
+  // blocks per line: as asked, or automatic: spread lines over clusters of up
+  // to 8 blocks while the batch leaves SMs idle (two blocks fit an SM), with
+  // at least 32 nodes per block
+  a.cs = p->cluster;
+  if (a.cs == 0) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+    a.cs = 1;
+    while (a.cs < 8 && (long)B * a.cs * 2 <= 2L * sms && n / (a.cs * 2) >= 32) a.cs *= 2;
+  }
   a.bc0 = p->bc[0];
   a.bc1 = p->bc[1];
   a.fv = p->flux_variant;
@@ -399,10 +459,10 @@ fdcgks_status fdcgks_line_create(const fdcgks_line_params* p, fdcgks_line_t* out
   q.tau_c1 = p->tau_c1;
   q.tau_c2 = p->tau_c2;
   a.gas = make_gas<double>(q, 1.0);
-  // doubles: S, T, P, NF, A, tl, staging; ints: ns, flag
+  // doubles: S, T, P, NF, A, tl, staging, CFL partials; ints: ns, flag
   const size_t nS = (size_t)B * 6 * np, nP = (size_t)B * NPF * (n + 3), nN = (size_t)B * 6 * (n + 2),
-               nA = (size_t)B * 6 * n, nStage = (size_t)B * 6 * n;
-  const size_t nd = 2 * nS + nP + nN + nA + B + nStage;
+               nA = (size_t)B * 6 * n, nStage = (size_t)B * 6 * n, nPart = (size_t)B * 4 * a.cs;
+  const size_t nd = 2 * nS + nP + nN + nA + B + nStage + nPart;
   const size_t bytes = nd * sizeof(double) + 2 * (size_t)B * sizeof(int);
   cudaError_t e = cudaMalloc(&c->mem, bytes);
   if (e != cudaSuccess) {
@@ -424,6 +484,8 @@ fdcgks_status fdcgks_line_create(const fdcgks_line_params* p, fdcgks_line_t* out
   d += B;
   c->stage = d;
   d += nStage;
+  a.part = d;
+  d += nPart;
   a.ns = (int*)d;
   a.flag = a.ns + B;
   for (int k = 0; k < 4; ++k) a.op[k] = nullptr;

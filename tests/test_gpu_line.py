@@ -282,3 +282,24 @@ def test_sod_200_to_final_time_on_both_paths():
         assert np.abs(rho - ex[0]).mean() < er
         assert np.abs(u - ex[1]).mean() < eu
         assert rho.max() < top and rho.min() > 0.125 * 0.99
+
+
+@pytest.mark.parametrize("cluster", [2, 4, 8])
+def test_cluster_spread_line_equals_single_block(cluster):
+    """A line spread over a thread-block cluster computes every item with the
+    same arithmetic as one block: fixed steps and CFL runs agree bit for bit."""
+    cases = [inputs.lax_strip(96, 1, recon_vars=1), inputs.woodward_colella(128, flux_variant=62, geno_variant=1)]
+    for case in cases:
+        W, G = inputs.line_state(case)
+        out = {}
+        for cs in (1, cluster):
+            with fdcgks.Lines.from_case(case, batch=3, cluster=cs) as L:
+                L.set_state(np.ascontiguousarray(np.broadcast_to(W, (3,) + W.shape)),
+                            np.ascontiguousarray(np.broadcast_to(G, (3,) + G.shape)))
+                L.steps(1e-4, 7)
+                tt, kk = L.run(0.01, 0.4)
+                out[cs] = (L.get_state(device=False), tt, kk, L.check()[0])
+        (a, ta, ka, fa), (b, tb, kb, fb) = out[1], out[cluster]
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        assert np.array_equal(ta, tb) and np.array_equal(ka, kb) and np.array_equal(fa, fb)
+        assert ka[0] >= 5
