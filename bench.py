@@ -419,12 +419,16 @@ def run_lines(args, world):
     out = {"config": {"workload": "Woodward-Colella blast waves, [0,1], N = 400, reflecting ends, "
                                   "FD-CGKS(6-2), GENO App. D, CFL 0.4, to t = 0.038, one thread block per line; "
                                   "Sod (t = 0.2) and Lax (t = 0.16) tubes, N = 100"}}
-    for name, case, t_end, batch, cs in (("one_line", wc, 0.038, 1, 0), ("one_line_one_block", wc, 0.038, 1, 1),
-                                         ("batch", wc, 0.038, 4 * sms, 0),
-                                         ("sod", inputs.sod_strip(100, 1), 0.2, 1, 0),
-                                         ("lax", inputs.lax_strip(100, 1), 0.16, 1, 0)):
+    FP64, MIXED = fdcgks.FP64, fdcgks.MIXED
+    for name, case, t_end, batch, cs, prec in (("one_line", wc, 0.038, 1, 0, FP64),
+                                               ("one_line_one_block", wc, 0.038, 1, 1, FP64),
+                                               ("batch", wc, 0.038, 4 * sms, 0, FP64),
+                                               ("one_line_mixed", wc, 0.038, 1, 0, MIXED),
+                                               ("batch_mixed", wc, 0.038, 4 * sms, 0, MIXED),
+                                               ("sod", inputs.sod_strip(100, 1), 0.2, 1, 0, FP64),
+                                               ("lax", inputs.lax_strip(100, 1), 0.16, 1, 0, FP64)):
         W, G = inputs.line_state(case)
-        with fdcgks.Lines.from_case(case, batch, cluster=cs) as L:
+        with fdcgks.Lines.from_case(case, batch, cluster=cs, precision=prec) as L:
             L.set_state(np.ascontiguousarray(np.broadcast_to(W, (batch,) + W.shape)),
                         np.ascontiguousarray(np.broadcast_to(G, (batch,) + G.shape)))
             torch.cuda.synchronize()
@@ -437,8 +441,8 @@ def run_lines(args, world):
             ms = max_over_ranks(e0.elapsed_time(e1), world)
             _, bad = L.check()
         updates = float(kk.sum()) * case.nx
-        out[name] = {"lines": batch, "blocks_per_line": cs or "auto", "steps": int(kk.max()), "t": float(tt.min()),
-                     "ms": ms,
+        out[name] = {"lines": batch, "blocks_per_line": cs or "auto", "precision": "mixed" if prec else "fp64",
+                     "steps": int(kk.max()), "t": float(tt.min()), "ms": ms,
                      "value": updates * world / (ms / 1e3), "unit": UNIT, "launches": 1, "nonphysical": bool(bad)}
     return out
 

@@ -351,7 +351,7 @@ const char* fdcgks_ens_last_error(fdcgks_ens_t ens);
  * The lines share grid, gas and options and evolve independently: one
  * thread block (or a cluster of blocks, see cluster) advances one line
  * through whole steps, so a call is one kernel launch whatever the number of
- * steps.  FP64 only.
+ * steps.  FP64 or mixed precision (see precision).
  *   - bc[0], bc[1]: PERIODIC (both ends), TRANSMISSIVE or SYMMETRY
  *     (a reflecting wall); n >= 3 (bounded) or >= 1 (periodic); batch >= 1.
  *   - State arrays W [batch][3][n] and Wx [batch][3][n], row-major; host or
@@ -374,6 +374,10 @@ typedef struct {
                                   on as many SMs), or 0: automatic (clusters while the
                                   batch leaves SMs idle, >= 32 nodes per block).  The
                                   results do not depend on it. */
+  int precision;               /* FDCGKS_FP64, or FDCGKS_MIXED: reconstruction, kinetic
+                                  solves and compact fluxes in FP32 (FP64 time
+                                  coefficients, as the 2-D mixed path); state and S2O4
+                                  accumulation in FP64 either way */
 } fdcgks_line_params;
 typedef struct fdcgks_line_ctx* fdcgks_line_t;
 fdcgks_status fdcgks_line_create(const fdcgks_line_params* params, fdcgks_line_t* out);

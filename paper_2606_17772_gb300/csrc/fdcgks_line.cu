@@ -20,7 +20,11 @@
 // path's: the line reconstruction of the 2-D interface points with the
 // y-momentum set to zero, the x-normal kinetic solve with V = 0 and no
 // tangential variation (the 1-D BGK gas is the 2-D one restricted so), and
-// the nodal solve with W_y = 0.  FP64.
+// the nodal solve with W_y = 0.  The compute type R is FP64, or FP32 (the
+// mixed path: reconstruction, kinetic solves and compact fluxes in FP32 with
+// the 2-D mixed path's FP64 time coefficients, the interface and nodal
+// outputs stored in FP32); the state, its stage copy and the S2O4
+// accumulation are FP64 in both.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -43,17 +47,18 @@ constexpr int NPF = 19;    // interface outputs: F, F_t, W^l, W^r, W^l_t, W^r_t 
 
 enum { LINE_STEPS = 0, LINE_RUN = 1, LINE_OPERATOR = 2 };
 
+template <class R>
 struct LineArgs {
   int n, np;                 // nodes; padded length n + 2 GH
   int cs;                    // blocks per line (a cluster when > 1)
   int bc0, bc1, fv, grad_base, recon_vars;
   double h, ih, gamma, mu;
-  GenoK<double> geno;
-  GasK<double> gas;          // the time-step fields are set per step
+  GenoK<R> geno;
+  GasK<R> gas;               // the time-step fields are set per step
   double* S;                 // [batch][6][np] state (W 3, W_x 3)
   double* T;                 // [batch][6][np] stage-1 state
-  double* P;                 // [batch][NPF][n + 3] interfaces k + 1/2, k = -2..n
-  double* NF;                // [batch][6][n + 2] nodal F, F_t at nodes -1..n
+  R* P;                      // [batch][NPF][n + 3] interfaces k + 1/2, k = -2..n
+  R* NF;                     // [batch][6][n + 2] nodal F, F_t at nodes -1..n
   double* A;                 // [batch][6][n] S2O4 accumulator and gradient base
   double* tl;                // [batch] line time
   int* ns;                   // [batch] steps taken by the last run
@@ -63,11 +68,14 @@ struct LineArgs {
 };
 
 // this thread's index among the line's threads, and their number
-__device__ __forceinline__ int lt_index(const LineArgs& a) { return (blockIdx.x % a.cs) * blockDim.x + threadIdx.x; }
-__device__ __forceinline__ int lt_count(const LineArgs& a) { return a.cs * blockDim.x; }
+template <class R>
+__device__ __forceinline__ int lt_index(const LineArgs<R>& a) { return (blockIdx.x % a.cs) * blockDim.x + threadIdx.x; }
+template <class R>
+__device__ __forceinline__ int lt_count(const LineArgs<R>& a) { return a.cs * blockDim.x; }
 
 // barrier over the line's threads (block or cluster), ordering their memory accesses
-__device__ __forceinline__ void line_sync(const LineArgs& a) {
+template <class R>
+__device__ __forceinline__ void line_sync(const LineArgs<R>& a) {
   if (a.cs == 1) __syncthreads();
   else cg::this_cluster().sync();
 }
@@ -78,7 +86,8 @@ __device__ __forceinline__ int slot4(int c) { return c == 2 ? 3 : c; }
 // ghost nodes of buffer B: periodic wrap, constant extrapolation with zero
 // gradient (transmissive), mirror with U odd and each gradient of the
 // opposite parity to its field (reflecting)
-__device__ void line_ghosts(const LineArgs& a, double* B) {
+template <class R>
+__device__ void line_ghosts(const LineArgs<R>& a, double* B) {
   for (int idx = lt_index(a); idx < 2 * GH; idx += lt_count(a)) {
     const int side = idx / GH, k = 1 + idx % GH;
     const int b = side == 0 ? a.bc0 : a.bc1;
@@ -103,24 +112,26 @@ __device__ void line_ghosts(const LineArgs& a, double* B) {
 }
 
 // interface solves (k = -2..n) and nodal fluxes (j = -1..n) of buffer B
-__device__ void line_fluxes(const LineArgs& a, const GasK<double>& gas, const double* B, double* P, double* NF) {
+template <class R>
+__device__ void line_fluxes(const LineArgs<R>& a, const GasK<R>& gas, const double* B, R* P, R* NF) {
   const int ni = a.n + 3, nn = a.n + 2;
+  const R h = (R)a.h, ih = (R)a.ih;
   for (int idx = lt_index(a); idx < ni + nn; idx += lt_count(a)) {
     if (idx < ni) {
       const int k = idx - 2;   // interface k + 1/2 from nodes k-1..k+2
-      auto ld = [&](int, int e, int f) -> double {
+      auto ld = [&](int, int e, int f) -> R {
         const int s = f & 3;
-        if (s == 2) return 0.0;                       // rho V
+        if (s == 2) return R(0);                      // rho V
         const int c = s == 3 ? 2 : s;
-        return B[((f < 4 ? 0 : 3) + c) * a.np + GH + (k - 1 + e)];
+        return (R)B[((f < 4 ? 0 : 3) + c) * a.np + GH + (k - 1 + e)];
       };
-      double vl[4], dl[4], vr[4], dr[4], chi;
-      if (a.recon_vars) recon_line_char(a.geno, gas.gm1, 0, ld, 0, a.h, a.ih, vl, dl, vr, dr, chi);
-      else recon_line_ld(a.geno, ld, 0, a.h, a.ih, vl, dl, vr, dr, chi);
-      const double zero[4] = {0.0, 0.0, 0.0, 0.0};
-      IfaceOut<double> o;
+      R vl[4], dl[4], vr[4], dr[4], chi;
+      if (a.recon_vars) recon_line_char(a.geno, gas.gm1, 0, ld, 0, h, ih, vl, dl, vr, dr, chi);
+      else recon_line_ld(a.geno, ld, 0, h, ih, vl, dl, vr, dr, chi);
+      const R zero[4] = {R(0), R(0), R(0), R(0)};
+      IfaceOut<R> o;
       iface_solve(gas, 0, vl, vr, dl, dr, zero, true, o);
-      double* q = P + idx;
+      R* q = P + idx;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const int s = slot4(c);
@@ -134,16 +145,16 @@ __device__ void line_fluxes(const LineArgs& a, const GasK<double>& gas, const do
       q[18 * ni] = chi;
     } else {
       const int j = idx - ni - 1;   // node j: value and GENO x-derivative
-      double W[4] = {0.0, 0.0, 0.0, 0.0}, Wx[4] = {0.0, 0.0, 0.0, 0.0}, Wy[4] = {0.0, 0.0, 0.0, 0.0};
+      R W[4] = {R(0), R(0), R(0), R(0)}, Wx[4] = {R(0), R(0), R(0), R(0)}, Wy[4] = {R(0), R(0), R(0), R(0)};
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const double* w = B + c * a.np + GH + j;
         const double* g = B + (3 + c) * a.np + GH + j;
-        const double q[3] = {w[-1], w[0], w[1]}, gx[3] = {g[-1], g[0], g[1]};
-        W[slot4(c)] = w[0];
-        Wx[slot4(c)] = recon_node(a.geno, q, gx, a.h, a.ih);
+        const R q[3] = {(R)w[-1], (R)w[0], (R)w[1]}, gx[3] = {(R)g[-1], (R)g[0], (R)g[1]};
+        W[slot4(c)] = q[1];
+        Wx[slot4(c)] = recon_node(a.geno, q, gx, h, ih);
       }
-      double F[4], G[4], Ft[4], Gt[4];
+      R F[4], G[4], Ft[4], Gt[4];
       nodal_flux(gas, W, Wx, Wy, F, G, Ft, Gt);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -156,27 +167,29 @@ __device__ void line_fluxes(const LineArgs& a, const GasK<double>& gas, const do
 
 // node operator (Eqs. fd-conservative-form, fd-conservative-flux*,
 // define-averaged-gradient) and the S2O4 stage update Bin -> Bout
-__device__ void line_update(const LineArgs& a, int mode, int stage, double dt, const double* P, const double* NF,
+template <class R>
+__device__ void line_update(const LineArgs<R>& a, int mode, int stage, double dt, const R* P, const R* NF,
                             const double* Bin, double* Bout, double* A, int line, int* flag) {
   const int ni = a.n + 3, nn = a.n + 2;
+  const R ih = (R)a.ih;
   for (int j = lt_index(a); j < a.n; j += lt_count(a)) {
-    const double chip = P[18 * ni + j + 2], chim = P[18 * ni + j + 1];
+    const R chip = P[18 * ni + j + 2], chim = P[18 * ni + j + 1];
     double L[3], Lt[3], gb[3], gt[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const double* F = P + c * ni;
-      const double* Ft = P + (3 + c) * ni;
-      const double* nF = NF + c * nn;
-      const double* nFt = NF + (3 + c) * nn;
+      const R* F = P + c * ni;
+      const R* Ft = P + (3 + c) * ni;
+      const R* nF = NF + c * nn;
+      const R* nFt = NF + (3 + c) * nn;
       // interface k + 1/2 sits at P index k + 2, node k at NF index k + 1
-      const double fp = compact_flux(a.fv, chip, F[j + 1], F[j + 2], F[j + 3], nF[j + 1], nF[j + 2]);
-      const double fm = compact_flux(a.fv, chim, F[j], F[j + 1], F[j + 2], nF[j], nF[j + 1]);
-      const double ftp = compact_flux(a.fv, chip, Ft[j + 1], Ft[j + 2], Ft[j + 3], nFt[j + 1], nFt[j + 2]);
-      const double ftm = compact_flux(a.fv, chim, Ft[j], Ft[j + 1], Ft[j + 2], nFt[j], nFt[j + 1]);
-      L[c] = -(fp - fm) * a.ih;
-      Lt[c] = -(ftp - ftm) * a.ih;
-      gb[c] = (P[(6 + c) * ni + j + 2] - P[(9 + c) * ni + j + 1]) * a.ih;
-      gt[c] = (P[(12 + c) * ni + j + 2] - P[(15 + c) * ni + j + 1]) * a.ih;
+      const R fp = compact_flux(a.fv, chip, F[j + 1], F[j + 2], F[j + 3], nF[j + 1], nF[j + 2]);
+      const R fm = compact_flux(a.fv, chim, F[j], F[j + 1], F[j + 2], nF[j], nF[j + 1]);
+      const R ftp = compact_flux(a.fv, chip, Ft[j + 1], Ft[j + 2], Ft[j + 3], nFt[j + 1], nFt[j + 2]);
+      const R ftm = compact_flux(a.fv, chim, Ft[j], Ft[j + 1], Ft[j + 2], nFt[j], nFt[j + 1]);
+      L[c] = (double)(-(fp - fm) * ih);
+      Lt[c] = (double)(-(ftp - ftm) * ih);
+      gb[c] = (double)((P[(6 + c) * ni + j + 2] - P[(9 + c) * ni + j + 1]) * ih);
+      gt[c] = (double)((P[(12 + c) * ni + j + 2] - P[(15 + c) * ni + j + 1]) * ih);
     }
     if (mode == LINE_OPERATOR) {
       const long o = (long)line * 3 * a.n + j;
@@ -213,7 +226,8 @@ __device__ void line_update(const LineArgs& a, int mode, int stage, double dt, c
 // the line's CFL time step (the same in every thread of the line): block
 // maxima of (|U| + c)/h and nu, then across the cluster through global memory
 // (k alternates the partial buffer between consecutive steps)
-__device__ double line_cfl(const LineArgs& a, const double* B, double cfl, int line, int k) {
+template <class R>
+__device__ double line_cfl(const LineArgs<R>& a, const double* B, double cfl, int line, int k) {
   __shared__ double sr[LT / 32], sn[LT / 32];
   double rate = 0.0, numax = 0.0;
   for (int j = lt_index(a); j < a.n; j += lt_count(a))
@@ -251,8 +265,9 @@ __device__ double line_cfl(const LineArgs& a, const double* B, double cfl, int l
   return dt;
 }
 
-__device__ void line_stage(const LineArgs& a, const GasK<double>& gas, int mode, int stage, double dt,
-                           double* Bin, double* Bout, double* P, double* NF, double* A, int line, int* flag) {
+template <class R>
+__device__ void line_stage(const LineArgs<R>& a, const GasK<R>& gas, int mode, int stage, double dt, double* Bin,
+                           double* Bout, R* P, R* NF, double* A, int line, int* flag) {
   line_ghosts(a, Bin);
   line_sync(a);
   line_fluxes(a, gas, Bin, P, NF);
@@ -261,21 +276,30 @@ __device__ void line_stage(const LineArgs& a, const GasK<double>& gas, int mode,
   line_sync(a);
 }
 
-__global__ void __launch_bounds__(LT) line_kernel(LineArgs a, int mode, double dt_fixed, int nsteps, double t_end,
+// the time-step fields of the gas constants (FP64 and compute-type copies)
+template <class R>
+__device__ __forceinline__ void gas_set_dt(GasK<R>& gas, double dt) {
+  gas.dt = dt;
+  gas.inv_dt = 1.0 / dt;
+  gas.dt_r = (R)dt;
+  gas.inv_dt_r = (R)(1.0 / dt);
+}
+
+template <class R>
+__global__ void __launch_bounds__(LT) line_kernel(LineArgs<R> a, int mode, double dt_fixed, int nsteps, double t_end,
                                                   double cfl, int max_steps) {
   const int b = blockIdx.x / a.cs;
   const bool lead = blockIdx.x % a.cs == 0 && threadIdx.x == 0;
   const long pad = 6L * a.np;
   double* S = a.S + b * pad;
   double* T = a.T + b * pad;
-  double* P = a.P + (long)b * NPF * (a.n + 3);
-  double* NF = a.NF + (long)b * 6 * (a.n + 2);
+  R* P = a.P + (long)b * NPF * (a.n + 3);
+  R* NF = a.NF + (long)b * 6 * (a.n + 2);
   double* A = a.A + (long)b * 6 * a.n;
   int* flag = a.flag + b;
-  GasK<double> gas = a.gas;
+  GasK<R> gas = a.gas;
   if (mode == LINE_OPERATOR) {
-    gas.dt = gas.dt_r = dt_fixed;
-    gas.inv_dt = gas.inv_dt_r = 1.0 / dt_fixed;
+    gas_set_dt(gas, dt_fixed);
     line_stage(a, gas, mode, 0, dt_fixed, S, T, P, NF, A, b, flag);
     return;
   }
@@ -292,8 +316,7 @@ __global__ void __launch_bounds__(LT) line_kernel(LineArgs a, int mode, double d
         break;
       }
     }
-    gas.dt = gas.dt_r = dt;
-    gas.inv_dt = gas.inv_dt_r = 1.0 / dt;
+    gas_set_dt(gas, dt);
     line_stage(a, gas, mode, 0, dt, S, T, P, NF, A, b, flag);
     line_stage(a, gas, mode, 1, dt, T, S, P, NF, A, b, flag);
     t += dt;
@@ -331,7 +354,8 @@ __global__ void line_gather_kernel(const double* S, double* W, double* Wx, int n
 
 struct fdcgks_line_ctx {
   fdcgks_line_params p;
-  LineArgs a;
+  LineArgs<double> a;        // FP64 path (the shared buffers; a32 aliases them for the mixed path)
+  LineArgs<float> a32;
   cudaStream_t stream;
   void* mem = nullptr;       // one allocation for every array
   double* stage = nullptr;   // [2][batch][3][n] host-copy staging
@@ -371,6 +395,7 @@ const char* check_line_params(const fdcgks_line_params* p) {
   if (p->bc[0] != FDCGKS_BC_PERIODIC && p->n < 3) return "a bounded line needs n >= 3";
   if (p->cluster != 0 && p->cluster != 1 && p->cluster != 2 && p->cluster != 4 && p->cluster != 8)
     return "cluster must be 0 (automatic), 1, 2, 4 or 8";
+  if (p->precision != FDCGKS_FP64 && p->precision != FDCGKS_MIXED) return "precision must be FP64 or MIXED";
   // the remaining options are those of the 2-D scheme
   fdcgks_params q;
   std::memset(&q, 0, sizeof(q));
@@ -408,7 +433,13 @@ fdcgks_status launch_line(fdcgks_line_t c, int mode, double dt, int nsteps, doub
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  LINE_TRY(c, cudaLaunchKernelEx(&cfg, line_kernel, c->a, mode, dt, nsteps, t_end, cfl, max_steps));
+  if (c->p.precision == FDCGKS_MIXED) {
+    LineArgs<float> a = c->a32;
+    for (int k = 0; k < 4; ++k) a.op[k] = c->a.op[k];
+    LINE_TRY(c, cudaLaunchKernelEx(&cfg, line_kernel<float>, a, mode, dt, nsteps, t_end, cfl, max_steps));
+  } else {
+    LINE_TRY(c, cudaLaunchKernelEx(&cfg, line_kernel<double>, c->a, mode, dt, nsteps, t_end, cfl, max_steps));
+  }
   ++c->launches;
   return FDCGKS_OK;
 }
@@ -427,7 +458,7 @@ fdcgks_status fdcgks_line_create(const fdcgks_line_params* p, fdcgks_line_t* out
   c->err[0] = 0;
   c->stream = (cudaStream_t)p->stream;
   const int n = p->n, B = p->batch, np = n + 2 * GH;
-  LineArgs& a = c->a;
+  LineArgs<double>& a = c->a;
   a.n = n;
   a.np = np;
   // blocks per line: as asked, or automatic: spread lines over clusters of up
@@ -489,6 +520,18 @@ fdcgks_status fdcgks_line_create(const fdcgks_line_params* p, fdcgks_line_t* out
   a.ns = (int*)d;
   a.flag = a.ns + B;
   for (int k = 0; k < 4; ++k) a.op[k] = nullptr;
+  // the mixed path's view: the same buffers, FP32 interface and nodal outputs
+  // in the (larger) FP64 arrays' space, FP32 constants
+  LineArgs<float>& f = c->a32;
+  f.n = a.n; f.np = a.np; f.cs = a.cs;
+  f.bc0 = a.bc0; f.bc1 = a.bc1; f.fv = a.fv; f.grad_base = a.grad_base; f.recon_vars = a.recon_vars;
+  f.h = a.h; f.ih = a.ih; f.gamma = a.gamma; f.mu = a.mu;
+  f.geno = make_geno<float>(p->geno_variant);
+  f.gas = make_gas<float>(q, 1.0);
+  f.S = a.S; f.T = a.T; f.A = a.A; f.tl = a.tl; f.ns = a.ns; f.flag = a.flag; f.part = a.part;
+  f.P = (float*)a.P;
+  f.NF = (float*)a.NF;
+  for (int k = 0; k < 4; ++k) f.op[k] = nullptr;
   e = cudaMemsetAsync(c->mem, 0, bytes, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
@@ -569,13 +612,12 @@ fdcgks_status fdcgks_line_stage_operator(fdcgks_line_t c, double dt, double* L, 
   if (!c) return lfail(nullptr, FDCGKS_ERR_ARG, "ctx is NULL");
   if (!(dt > 0.0) || !std::isfinite(dt)) return lfail(c, FDCGKS_ERR_ARG, "dt must be positive and finite");
   if (!L || !Lt || !gb || !gt) return lfail(c, FDCGKS_ERR_ARG, "output pointer is NULL");
-  LineArgs keep = c->a;
   c->a.op[0] = L;
   c->a.op[1] = Lt;
   c->a.op[2] = gb;
   c->a.op[3] = gt;
   fdcgks_status s = launch_line(c, LINE_OPERATOR, dt, 0, 0.0, 0.0, 0);
-  c->a = keep;
+  for (int k = 0; k < 4; ++k) c->a.op[k] = nullptr;
   return s;
 }
 

@@ -62,11 +62,13 @@ class LineParams(ctypes.Structure):
         ("recon_vars", ctypes.c_int),
         ("stream", ctypes.c_void_p),
         ("cluster", ctypes.c_int),
+        ("precision", ctypes.c_int),
     ]
 
 
 def line_params(n, batch=1, x0=0.0, x1=1.0, gamma=1.4, mu=0.0, Pr=1.0, bc=(1, 1), flux_variant=64,
-                geno_variant=0, grad_base=0, tau_c1=0.0, tau_c2=0.0, recon_vars=0, stream=None, cluster=0):
+                geno_variant=0, grad_base=0, tau_c1=0.0, tau_c2=0.0, recon_vars=0, stream=None, cluster=0,
+                precision=FP64):
     p = LineParams()
     p.n, p.batch, p.x0, p.x1 = n, batch, x0, x1
     p.gamma, p.mu, p.Pr = gamma, mu, Pr
@@ -75,14 +77,15 @@ def line_params(n, batch=1, x0=0.0, x1=1.0, gamma=1.4, mu=0.0, Pr=1.0, bc=(1, 1)
     p.tau_c1, p.tau_c2, p.recon_vars = tau_c1, tau_c2, recon_vars
     p.stream = stream
     p.cluster = cluster
+    p.precision = precision
     return p
 
 
-def line_params_for_case(case, batch=1, stream=None, cluster=0):
+def line_params_for_case(case, batch=1, stream=None, cluster=0, precision=FP64):
     """LineParams of a strip case (inputs.Case; its x extent, gas, x-ends and options)."""
     return line_params(case.nx, batch, case.x0, case.x1, case.gamma, case.mu, case.Pr, tuple(case.bc[:2]),
                        case.flux_variant, case.geno_variant, case.grad_base, case.tau_c1, case.tau_c2,
-                       case.recon_vars, stream, cluster)
+                       case.recon_vars, stream, cluster, precision)
 
 
 class Side(ctypes.Structure):
@@ -612,8 +615,8 @@ class Lines:
         self.n, self.batch = params.n, params.batch
 
     @classmethod
-    def from_case(cls, case, batch=1, cluster=0):
-        return cls(line_params_for_case(case, batch, cluster=cluster))
+    def from_case(cls, case, batch=1, cluster=0, precision=FP64):
+        return cls(line_params_for_case(case, batch, cluster=cluster, precision=precision))
 
     def close(self):
         if getattr(self, "_h", None):

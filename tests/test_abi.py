@@ -88,10 +88,10 @@ def test_line_params_struct_layout_matches_header():
 #include <stddef.h>
 #include "fdcgks.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(fdcgks_line_params), offsetof(fdcgks_line_params, bc),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(fdcgks_line_params), offsetof(fdcgks_line_params, bc),
          offsetof(fdcgks_line_params, flux_variant), offsetof(fdcgks_line_params, tau_c1),
          offsetof(fdcgks_line_params, recon_vars), offsetof(fdcgks_line_params, stream),
-         offsetof(fdcgks_line_params, cluster));
+         offsetof(fdcgks_line_params, cluster), offsetof(fdcgks_line_params, precision));
   return 0;
 }
 """
@@ -103,12 +103,12 @@ int main(void) {
         vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     P = fdcgks.LineParams
     assert vals == [ctypes.sizeof(P), P.bc.offset, P.flux_variant.offset, P.tau_c1.offset, P.recon_vars.offset,
-                    P.stream.offset, P.cluster.offset]
+                    P.stream.offset, P.cluster.offset, P.precision.offset]
 
 
 @pytest.mark.parametrize("bad", [dict(n=2), dict(n=0), dict(batch=0), dict(bc=(0, 1)), dict(bc=(3, 3)),
                                  dict(flux_variant=63), dict(gamma=1.0), dict(recon_vars=2), dict(cluster=3),
-                                 dict(cluster=16)])
+                                 dict(cluster=16), dict(precision=2)])
 def test_invalid_line_parameters_are_rejected_before_device_work(lib, bad):
     kw = dict(n=20, batch=1, bc=(1, 1))
     kw.update(bad)

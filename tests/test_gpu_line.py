@@ -303,3 +303,55 @@ def test_cluster_spread_line_equals_single_block(cluster):
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
         assert np.array_equal(ta, tb) and np.array_equal(ka, kb) and np.array_equal(fa, fb)
         assert ka[0] >= 5
+
+
+@pytest.mark.parametrize("name", ["periodic_64", "transmissive_viscous", "reflecting_char"])
+def test_mixed_precision_steps_within_fp32_error(name):
+    """Mixed precision (FP32 reconstruction and kinetic solves, FP64 state and
+    accumulation): 20 steps of smooth lines against the FP64 oracle, within
+    the FP32 arithmetic's error accumulated over the steps (5e-6 of the state,
+    1e-4 of the gradients, relative to each group's magnitude; 1.4e-6 of the
+    state measured on the periodic line)."""
+    case = CASES[name]()
+    p = oracle.make_params(**case.oracle_kwargs())
+    W, G = inputs.line_state(case)
+    ref = oracle.steps_1d(p, 0.004, 20, W, G)
+    with fdcgks.Lines.from_case(case, precision=fdcgks.MIXED) as L:
+        L.set_state(W, G)
+        L.steps(0.004, 20)
+        gw, gg = L.get_state(device=False)
+        assert L.check()[1] == 0
+    ew, eg = errs((gw[0], gg[0]), ref)
+    assert ew < 5e-6 and eg < 1e-4, (ew, eg)
+    assert ew > 0.0                               # the FP32 arithmetic is in use
+
+
+def test_mixed_precision_sod_and_blast_waves_to_final_time():
+    """Mixed-precision CFL runs of the Sod tube (exact solution as for FP64) and
+    of the Woodward-Colella blast waves (stays physical; density peak within
+    2 % of the FP64 run), each on a cluster and bit-identical on one block."""
+    sod = inputs.sod_strip(200, 1)
+    X, _ = sod.node_xy(False)
+    ex = exact_riemann.sample((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), X[0], 0.2)
+    W, G = inputs.line_state(sod)
+    res = {}
+    for cs in (0, 1):
+        with fdcgks.Lines.from_case(sod, precision=fdcgks.MIXED, cluster=cs) as L:
+            L.set_state(W, G)
+            tt, kk = L.run(0.2, 0.3)
+            res[cs] = L.get_state(device=False)
+            assert L.check()[1] == 0
+    assert np.array_equal(res[0][0], res[1][0])
+    rho = res[0][0][0][0]
+    assert np.abs(rho - ex[0]).mean() < 0.0040
+    assert np.abs(res[0][0][0][1] / rho - ex[1]).mean() < 0.0105
+    wc = inputs.woodward_colella(400, flux_variant=62, geno_variant=1)
+    W, G = inputs.line_state(wc)
+    peaks = {}
+    for prec in (fdcgks.FP64, fdcgks.MIXED):
+        with fdcgks.Lines.from_case(wc, precision=prec) as L:
+            L.set_state(W, G)
+            tt, kk = L.run(0.038, 0.4)
+            assert L.check()[1] == 0 and tt[0] == pytest.approx(0.038)
+            peaks[prec] = L.get_state(device=False)[0][0][0].max()
+    assert peaks[fdcgks.MIXED] == pytest.approx(peaks[fdcgks.FP64], rel=0.02)
