@@ -379,8 +379,10 @@ def run_double_mach(args, world):
         case = inputs.double_mach(nx, ny, flux_variant=62, recon_vars=1)
         nodes = case.nx * case.ny + case.nxd * case.nyd
         res = {"config": {"workload": "double Mach reflection, [0,4]x[0,1], %dx%d (+%dx%d dual), Mach 10, "
-                                      "FD-CGKS(6-2), characteristic reconstruction; window after 20 CFL-0.4 steps"
-                                      % (nx, ny, case.nxd, case.nyd), "node_updates_per_step": nodes}}
+                                      "FD-CGKS(6-2), characteristic reconstruction, tau c1 = 0.05, c2 = 25; "
+                                      "window after 20 CFL-0.4 steps; full_run_mixed: to t = 0.2 with a CFL-0.4 "
+                                      "step each step (host loop)" % (nx, ny, case.nxd, case.nyd),
+                          "node_updates_per_step": nodes}}
         for name, prec, k in (("fp64", fdcgks.FP64, args.dmr_steps), ("mixed", fdcgks.MIXED, 4 * args.dmr_steps)):
             with fdcgks.Solver.from_case(case, prec) as s:
                 s.set_state(*case.initial_state())
@@ -399,6 +401,22 @@ def run_double_mach(args, world):
                 t_end = s.get_time()
             res[name] = {"value": nodes * k * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / k, "steps": k,
                          "dt": dt, "t_end": t_end, "nonphysical": bool(bad)}
+        # the paper's run to t = 0.2 in mixed precision (time to solution)
+        from paper_2606_17772_gb300 import runs
+        with fdcgks.Solver.from_case(case, fdcgks.MIXED) as s:
+            s.set_state(*case.initial_state())
+            torch.cuda.synchronize()
+            barrier(world)
+            t0 = time.perf_counter()
+            try:
+                t_run, n_run = runs.advance(s, 0.2, 0.4)
+                ok = True
+            except RuntimeError:
+                t_run, n_run, ok = s.get_time(), -1, False
+            torch.cuda.synchronize()
+            wall = max_over_ranks(time.perf_counter() - t0, world)
+            rho_max = float(s.get_state(device=False)[0][0].max())
+        res["full_run_mixed"] = {"t": t_run, "steps": n_run, "seconds": wall, "physical": ok, "rho_max": rho_max}
         out["%dx%d" % (nx, ny)] = res
     return out
 
