@@ -310,8 +310,9 @@ def test_mixed_precision_steps_within_fp32_error(name):
     """Mixed precision (FP32 reconstruction and kinetic solves, FP64 state and
     accumulation): 20 steps of smooth lines against the FP64 oracle, within
     the FP32 arithmetic's error accumulated over the steps (5e-6 of the state,
-    1e-4 of the gradients, relative to each group's magnitude; 1.4e-6 of the
-    state measured on the periodic line)."""
+    5e-4 of the gradients, relative to each group's magnitude; 1.4e-6 and
+    1.4e-4 measured on the periodic line: the averaged gradients are
+    differences of interface values over h, which loses FP32 digits)."""
     case = CASES[name]()
     p = oracle.make_params(**case.oracle_kwargs())
     W, G = inputs.line_state(case)
@@ -322,7 +323,7 @@ def test_mixed_precision_steps_within_fp32_error(name):
         gw, gg = L.get_state(device=False)
         assert L.check()[1] == 0
     ew, eg = errs((gw[0], gg[0]), ref)
-    assert ew < 5e-6 and eg < 1e-4, (ew, eg)
+    assert ew < 5e-6 and eg < 5e-4, (ew, eg)
     assert ew > 0.0                               # the FP32 arithmetic is in use
 
 
