@@ -41,9 +41,10 @@ def advance(solver, t_end, cfl, check_every=200, t0=0.0):
     return t, n
 
 
-def viscous_shock_tube(nx=1000, ny=500, precision=fdcgks.MIXED, t_end=1.0, cfl=0.4):
-    """Run Sec. 5.8's viscous shock tube; returns a summary dict."""
-    case = inputs.viscous_shock_tube(nx, ny)
+def viscous_shock_tube(nx=1000, ny=500, precision=fdcgks.MIXED, t_end=1.0, cfl=0.4, **kw):
+    """Run Sec. 5.8's viscous shock tube; returns a summary dict.  kw: scheme
+    options of inputs.viscous_shock_tube (tau_c1, tau_c2, recon_vars, ...)."""
+    case = inputs.viscous_shock_tube(nx, ny, **kw)
     with fdcgks.Solver.from_case(case, precision) as s:
         s.set_state(*case.initial_state())
         w0 = time.perf_counter()
@@ -61,8 +62,8 @@ def viscous_shock_tube(nx=1000, ny=500, precision=fdcgks.MIXED, t_end=1.0, cfl=0
     w = (0.075 - yrow[k]) / (yrow[k + 1] - yrow[k])
     rho_line = (1 - w) * Wp[0, k] + w * Wp[0, k + 1]
     return {
-        "case": "viscous shock tube, Re 200 (mu 0.005), Pr %.2f, %d x %d, %s, CFL %.2f" % (
-            case.Pr, nx, ny, "mixed" if precision == fdcgks.MIXED else "fp64", cfl),
+        "case": "viscous shock tube, Re 200 (mu 0.005), Pr %.2f, %d x %d, %s, CFL %.2f, tau c1 %g c2 %g" % (
+            case.Pr, nx, ny, "mixed" if precision == fdcgks.MIXED else "fp64", cfl, case.tau_c1, case.tau_c2),
         "t": t, "steps": n, "wall_seconds": wall,
         "node_updates_per_s": n * (nx * ny + case.nxd * case.nyd) / wall,
         "rho_min": float(min(Wp[0].min(), Wd[0].min())), "rho_max": float(max(Wp[0].max(), Wd[0].max())),
@@ -82,9 +83,9 @@ def _timed_run(case, precision, t_end, cfl):
     return state, t, n, wall, t_ctx
 
 
-def double_mach(nx=960, ny=240, precision=fdcgks.FP64, t_end=0.2, cfl=0.4, flux_variant=62, recon_vars=1):
+def double_mach(nx=960, ny=240, precision=fdcgks.FP64, t_end=0.2, cfl=0.4, flux_variant=62, recon_vars=1, **kw):
     """Run Sec. 5.5's double Mach reflection; returns a summary dict."""
-    case = inputs.double_mach(nx, ny, flux_variant=flux_variant, recon_vars=recon_vars)
+    case = inputs.double_mach(nx, ny, flux_variant=flux_variant, recon_vars=recon_vars, **kw)
     (Wp, Gp, Wd, Gd), t, n, wall, t_ctx = _timed_run(case, precision, t_end, cfl)
     xp, yp = case.node_xy(False)
     xd, _ = case.node_xy(True)
@@ -101,13 +102,14 @@ def double_mach(nx=960, ny=240, precision=fdcgks.FP64, t_end=0.2, cfl=0.4, flux_
     }
 
 
-def woodward_colella(nx=400, t_end=0.038, cfl=0.4, flux_variant=62, recon_vars=0, geno_variant=1):
+def woodward_colella(nx=400, t_end=0.038, cfl=0.4, flux_variant=62, recon_vars=0, geno_variant=1, **kw):
     """Run Sec. 5.3's interacting blast waves with the one-dimensional scheme
     (one launch: the line's own CFL steps run inside the kernel); returns a
     summary dict.  FP64.  Defaults: FD-CGKS(6-2) with App. D's GENO constants
     (with the Sec. 3.2 constants and tau_c2 = 1 the line loses positivity at
     t = 0.027)."""
-    case = inputs.woodward_colella(nx, flux_variant=flux_variant, recon_vars=recon_vars, geno_variant=geno_variant)
+    case = inputs.woodward_colella(nx, flux_variant=flux_variant, recon_vars=recon_vars, geno_variant=geno_variant,
+                                   **kw)
     W, G = inputs.line_state(case)
     with fdcgks.Lines.from_case(case) as L:
         L.set_state(W, G)
@@ -141,14 +143,17 @@ def main():
     ap.add_argument("--cfl", type=float, default=0.4)
     ap.add_argument("--flux", type=int, choices=[62, 64], default=None)
     ap.add_argument("--recon-vars", type=int, choices=[0, 1], default=None)
+    ap.add_argument("--tau-c1", type=float, default=None, help="collision time constant c1 (default: the case's)")
+    ap.add_argument("--tau-c2", type=float, default=None, help="collision time constant c2 (default: the case's)")
     ap.add_argument("--out", default=None, help="write the JSON summary here (default: stdout)")
     a = ap.parse_args()
     from . import build
     build.build()
     prec = fdcgks.MIXED if a.precision == "mixed" else fdcgks.FP64
-    opt = {k: v for k, v in (("flux_variant", a.flux), ("recon_vars", a.recon_vars)) if v is not None}
+    opt = {k: v for k, v in (("flux_variant", a.flux), ("recon_vars", a.recon_vars), ("tau_c1", a.tau_c1),
+                             ("tau_c2", a.tau_c2)) if v is not None}
     if a.case == "viscous_tube":
-        res = viscous_shock_tube(a.nx or 1000, a.ny or 500, prec, a.t_end or 1.0, a.cfl)
+        res = viscous_shock_tube(a.nx or 1000, a.ny or 500, prec, a.t_end or 1.0, a.cfl, **opt)
     elif a.case == "double_mach":
         res = double_mach(a.nx or 960, a.ny or 240, prec, a.t_end or 0.2, a.cfl, **opt)
     else:
