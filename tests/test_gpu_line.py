@@ -356,3 +356,20 @@ def test_mixed_precision_sod_and_blast_waves_to_final_time():
             assert L.check()[1] == 0 and tt[0] == pytest.approx(0.038)
             peaks[prec] = L.get_state(device=False)[0][0][0].max()
     assert peaks[fdcgks.MIXED] == pytest.approx(peaks[fdcgks.FP64], rel=0.02)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5])
+def test_tiny_periodic_lines_match_oracle(n):
+    """Degenerate periodic lines (fewer nodes than ghost layers: the ghost map
+    wraps around more than once); n = 1 is a uniform state and stays so."""
+    case = inputs.random_smooth(n, 1, seed=30 + n, amp=0.1, bc=(0, 0, 0, 0), tau_c1=0.05, tau_c2=1.0)
+    p = oracle.make_params(**case.oracle_kwargs())
+    W, G = inputs.line_state(case)
+    ref = oracle.steps_1d(p, 0.002, 3, W, G)
+    with fdcgks.Lines.from_case(case) as L:
+        L.set_state(W, G)
+        L.steps(0.002, 3)
+        gw, gg = L.get_state(device=False)
+    assert max(errs((gw[0], gg[0]), ref)) < 1e-12
+    if n == 1:
+        assert np.array_equal(gw[0], W)
