@@ -3,7 +3,7 @@
 
 Workload: the 2-D isentropic vortex on a periodic [0,10]^2 domain at 1024^2
 primary nodes (plus 1024^2 dual nodes), strength 5 at (5,5), free stream
-(1,1,1,1), gamma = 1.4, FD-CGKS(6-4), GENO (Sec. 3.2 constants), CFL 0.4.
+(1,1,1,1), gamma = 1.4, FD-CGKS(6-4), GENO (App. D constants), CFL 0.2.
 A step is one full S2O4 step (two stages) of both grids; a node update is
 one step of one primary or dual node (2 * 1024^2 per step).
 
@@ -199,7 +199,7 @@ def oracle_rate(n_sample, nsteps):
     case = inputs.vortex(n_sample)
     p = oracle.make_params(**case.oracle_kwargs())
     S = case.initial_state()
-    dt = 0.4 * case.hx / (math.sqrt(2.0) + math.sqrt(1.4)) * 0.9
+    dt = 0.2 * case.hx / (math.sqrt(2.0) + math.sqrt(1.4)) * 0.9
     warm = inputs.vortex(16)            # load the library outside the timing
     oracle.steps(oracle.make_params(**warm.oracle_kwargs()), dt, 1, *warm.initial_state())
     t0 = time.perf_counter()
@@ -219,7 +219,7 @@ def run_reference(args):
     case = inputs.vortex(ns)
     p = oracle.make_params(**case.oracle_kwargs())
     S = case.initial_state()
-    dt = 0.4 * case.hx / (math.sqrt(2.0) + math.sqrt(1.4)) * 0.9
+    dt = 0.2 * case.hx / (math.sqrt(2.0) + math.sqrt(1.4)) * 0.9
     for _ in range(args.warmup):
         S = oracle.steps(p, dt, 1, *S)
     t0 = time.perf_counter()
@@ -566,7 +566,7 @@ def main():
             continue
         with fdcgks.Solver.from_case(case, prec) as s:
             s.set_state(*S_dev)
-            dt = s.cfl_dt(0.4)
+            dt = s.cfl_dt(0.2)
             ms, pms, pn, launches, clocks = timed_steps(s, dt, args.steps, args.warmup, world, local,
                                                         sample_clocks=(name == "fp64" and rank == 0))
             out = s.get_state()
@@ -597,7 +597,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": fp["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "isentropic vortex %d^2 primary + %d^2 dual, periodic [0,10]^2, strength 5, "
-                                   "FD-CGKS(6-4), GENO, CFL 0.4" % (n, n),
+                                   "FD-CGKS(6-4), GENO (App. D constants), CFL 0.2" % (n, n),
                        "grid": [n, n], "node_updates_per_step": nodes, "parallelism": "replicas",
                        "l2": "working set %.2f GB > 129 MB L2 (no flush needed)" %
                              (nodes * 8 * (24 + 24 + 12) / 1e9 + nodes * 8 * 66 / 1e9)},
@@ -632,7 +632,7 @@ def main():
         outp = [torch.empty_like(t).pin_memory() for t in pin]
         with fdcgks.Solver.from_case(case, fdcgks.FP64) as s:
             s.set_state(*pin)
-            dt = s.cfl_dt(0.4)
+            dt = s.cfl_dt(0.2)
             for _ in range(max(1, args.warmup)):
                 s.set_state(*pin)
                 s.step(dt)

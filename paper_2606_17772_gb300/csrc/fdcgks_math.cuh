@@ -113,8 +113,22 @@ template <class R> FD_HD R rpow(R x, int r) { return r == 3 ? x * x * x : x * x;
 template <class R> struct IsF32 { static constexpr bool v = false; };
 template <> struct IsF32<float> { static constexpr bool v = true; };
 
+// FP32 rounding floor of the smoothness indicators: the indicators are
+// squares of differences of O(|Q|) values, which FP32 resolves only to about
+// u |Q| (u = 2^-24); below (64 u |Q|)^2 they measure rounding, not the data.
+// The FP32 path adds it to eps_a, so that data varying by less than about
+// 4e-6 of their magnitude count as smooth (FP64: no floor).
 template <class R>
-FD_HD R geno_chi(const GenoK<R>& g, R IS0, R IS1, R IS2) {
+FD_HD R geno_floor(R qmax) {
+  if (IsF32<R>::v) {
+    const R e = R(64.0 * 5.9604644775390625e-8) * qmax;
+    return e * e;
+  }
+  return R(0);
+}
+
+template <class R>
+FD_HD R geno_chi(const GenoK<R>& g, R IS0, R IS1, R IS2, R floor = R(0)) {
   if (g.linear) return R(1);
   R ISL = s_min(IS0, s_min(IS1, IS2));
   R ISH = s_max(IS0, s_max(IS1, IS2));
@@ -122,8 +136,9 @@ FD_HD R geno_chi(const GenoK<R>& g, R IS0, R IS1, R IS2) {
   R alpha;
   if (IsF32<R>::v) {
     // FP32: quotient form (the product form could overflow for large IS)
-    R aH = R(1) + rpow(s_div(tau, ISH + g.eps_a), g.r);
-    R aL = R(1) + rpow(s_div(tau, ISL + g.eps_a), g.r);
+    const R ea = g.eps_a + floor;
+    R aH = R(1) + rpow(s_div(tau, ISH + ea), g.r);
+    R aL = R(1) + rpow(s_div(tau, ISL + ea), g.r);
     alpha = s_div(R(2) * aH, aH + aL);
   } else {
     // alpha = 2 aH/(aH + aL), aH = 1 + (tau/h)^r, aL = 1 + (tau/l)^r, written
@@ -171,6 +186,7 @@ FD_HD void recon_interface(const GenoK<R>& g, const R Q[4], const R Qx[4], R h, 
   // shared high-order derivative (identical for left and right)
   R PHx = -((Q[0] + R(45) * Q[1] - R(45) * Q[2] - Q[3]) * ih + R(9) * (Qx[1] + Qx[2])) * c30;
   R dq12 = (Q[2] - Q[1]) * ih;    // q2x = q3x (left), q2x = q3x (right)
+  const R fl = geno_floor(s_max(s_max(s_abs(Q[0]), s_abs(Q[1])), s_max(s_abs(Q[2]), s_abs(Q[3]))));
   // ---- left state (App. C1) ----
   {
     R PH = ((R(7) * Q[0] + R(35) * Q[1] + R(21) * Q[2] + Q[3]) + (Qx[0] + R(22) * Qx[1] - R(7) * Qx[2]) * h) * c64;
@@ -187,7 +203,7 @@ FD_HD void recon_interface(const GenoK<R>& g, const R Q[4], const R Qx[4], R h, 
     t = Q[1] - R(2) * Q[2] + Q[3];
     u = R(3) * Q[1] - R(4) * Q[2] + Q[3];
     R IS2 = R(13.0 / 12.0) * t * t + R(0.25) * u * u;
-    R chi = geno_chi(g, IS0, IS1, IS2);
+    R chi = geno_chi(g, IS0, IS1, IS2, fl);
     chil = chi;
     if (chi == R(1)) {
       vl = PH;
@@ -217,7 +233,7 @@ FD_HD void recon_interface(const GenoK<R>& g, const R Q[4], const R Qx[4], R h, 
     t = Q[0] - R(2) * Q[1] + Q[2];
     u = R(3) * Q[2] - R(4) * Q[1] + Q[0];
     R IS2 = R(13.0 / 12.0) * t * t + R(0.25) * u * u;
-    R chi = geno_chi(g, IS0, IS1, IS2);
+    R chi = geno_chi(g, IS0, IS1, IS2, fl);
     chir = chi;
     if (chi == R(1)) {
       vr = PH;
@@ -250,7 +266,7 @@ FD_HD R recon_node(const GenoK<R>& g, const R Q[3], const R Qx[3], R h, R ih) {
   t = Q[2] - Q[1] - Qx[2] * h;
   u = R(2) * (Q[2] - Q[1]) - Qx[2] * h;
   R IS2 = R(13.0 / 3.0) * t * t + u * u;
-  R chi = geno_chi(g, IS0, IS1, IS2);
+  R chi = geno_chi(g, IS0, IS1, IS2, geno_floor(s_max(s_abs(Q[1]), s_max(s_abs(Q[0]), s_abs(Q[2])))));
   if (chi == R(1)) return PHx;
   R w[3];
   geno_weights(g, g.d_node, IS0, IS1, IS2, w);

@@ -10,10 +10,13 @@ JSON summary:
   * double Mach reflection (Sec. 5.5) to t = 0.2: density extrema and the
     density on the wall and along y = 0.5 (the figure is a contour plot);
   * Woodward-Colella blast waves (Sec. 5.3) to t = 0.038 with the
-    one-dimensional scheme: density and pressure along the tube.
+    one-dimensional scheme: density and pressure along the tube;
+  * the isentropic vortex once around the periodic box on 128^2 ... 1024^2:
+    errors against the exact solution and the observed order.
 
     python -m paper_2606_17772_gb300.runs --case viscous_tube --nx 1000 --ny 500 --precision mixed
     python -m paper_2606_17772_gb300.runs --case double_mach --nx 960 --ny 240 --precision fp64
+    python -m paper_2606_17772_gb300.runs --case vortex_convergence
 """
 import argparse
 import json
@@ -70,6 +73,43 @@ def viscous_shock_tube(nx=1000, ny=500, precision=fdcgks.MIXED, t_end=1.0, cfl=0
         "x_wall": xd[0].tolist(), "rho_wall": rho_wall.tolist(),
         "x_line": xp[0].tolist(), "rho_y0075": rho_line.tolist(),
     }
+
+
+def vortex_convergence(ns=(128, 256, 512, 1024), precisions=(fdcgks.FP64, fdcgks.MIXED), t_end=10.0, cfl=0.2,
+                       **kw):
+    """The isentropic vortex (strength 5, free stream (1, 1, 1, 1)) advected once
+    around the periodic [0, 10]^2 box (t = 10: the exact solution is the
+    initial state) on each grid: L1 error of the density against the exact
+    solution (mean absolute error over the primary nodes, and the same
+    integral over the domain), the observed order between successive grids,
+    and for the mixed path the L1 difference from the FP64 run."""
+    out = {"case": "isentropic vortex, [0,10]^2 periodic, strength 5, to t = %g, CFL %.2f, %s" % (
+        t_end, cfl, json.dumps(kw)), "grids": []}
+    prev = {}
+    for n in ns:
+        case = inputs.vortex(n, **kw)
+        S0 = case.initial_state()
+        exact = S0[0][0]
+        row = {"n": n}
+        rho = {}
+        for prec in precisions:
+            name = "mixed" if prec == fdcgks.MIXED else "fp64"
+            with fdcgks.Solver.from_case(case, prec) as s:
+                s.set_state(*S0)
+                w0 = time.perf_counter()
+                t, k = advance(s, t_end, cfl)
+                wall = time.perf_counter() - w0
+                rho[name] = s.get_state(device=False)[0][0]
+            err = np.abs(rho[name] - exact)
+            row[name] = {"steps": k, "wall_seconds": wall, "L1_mean": float(err.mean()),
+                         "L1_integral": float(err.sum() * case.hx * case.hy), "Linf": float(err.max())}
+            if name in prev:
+                row[name]["order_L1"] = float(np.log2(prev[name] / err.mean()))
+            prev[name] = err.mean()
+        if "fp64" in rho and "mixed" in rho:
+            row["mixed_vs_fp64_L1_mean"] = float(np.abs(rho["mixed"] - rho["fp64"]).mean())
+        out["grids"].append(row)
+    return out
 
 
 def _timed_run(case, precision, t_end, cfl):
@@ -135,7 +175,8 @@ def woodward_colella(nx=400, t_end=0.038, cfl=0.4, flux_variant=62, recon_vars=0
 
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
-    ap.add_argument("--case", choices=["viscous_tube", "double_mach", "woodward_colella"], default="viscous_tube")
+    ap.add_argument("--case", choices=["viscous_tube", "double_mach", "woodward_colella", "vortex_convergence"],
+                    default="viscous_tube")
     ap.add_argument("--nx", type=int, default=None)
     ap.add_argument("--ny", type=int, default=None)
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
@@ -152,7 +193,9 @@ def main():
     prec = fdcgks.MIXED if a.precision == "mixed" else fdcgks.FP64
     opt = {k: v for k, v in (("flux_variant", a.flux), ("recon_vars", a.recon_vars), ("tau_c1", a.tau_c1),
                              ("tau_c2", a.tau_c2)) if v is not None}
-    if a.case == "viscous_tube":
+    if a.case == "vortex_convergence":
+        res = vortex_convergence(t_end=a.t_end or 10.0, cfl=a.cfl if a.cfl != 0.4 else 0.2, **opt)
+    elif a.case == "viscous_tube":
         res = viscous_shock_tube(a.nx or 1000, a.ny or 500, prec, a.t_end or 1.0, a.cfl, **opt)
     elif a.case == "double_mach":
         res = double_mach(a.nx or 960, a.ny or 240, prec, a.t_end or 0.2, a.cfl, **opt)
