@@ -124,7 +124,10 @@ fdcgks_status fdcgks_steps(fdcgks_t ctx, double dt, int nsteps);
 
 /* CFL time step (Sec. 5): cfl * min over all nodes of both grids of
  * min(hx/(|U|+c), hy/(|V|+c)); with mu > 0 also bounded by
- * cfl * min(hx,hy)^2 / (8 nu_max), nu = mu/rho.  Synchronizes the stream. */
+ * cfl * min(hx,hy)^2 / (8 nu_max), nu = mu/rho.  Synchronizes the stream.
+ * The bound is per direction: for smooth flow oblique to the grid, cfl 0.4
+ * lets the scheme's grid-scale diagonal modes grow slowly (visible over
+ * thousands of steps, first in mixed precision); cfl 0.2 is stable. */
 fdcgks_status fdcgks_cfl_dt(fdcgks_t ctx, double cfl, double* dt_out);
 
 /* Read and clear the device non-physical flag (synchronizes the stream).
