@@ -373,3 +373,4 @@ def test_tiny_periodic_lines_match_oracle(n):
     assert max(errs((gw[0], gg[0]), ref)) < 1e-12
     if n == 1:
         assert np.array_equal(gw[0], W)
+

@@ -156,3 +156,24 @@ def test_adjoint_refuses_split_sides():
         with pytest.raises(fdcgks.FdcgksError) as e:
             s.vjp_steps(0.001, 1, S, S)
         assert e.value.status == 1
+
+
+@pytest.mark.parametrize("precision", [fdcgks.FP64, fdcgks.MIXED])
+def test_double_mach_runs_to_final_time(precision):
+    """The double Mach reflection with its run settings (FD-CGKS(6-2),
+    characteristic reconstruction, tau c1 = 0.05, c2 = 25) at 240 x 60 runs to
+    t = 0.2 with CFL-0.4 steps and stays physical; the split top boundary's
+    clock ends at the final time; the reflected shock compresses the gas well
+    beyond the post-shock density 8."""
+    from paper_2606_17772_gb300 import runs
+    case = inputs.double_mach(240, 60, flux_variant=62, recon_vars=1)
+    with fdcgks.Solver.from_case(case, precision) as s:
+        s.set_state(*case.initial_state())
+        t, n = runs.advance(s, 0.2, 0.4)
+        assert abs(s.get_time() - t) <= 1e-12
+        Wp, _, Wd, _ = s.get_state(device=False)
+    assert t == pytest.approx(0.2) and n > 100
+    for W in (Wp, Wd):
+        p = 0.4 * (W[3] - 0.5 * (W[1] ** 2 + W[2] ** 2) / W[0])
+        assert np.isfinite(W).all() and W[0].min() > 1.0 and p.min() > 0.5
+    assert 12.0 < Wp[0].max() < 30.0
