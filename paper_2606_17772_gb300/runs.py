@@ -65,8 +65,9 @@ def viscous_shock_tube(nx=1000, ny=500, precision=fdcgks.MIXED, t_end=1.0, cfl=0
     w = (0.075 - yrow[k]) / (yrow[k + 1] - yrow[k])
     rho_line = (1 - w) * Wp[0, k] + w * Wp[0, k + 1]
     return {
-        "case": "viscous shock tube, Re 200 (mu 0.005), Pr %.2f, %d x %d, %s, CFL %.2f, tau c1 %g c2 %g" % (
-            case.Pr, nx, ny, "mixed" if precision == fdcgks.MIXED else "fp64", cfl, case.tau_c1, case.tau_c2),
+        "case": "viscous shock tube, Re 200 (mu 0.005), Pr %.2f, %d x %d, %s, CFL %.2f, tau c1 %g c2 %g, GENO %d" % (
+            case.Pr, nx, ny, "mixed" if precision == fdcgks.MIXED else "fp64", cfl, case.tau_c1, case.tau_c2,
+            case.geno_variant),
         "t": t, "steps": n, "wall_seconds": wall,
         "node_updates_per_s": n * (nx * ny + case.nxd * case.nyd) / wall,
         "rho_min": float(min(Wp[0].min(), Wd[0].min())), "rho_max": float(max(Wp[0].max(), Wd[0].max())),
@@ -184,6 +185,8 @@ def main():
     ap.add_argument("--cfl", type=float, default=0.4)
     ap.add_argument("--flux", type=int, choices=[62, 64], default=None)
     ap.add_argument("--recon-vars", type=int, choices=[0, 1], default=None)
+    ap.add_argument("--geno", type=int, choices=[0, 1, 2], default=None,
+                    help="GENO constants: 0 Sec. 3.2 text, 1 App. D, 2 linear (default: the case's)")
     ap.add_argument("--tau-c1", type=float, default=None, help="collision time constant c1 (default: the case's)")
     ap.add_argument("--tau-c2", type=float, default=None, help="collision time constant c2 (default: the case's)")
     ap.add_argument("--out", default=None, help="write the JSON summary here (default: stdout)")
@@ -192,7 +195,7 @@ def main():
     build.build()
     prec = fdcgks.MIXED if a.precision == "mixed" else fdcgks.FP64
     opt = {k: v for k, v in (("flux_variant", a.flux), ("recon_vars", a.recon_vars), ("tau_c1", a.tau_c1),
-                             ("tau_c2", a.tau_c2)) if v is not None}
+                             ("tau_c2", a.tau_c2), ("geno_variant", a.geno)) if v is not None}
     if a.case == "vortex_convergence":
         res = vortex_convergence(t_end=a.t_end or 10.0, cfl=a.cfl if a.cfl != 0.4 else 0.2, **opt)
     elif a.case == "viscous_tube":
