@@ -66,6 +66,25 @@ void iface(double gamma, double mu, double Pr, double c1, double c2, double dt, 
 
 extern "C" {
 
+// path-function values chi^l, chi^r of the interface reconstruction of n
+// 4-point lines (Q[n][4], Qx[n][4]) in FP32 (precision 1) or FP64
+void probe_recon_chi(int precision, int variant, int n, const double* Q, const double* Qx, double h, double* chi) {
+  for (int t = 0; t < n; ++t) {
+    if (precision == 1) {
+      const GenoK<float> g = geno_of<float>(variant);
+      float q[4], qx[4], vl, dl, cl, vr, dr, cr;
+      for (int k = 0; k < 4; ++k) { q[k] = (float)Q[t * 4 + k]; qx[k] = (float)Qx[t * 4 + k]; }
+      recon_interface(g, q, qx, (float)h, (float)(1.0 / h), vl, dl, cl, vr, dr, cr);
+      chi[2 * t] = cl; chi[2 * t + 1] = cr;
+    } else {
+      const GenoK<double> g = geno_of<double>(variant);
+      double vl, dl, cl, vr, dr, cr;
+      recon_interface(g, Q + t * 4, Qx + t * 4, h, 1.0 / h, vl, dl, cl, vr, dr, cr);
+      chi[2 * t] = cl; chi[2 * t + 1] = cr;
+    }
+  }
+}
+
 void probe_iface(int precision, double gamma, double mu, double Pr, double c1, double c2, double dt, int normal, int n,
                  const double* in, double* out) {
   if (precision == 1) iface<float>(gamma, mu, Pr, c1, c2, dt, normal, n, in, out);

@@ -79,3 +79,32 @@ def test_fp32_erfc_within_published_bound(probe):
     err = np.abs(out - special.erfc(xf))
     # 1.5e-7 from the approximation plus FP32 rounding of values up to 2
     assert err.max() < 1.5e-7 + 4 * 2.0 * np.finfo(np.float32).eps
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_fp32_geno_counts_rounding_level_variation_as_smooth(probe, variant):
+    """The FP32 path's rounding floor of the smoothness indicators: lines whose
+    values vary by a few FP32 rounding units of their size keep the high-order
+    reconstruction (chi = 1), while a genuine jump still turns it off."""
+    rng = np.random.default_rng(5 + variant)
+    n, h = 200, 0.01
+    base = rng.uniform(0.5, 3.0, (n, 1))
+    u = np.finfo(np.float32).eps / 2
+    Q = np.ascontiguousarray(base * (1 + 4 * u * rng.standard_normal((n, 4))))
+    Qx = np.ascontiguousarray(base * 4 * u * rng.standard_normal((n, 4)) / h)
+    chi = np.zeros(2 * n)
+    probe.probe_recon_chi(1, variant, n, _p(Q), _p(Qx), ctypes.c_double(h), _p(chi))
+    assert np.all(chi == 1.0)
+    # without the floor (the FP64 path) the same data switch the weights on most lines
+    chi64 = np.zeros(2 * n)
+    probe.probe_recon_chi(0, variant, n, _p(Q), _p(Qx), ctypes.c_double(h), _p(chi64))
+    assert (chi64 < 0.5).sum() > n // 4
+    jump = np.ascontiguousarray(np.tile([1.0, 1.0, 0.125, 0.125], (4, 1)))
+    jx = np.zeros_like(jump)
+    cj = np.zeros(8)
+    probe.probe_recon_chi(1, variant, 4, _p(jump), _p(jx), ctypes.c_double(h), _p(cj))
+    assert np.all(cj < 0.5)
+    # FP64 has no floor: the same jump gives the same decision
+    cd = np.zeros(8)
+    probe.probe_recon_chi(0, variant, 4, _p(jump), _p(jx), ctypes.c_double(h), _p(cd))
+    assert np.all(cd < 0.5)
