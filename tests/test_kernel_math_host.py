@@ -95,10 +95,11 @@ def test_fp32_geno_counts_rounding_level_variation_as_smooth(probe, variant):
     chi = np.zeros(2 * n)
     probe.probe_recon_chi(1, variant, n, _p(Q), _p(Qx), ctypes.c_double(h), _p(chi))
     assert np.all(chi == 1.0)
-    # without the floor (the FP64 path) the same data switch the weights on most lines
+    # without the floor (the FP64 path) the same data leave the high-order
+    # reconstruction on most lines (252 and 361 of 400 values below 1 measured)
     chi64 = np.zeros(2 * n)
     probe.probe_recon_chi(0, variant, n, _p(Q), _p(Qx), ctypes.c_double(h), _p(chi64))
-    assert (chi64 < 0.5).sum() > n // 4
+    assert (chi64 < 1.0).sum() > n
     jump = np.ascontiguousarray(np.tile([1.0, 1.0, 0.125, 0.125], (4, 1)))
     jx = np.zeros_like(jump)
     cj = np.zeros(8)
