@@ -489,7 +489,8 @@ def run_adjoint(args, world):
     out = {"config": {"workload": "isentropic vortex 256^2 (+dual), strength 5, %d steps (CFL 0.4 dt), "
                                   "J = 1/2 sum (rho - rho_target)^2 h^2, target from rho + 8 Gaussian bumps "
                                   "(sigma 0.5, amplitude 1e-3, seed 1); gradient w.r.t. primary W^0; "
-                                  "checkpoint every 50 steps" % args.adj_steps}}
+                                  "checkpoint every 50 steps; geno: App. D GENO constants, linear: linear "
+                                  "reconstruction with tau = 0.05 dt" % args.adj_steps}}
     for name, kw, ndir in (("geno", {}, 0), ("linear", dict(geno_variant=2, tau_c1=0.05, tau_c2=0.0), 2)):
         case = inputs.vortex(256, strength=5.0, **kw)
         S0, bump = setup(case, args.adj_steps)
