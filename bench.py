@@ -268,7 +268,7 @@ def timed_steps(solver, dt, steps, warmup, world, device_index, sample_clocks):
 def run_ensemble(args, world, rank, local):
     """Batched ensemble workload: seeded periodic isentropic vortices on uneven
     grids (N log-uniform in [32, 512], strength U[1, 5], centre uniform),
-    mixed precision, every member taking its own CFL-0.4 step each step,
+    mixed precision, every member taking its own CFL-0.2 step each step,
     one CUDA-graph step per launch, tile shapes from the autotuner."""
     import numpy as np
     import torch
@@ -281,9 +281,9 @@ def run_ensemble(args, world, rank, local):
         if args.ens_no_tune:
             cfg, tune_ms = ens.get_tiles(), None
         else:
-            cfg, tune_ms = ens.tune(cfl=0.4, trial_steps=3)
+            cfg, tune_ms = ens.tune(cfl=0.2, trial_steps=3)
         tune_s = time.perf_counter() - t0
-        ens.run(args.warmup, cfl=0.4)
+        ens.run(args.warmup, cfl=0.2)
         stream = torch.cuda.ExternalStream(ens.stream)
         sampler = ClockSampler(local) if rank == 0 else None
         if sampler:
@@ -294,7 +294,7 @@ def run_ensemble(args, world, rank, local):
         launches0 = ens.launches()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        ens.run(args.ens_steps, cfl=0.4)
+        ens.run(args.ens_steps, cfl=0.2)
         e1.record(stream)
         e1.synchronize()
         barrier(world)
@@ -302,12 +302,12 @@ def run_ensemble(args, world, rank, local):
         ms = max_over_ranks(e0.elapsed_time(e1), world)
         launches = ens.launches() - launches0
         t, _, st = ens.status()
-        phases = ens.profile(3, cfl=0.4)
+        phases = ens.profile(3, cfl=0.2)
         nodes = ens.nodes
         # roofline of the point phase: FP32 flops of the interior points of
         # every member (counts of the largest member's state, the same per point)
         big = max(range(len(cases)), key=lambda m: cases[m].nx)
-        cnt = flops.step_counts(cases[big], cases[big].initial_state(), 0.4 * cases[big].hx / 3.0, precision=1)
+        cnt = flops.step_counts(cases[big], cases[big].initial_state(), 0.2 * cases[big].hx / 3.0, precision=1)
         npts = sum(c.nx * c.ny for c in cases)
         pt_flops = 2 * npts * (cnt["point_stage1"]["fp32"] + cnt["point_stage2"]["fp32"])
         pt_ms = phases["points"] / 3
@@ -317,7 +317,7 @@ def run_ensemble(args, world, rank, local):
         "value": nodes * args.ens_steps * world / (ms / 1e3), "unit": UNIT, "dtype": "f32+f64",
         "ms_per_step": ms / args.ens_steps, "steps": args.ens_steps, "warmup": args.warmup,
         "config": {"workload": "%d periodic isentropic vortices on [0,10]^2, N log-uniform in [32, %d] "
-                               "(seed 0; N from %d to %d), strength U[1,5], centre uniform; own CFL-0.4 dt "
+                               "(seed 0; N from %d to %d), strength U[1,5], centre uniform; own CFL-0.2 dt "
                                "per member per step, computed on the device" % (len(cases), args.ens_nmax,
                                                                                  sizes[0], sizes[-1]),
                    "members": len(cases), "node_updates_per_step": nodes, "tiles": cfg,
@@ -486,7 +486,7 @@ def run_adjoint(args, world):
             bump += np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (2 * 0.5 ** 2))
         return S0, bump
 
-    out = {"config": {"workload": "isentropic vortex 256^2 (+dual), strength 5, %d steps (CFL 0.4 dt), "
+    out = {"config": {"workload": "isentropic vortex 256^2 (+dual), strength 5, %d steps (CFL 0.2 dt), "
                                   "J = 1/2 sum (rho - rho_target)^2 h^2, target from rho + 8 Gaussian bumps "
                                   "(sigma 0.5, amplitude 1e-3, seed 1); gradient w.r.t. primary W^0; "
                                   "checkpoint every 50 steps; geno: App. D GENO constants, linear: linear "
@@ -498,7 +498,7 @@ def run_adjoint(args, world):
         n = args.adj_steps
         with fdcgks.Solver.from_case(case) as s:
             s.set_state(*S0)
-            dt = s.cfl_dt(0.4)
+            dt = s.cfl_dt(0.2)
             Wt = S0[0].clone()
             Wt[0] += torch.from_numpy(1e-3 * bump).cuda()
             s.set_state(Wt, *S0[1:])
