@@ -510,6 +510,7 @@ def run_adjoint(args, world):
                 s.steps(dt, n)
                 return 0.5 * float(((s.get_state()[0][0] - target) ** 2).sum()) * h2
 
+            J(S0[0])                                   # warm-up (first launches, allocations)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             J0 = J(S0[0])
@@ -518,6 +519,7 @@ def run_adjoint(args, world):
             fin = s.get_state()
             seed = [torch.zeros_like(t) for t in S0]
             seed[0][0] = (fin[0][0] - target) * h2
+            s.vjp_steps(dt, 1, S0, seed, checkpoint_every=50)   # warm-up of the adjoint kernels
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             g = s.vjp_steps(dt, n, S0, seed, checkpoint_every=50)
