@@ -446,9 +446,12 @@ def run_lines(args, world):
                                                ("sod", inputs.sod_strip(100, 1), 0.2, 1, 0, FP64),
                                                ("lax", inputs.lax_strip(100, 1), 0.16, 1, 0, FP64)):
         W, G = inputs.line_state(case)
+        Wb = np.ascontiguousarray(np.broadcast_to(W, (batch,) + W.shape))
+        Gb = np.ascontiguousarray(np.broadcast_to(G, (batch,) + G.shape))
         with fdcgks.Lines.from_case(case, batch, cluster=cs, precision=prec) as L:
-            L.set_state(np.ascontiguousarray(np.broadcast_to(W, (batch,) + W.shape)),
-                        np.ascontiguousarray(np.broadcast_to(G, (batch,) + G.shape)))
+            L.set_state(Wb, Gb)
+            L.steps(1e-9, 1)                           # warm-up: the kernel's first launch
+            L.set_state(Wb, Gb)                        # back to t = 0
             torch.cuda.synchronize()
             barrier(world)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
