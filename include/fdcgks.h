@@ -130,6 +130,12 @@ fdcgks_status fdcgks_steps(fdcgks_t ctx, double dt, int nsteps);
  * thousands of steps, first in mixed precision); cfl 0.2 is stable. */
 fdcgks_status fdcgks_cfl_dt(fdcgks_t ctx, double cfl, double* dt_out);
 
+/* The two-dimensional form of the same bound: cfl / max over all nodes of
+ * both grids of ((|U|+c)/hx + (|V|+c)/hy), with the same viscous bound.  At
+ * most the per-direction step, half of it for flow at 45 degrees; cfl 0.4 in
+ * this form is stable for smooth oblique flow.  Synchronizes the stream. */
+fdcgks_status fdcgks_cfl_dt_sum(fdcgks_t ctx, double cfl, double* dt_out);
+
 /* Read and clear the device non-physical flag (synchronizes the stream).
  * *nonphysical = 1 if a step produced non-positive/non-finite rho or p. */
 fdcgks_status fdcgks_check(fdcgks_t ctx, int* nonphysical);

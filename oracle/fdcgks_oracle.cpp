@@ -1505,6 +1505,32 @@ double oracle_cfl_dt(const oracle_params* p, double cfl, const double* Wp, const
   return dt;
 }
 
+// the two-dimensional form of the CFL bound: CFL / max((|U|+c)/hx + (|V|+c)/hy)
+// over both grids, with the same viscous bound
+double oracle_cfl_dt_sum(const oracle_params* p, double cfl, const double* Wp, const double* Wd) {
+  Scheme S;
+  if (!make_scheme(p, S)) return -1.0;
+  double rate = 0.0, numax = 0.0;
+  const double* arrs[2] = {Wp, Wd};
+  int nxs[2] = {p->nx, S.nxd}, nys[2] = {p->ny, S.nyd};
+  for (int g = 0; g < 2; ++g) {
+    size_t NN = (size_t)nxs[g] * nys[g];
+    for (size_t n = 0; n < NN; ++n) {
+      double rho = arrs[g][n], U = arrs[g][NN + n] / rho, V = arrs[g][2 * NN + n] / rho;
+      double pr = (p->gamma - 1.0) * (arrs[g][3 * NN + n] - 0.5 * rho * (U * U + V * V));
+      double c = std::sqrt(p->gamma * pr / rho);
+      rate = std::fmax(rate, (std::fabs(U) + c) / S.hx + (std::fabs(V) + c) / S.hy);
+      numax = std::fmax(numax, p->mu / rho);
+    }
+  }
+  double dt = cfl / rate;
+  if (numax > 0.0) {
+    double h = std::fmin(S.hx, S.hy);
+    dt = std::fmin(dt, cfl * h * h / (8.0 * numax));
+  }
+  return dt;
+}
+
 // ---- component-level entry points for the pins ----
 
 double oracle_maxwell_moment(double rho, double U, double V, double lam, double K, int a, int b, int c,

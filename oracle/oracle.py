@@ -45,6 +45,7 @@ def lib():
         _lib.oracle_maxwell_moment.restype = ctypes.c_double
         _lib.oracle_compact_flux.restype = ctypes.c_double
         _lib.oracle_cfl_dt_1d.restype = ctypes.c_double
+        _lib.oracle_cfl_dt_sum.restype = ctypes.c_double
     return _lib
 
 
@@ -129,6 +130,11 @@ def stage_1d(p, dt, W, Gx):
     if rc != 0:
         raise ValueError("oracle_stage_1d failed")
     return out
+
+
+def cfl_dt_sum(p, cfl, Wp, Wd):
+    """The two-dimensional form of the CFL bound (rates of the directions added)."""
+    return lib().oracle_cfl_dt_sum(ctypes.byref(p), ctypes.c_double(cfl), _ptr(_arr(Wp)), _ptr(_arr(Wd)))
 
 
 def cfl_dt_1d(p, cfl, W):

@@ -229,7 +229,20 @@ cudaError_t fdk::launch_validate(const double* S, const Layout& L, double gamma,
 }
 
 // per-block maxima of (|U|+c)/hx, (|V|+c)/hy (as one rate) and nu = mu/rho
-__global__ void cfl_kernel(const double* S, Layout L, double gamma, double mu, double ihx, double ihy, double* out) {
+// the rates of cfl_rates added over the directions, (|U|+c)/hx + (|V|+c)/hy
+// (the two-dimensional form of the CFL bound)
+__device__ void cfl_rates_sum(double r, double ru, double rv, double E, double gamma, double mu, double ihx,
+                              double ihy, double& rate, double& numax) {
+  const double ir = 1.0 / r;
+  const double U = ru * ir, V = rv * ir;
+  const double p = (gamma - 1.0) * (E - 0.5 * r * (U * U + V * V));
+  const double cs = sqrt(gamma * p * ir);
+  rate = fmax(rate, (fabs(U) + cs) * ihx + (fabs(V) + cs) * ihy);
+  numax = fmax(numax, mu * ir);
+}
+
+__global__ void cfl_kernel(const double* S, Layout L, double gamma, double mu, double ihx, double ihy, int sum,
+                           double* out) {
   double rate = 0.0, numax = 0.0;
   const long n0 = (long)L.nx * L.ny, n1 = (long)L.nxd * L.nyd;
   for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n0 + n1; t += (long)gridDim.x * blockDim.x) {
@@ -239,8 +252,12 @@ __global__ void cfl_kernel(const double* S, Layout L, double gamma, double mu, d
     int i = (int)(q % nxg), j = (int)(q / nxg);
     const double* Sg = S + (long)g * NFLD * L.plane;
     const long c0 = cell(L, i, j);
-    cfl_rates(Sg[c0], Sg[L.plane + c0], Sg[2 * L.plane + c0], Sg[3 * L.plane + c0], gamma, mu, ihx, ihy, rate,
-              numax);
+    if (sum)
+      cfl_rates_sum(Sg[c0], Sg[L.plane + c0], Sg[2 * L.plane + c0], Sg[3 * L.plane + c0], gamma, mu, ihx, ihy, rate,
+                    numax);
+    else
+      cfl_rates(Sg[c0], Sg[L.plane + c0], Sg[2 * L.plane + c0], Sg[3 * L.plane + c0], gamma, mu, ihx, ihy, rate,
+                numax);
   }
   // warp-shuffle max, then across warps in shared memory
   for (int o = 16; o > 0; o >>= 1) {
@@ -569,12 +586,13 @@ fdcgks_status fdcgks_check(fdcgks_t c, int* nonphysical) {
   return FDCGKS_OK;
 }
 
-fdcgks_status fdcgks_cfl_dt(fdcgks_t c, double cfl, double* dt_out) {
+static fdcgks_status cfl_dt_impl(fdcgks_t c, double cfl, int sum, double* dt_out) {
   if (!c || !dt_out) return fail(c, FDCGKS_ERR_ARG, "NULL argument");
   if (!c->has_state) return fail(c, FDCGKS_ERR_STATE, "no state loaded");
   if (!(cfl > 0.0) || !std::isfinite(cfl)) return fail(c, FDCGKS_ERR_ARG, "cfl must be positive and finite");
   CUDA_TRY(c, join_state(c));
-  cfl_kernel<<<c->red_blocks, 256, 0, c->stream>>>(c->S, c->L, c->p.gamma, c->p.mu, 1.0 / c->hx, 1.0 / c->hy, c->red);
+  cfl_kernel<<<c->red_blocks, 256, 0, c->stream>>>(c->S, c->L, c->p.gamma, c->p.mu, 1.0 / c->hx, 1.0 / c->hy, sum,
+                                                   c->red);
   CUDA_TRY(c, cudaGetLastError());
   double* h = new double[2 * c->red_blocks];
   cudaError_t e = cudaMemcpyAsync(h, c->red, sizeof(double) * 2 * c->red_blocks, cudaMemcpyDeviceToHost, c->stream);
@@ -598,6 +616,10 @@ fdcgks_status fdcgks_cfl_dt(fdcgks_t c, double cfl, double* dt_out) {
   *dt_out = dt;
   return FDCGKS_OK;
 }
+
+fdcgks_status fdcgks_cfl_dt(fdcgks_t c, double cfl, double* dt_out) { return cfl_dt_impl(c, cfl, 0, dt_out); }
+
+fdcgks_status fdcgks_cfl_dt_sum(fdcgks_t c, double cfl, double* dt_out) { return cfl_dt_impl(c, cfl, 1, dt_out); }
 
 fdcgks_status fdcgks_stage_operator(fdcgks_t c, double dt, double* Lp, double* Ltp, double* gbp, double* gtp,
                                     double* Ld, double* Ltd, double* gbd, double* gtd) {

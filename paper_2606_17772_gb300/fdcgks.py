@@ -19,7 +19,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "non-physical stat
           5: "device wait timed out", 6: "out of device memory"}
 
 EXPORTS = ["fdcgks_create", "fdcgks_destroy", "fdcgks_dims", "fdcgks_set_state", "fdcgks_get_state",
-           "fdcgks_step", "fdcgks_steps", "fdcgks_cfl_dt", "fdcgks_check", "fdcgks_stage_operator",
+           "fdcgks_step", "fdcgks_steps", "fdcgks_cfl_dt", "fdcgks_cfl_dt_sum", "fdcgks_check", "fdcgks_stage_operator",
            "fdcgks_iface_batch", "fdcgks_nodal_batch", "fdcgks_recon_batch", "fdcgks_last_error",
            "fdcgks_status_string", "fdcgks_set_profiling", "fdcgks_get_profile", "fdcgks_cfl_dt_noalloc",
            "fdcgks_ens_create", "fdcgks_ens_destroy", "fdcgks_ens_set_state", "fdcgks_ens_get_state",
@@ -146,6 +146,7 @@ def load(path=None):
     lib.fdcgks_step.argtypes = [_VP, ctypes.c_double]
     lib.fdcgks_steps.argtypes = [_VP, ctypes.c_double, ctypes.c_int]
     lib.fdcgks_cfl_dt.argtypes = [_VP, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    lib.fdcgks_cfl_dt_sum.argtypes = [_VP, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
     lib.fdcgks_check.argtypes = [_VP, ctypes.POINTER(ctypes.c_int)]
     lib.fdcgks_stage_operator.argtypes = [_VP, ctypes.c_double] + [_VP] * 8
     lib.fdcgks_iface_batch.argtypes = [ctypes.POINTER(Params), ctypes.c_int, ctypes.c_double, ctypes.c_int, _VP, _VP]
@@ -191,7 +192,8 @@ def load(path=None):
     lib.fdcgks_status_string.argtypes = [ctypes.c_int]
     lib.fdcgks_status_string.restype = ctypes.c_char_p
     for name in ("fdcgks_create", "fdcgks_dims", "fdcgks_set_state", "fdcgks_get_state", "fdcgks_step",
-                 "fdcgks_steps", "fdcgks_cfl_dt", "fdcgks_check", "fdcgks_stage_operator", "fdcgks_iface_batch",
+                 "fdcgks_steps", "fdcgks_cfl_dt", "fdcgks_cfl_dt_sum", "fdcgks_check", "fdcgks_stage_operator",
+                 "fdcgks_iface_batch",
                  "fdcgks_nodal_batch", "fdcgks_recon_batch", "fdcgks_set_profiling", "fdcgks_get_profile",
                  "fdcgks_cfl_dt_noalloc", "fdcgks_ens_create", "fdcgks_ens_set_state", "fdcgks_ens_get_state",
                  "fdcgks_ens_run", "fdcgks_ens_status", "fdcgks_ens_set_tiles", "fdcgks_ens_get_tiles",
@@ -350,9 +352,11 @@ class Solver:
     def steps(self, dt, n):
         _check(load().fdcgks_steps(self._h, ctypes.c_double(dt), int(n)), self._h)
 
-    def cfl_dt(self, cfl):
+    def cfl_dt(self, cfl, form="direction"):
+        """CFL time step: form "direction" (fdcgks_cfl_dt) or "sum" (fdcgks_cfl_dt_sum)."""
         out = ctypes.c_double()
-        _check(load().fdcgks_cfl_dt(self._h, ctypes.c_double(cfl), ctypes.byref(out)), self._h)
+        fn = load().fdcgks_cfl_dt_sum if form == "sum" else load().fdcgks_cfl_dt
+        _check(fn(self._h, ctypes.c_double(cfl), ctypes.byref(out)), self._h)
         return out.value
 
     def check(self):

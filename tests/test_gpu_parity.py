@@ -215,6 +215,17 @@ def test_strong_shock_steps_match_oracle(name):
     assert errs[worst] < max(1e-10, 100 * spread), (worst, errs[worst], spread)
 
 
+def test_cfl_dt_sum_matches_oracle():
+    for case in (inputs.vortex(32), inputs.viscous_shock_tube(40, 20), inputs.random_smooth(20, 13, seed=2, amp=0.2)):
+        S = case.initial_state()
+        ref = oracle.cfl_dt_sum(oracle.make_params(**case.oracle_kwargs()), 0.4, S[0], S[2])
+        with fdcgks.Solver.from_case(case) as s:
+            s.set_state(*S)
+            got = s.cfl_dt(0.4, form="sum")
+            assert got <= s.cfl_dt(0.4)
+        assert got == pytest.approx(ref, rel=1e-14)
+
+
 def test_cfl_dt_matches_oracle():
     for case, cfl in ((inputs.vortex(32), 0.4), (inputs.viscous_shock_tube(40, 20), 0.3)):
         S = case.initial_state()

@@ -304,3 +304,22 @@ def test_viscous_shear_wave_decay():
     amp = (out[0][2, 0] / out[0][0, 0] * np.sin(k * X[0])).sum() * 2 / n
     rate = -math.log(amp / A) / (dt * nst)
     assert rate / (mu * k * k) == pytest.approx(1.0, abs=4 * mu * k * k * dt + 1e-5)
+
+
+def test_two_dimensional_cfl_form():
+    """The sum form of the CFL bound on a uniform state equals its closed form
+    cfl / ((|U|+c)/hx + (|V|+c)/hy), is half the per-direction step for flow at
+    45 degrees on a square grid, and the viscous bound caps both alike."""
+    U, V, rho, p, g = 0.7, 0.7, 1.3, 0.9, 1.4
+    c = inputs.random_smooth(16, 16, seed=0, bc=(0, 0, 0, 0))
+    c.prim = lambda x, y: (rho, U, V, p)
+    prm = oracle.make_params(**c.oracle_kwargs())
+    S = c.initial_state()
+    a = math.sqrt(g * p / rho)
+    dsum = oracle.cfl_dt_sum(prm, 0.4, S[0], S[2])
+    ddir = oracle.cfl_dt(prm, 0.4, S[0], S[2])
+    assert dsum == pytest.approx(0.4 / ((abs(U) + a) / c.hx + (abs(V) + a) / c.hy), rel=1e-14)
+    assert dsum == pytest.approx(0.5 * ddir, rel=1e-14)
+    c.mu = 5.0                                     # the viscous bound takes over
+    prm = oracle.make_params(**c.oracle_kwargs())
+    assert oracle.cfl_dt_sum(prm, 0.4, S[0], S[2]) == pytest.approx(oracle.cfl_dt(prm, 0.4, S[0], S[2]), rel=1e-14)
