@@ -604,10 +604,12 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "isentropic vortex %d^2 primary + %d^2 dual, periodic [0,10]^2, strength 5, "
                                    "FD-CGKS(6-4), GENO (App. D constants), CFL 0.2" % (n, n),
-                       "grid": [n, n], "node_updates_per_step": nodes, "parallelism": "replicas",
+                       "grid": [n, n], "node_updates_per_step": nodes,
+                       "primary_node_updates_per_step": n * n, "parallelism": "replicas",
                        "l2": "working set %.2f GB > 129 MB L2 (no flush needed)" %
                              (nodes * 8 * (24 + 24 + 12) / 1e9 + nodes * 8 * 66 / 1e9)},
-            "roofline": roof, "clocks": fp["clocks"], "gpu_launches": fp["launches"] * world}
+            "roofline": roof, "clocks": fp["clocks"], "gpu_launches": fp["launches"] * world,
+            "primary_node_updates_per_s": value * n * n / nodes}
 
     if "mixed" in results:
         mx = results["mixed"]
@@ -623,6 +625,7 @@ def main():
                    "Linf_rel_rho_vs_fp64": float(np.abs(a[0] - b[0]).max() / np.abs(b[0]).max()),
                    "after_steps": args.warmup + args.steps}
         line["mixed"] = {"value": mval, "unit": UNIT, "dtype": "f32+f64", "ms_per_step": mx["ms"] / args.steps,
+                         "primary_node_updates_per_s": mval * n * n / nodes,
                          "error": err,
                          "roofline": {"bound": "alu", "achieved": mach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                                       "frac": mach / FP32_PEAK_TFLOPS,
