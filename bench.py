@@ -474,7 +474,9 @@ def run_adjoint(args, world):
     adjoint (checkpoint every 50 steps) times, and the gradient along 2 random
     unit directions against central differences on the linear-reconstruction,
     c1-only collision time variant (where differences are in their linear
-    regime; with GENO's nonlinear weights the vortex far field is not)."""
+    regime; with GENO's nonlinear weights the vortex far field is not); and
+    the GENO window on a mixed-precision solver (mixed trajectory, FP64
+    reverse pass) with its gradient's distance from the FP64 one."""
     import numpy as np
     import torch
     from paper_2606_17772_gb300 import fdcgks, inputs
@@ -494,19 +496,26 @@ def run_adjoint(args, world):
                                   "(sigma 0.5, amplitude 1e-3, seed 1); gradient w.r.t. primary W^0; "
                                   "checkpoint every 50 steps; geno: App. D GENO constants, linear: linear "
                                   "reconstruction with tau = 0.05 dt" % args.adj_steps}}
-    for name, kw, ndir in (("geno", {}, 0), ("linear", dict(geno_variant=2, tau_c1=0.05, tau_c2=0.0), 2)):
+    fp64_geno = {}
+    runs = (("geno", {}, 0, fdcgks.FP64), ("linear", dict(geno_variant=2, tau_c1=0.05, tau_c2=0.0), 2, fdcgks.FP64),
+            ("geno_mixed", {}, 0, fdcgks.MIXED))
+    for name, kw, ndir, prec in runs:
         case = inputs.vortex(256, strength=5.0, **kw)
         S0, bump = setup(case, args.adj_steps)
         h2 = case.hx * case.hy
         n = args.adj_steps
-        with fdcgks.Solver.from_case(case) as s:
-            s.set_state(*S0)
-            dt = s.cfl_dt(0.2)
-            Wt = S0[0].clone()
-            Wt[0] += torch.from_numpy(1e-3 * bump).cuda()
-            s.set_state(Wt, *S0[1:])
-            s.steps(dt, n)
-            target = s.get_state()[0][0].clone()
+        with fdcgks.Solver.from_case(case, prec) as s:
+            if prec == fdcgks.MIXED:
+                # the FP64 run's step size and target, so that the gradients compare
+                dt, target = fp64_geno["dt"], fp64_geno["target"]
+            else:
+                s.set_state(*S0)
+                dt = s.cfl_dt(0.2)
+                Wt = S0[0].clone()
+                Wt[0] += torch.from_numpy(1e-3 * bump).cuda()
+                s.set_state(Wt, *S0[1:])
+                s.steps(dt, n)
+                target = s.get_state()[0][0].clone()
 
             def J(Wp0):
                 s.set_state(Wp0, *S0[1:])
@@ -541,6 +550,11 @@ def run_adjoint(args, world):
                      "adjoint_over_forward": ta / tf, "gradient_norm": float(g[0].norm())}
         if checks:
             out[name]["fd_rel_err"] = checks
+        if name == "geno":
+            fp64_geno.update(dt=dt, target=target, grad=g[0].clone())
+        if prec == fdcgks.MIXED:
+            out[name]["precision"] = "mixed trajectory, FP64 reverse pass"
+            out[name]["grad_rel_diff_vs_fp64"] = float((g[0] - fp64_geno["grad"]).norm() / fp64_geno["grad"].norm())
     return out
 
 

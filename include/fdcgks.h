@@ -249,8 +249,19 @@ fdcgks_status fdcgks_cfl_dt_noalloc(const fdcgks_params* params, const double* W
  *     more before its reverse pass (about three forward sweeps in all).  The
  *     call allocates a workspace of about ceil(nsteps / checkpoint_every) +
  *     checkpoint_every + 20 padded states and frees it before returning.
- *   - FP64 contexts only (FDCGKS_ERR_ARG otherwise).  Synchronizes the
- *     context stream. */
+ *   - Mixed-precision contexts: the trajectory (checkpoints, recomputed
+ *     segments, the final state the context keeps) is the context's own mixed
+ *     run, bit for bit; each step's reverse pass is the FP64 step's at those
+ *     states, so the adjoint accumulates in FP64 and the result is the FP64
+ *     step's derivative along the mixed trajectory.  With the linear
+ *     reconstruction it matches the mixed run's own derivative to the FP32
+ *     rounding of its fluxes.  With GENO it does not where the data vary by
+ *     less than about 4e-6 of their size (a vortex's far field): the mixed
+ *     step's GENO takes such data as smooth (an FP32 rounding floor in its
+ *     smoothness indicators), the FP64 step's weights follow them.
+ *   - Conservative reconstruction (recon_vars 0) and the boundary kinds of
+ *     params.bc only (no fdcgks_set_sides); FDCGKS_ERR_ARG otherwise.
+ *     Synchronizes the context stream. */
 fdcgks_status fdcgks_vjp_steps(fdcgks_t ctx, double dt, int nsteps, int checkpoint_every, const double* Wp0,
                                const double* Gp0, const double* Wd0, const double* Gd0, const double* aWp,
                                const double* aGp, const double* aWd, const double* aGd, double* gWp, double* gGp,

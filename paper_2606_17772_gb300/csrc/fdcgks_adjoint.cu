@@ -19,6 +19,14 @@
 // `checkpoint_every` steps; each step's intermediates (stage state, point and
 // nodal outputs of both stages, S2O4 accumulators) are recomputed once more
 // right before its reverse pass.
+// On a mixed-precision context the trajectory (checkpoints, segment states,
+// the final state) is the context's own mixed run, replayed through FP64
+// buffers that hold its float-float pairs exactly; each step's intermediates
+// and reverse pass are the FP64 step's at those states, so the adjoint state
+// accumulates in FP64 and the result is the FP64 step's derivative along the
+// mixed trajectory.  Where the data vary by less than about 4e-6 of their
+// size the mixed step's GENO takes them as smooth (its FP32 rounding floor)
+// and the FP64 step's does not; there the two derivatives differ.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -29,6 +37,7 @@
 #include "../../include/fdcgks.h"
 #include "fdcgks_dual.cuh"
 #include "fdcgks_kernels.cuh"
+#include "fdcgks_replay.h"
 
 namespace fdk {
 // the dual-number evaluation calls one out-of-line copy of the kinetic solve
@@ -479,6 +488,7 @@ struct Work {
   double *P1A = nullptr, *P1B = nullptr, *P2A = nullptr, *P2B = nullptr, *NF1 = nullptr, *NF2 = nullptr;
   double *A0 = nullptr, *A1 = nullptr, *As = nullptr, *Aacc = nullptr, *AgB = nullptr;
   double *PAa = nullptr, *PBa = nullptr, *NFa = nullptr;
+  double* fin = nullptr;     // final state (mixed contexts: loaded back at the end)
   int* flag = nullptr;
   char* arena = nullptr;
 };
@@ -630,7 +640,6 @@ extern "C" fdcgks_status fdcgks_vjp_steps(fdcgks_t ctx, double dt, int nsteps, i
                                           double* gWp, double* gGp, double* gWd, double* gGd) {
   Work w;
   if (!ctx_view(ctx, &w.v)) return afail(nullptr, FDCGKS_ERR_ARG, "ctx is NULL");
-  if (w.v.p.precision != FDCGKS_FP64) return afail(ctx, FDCGKS_ERR_ARG, "the adjoint needs an FP64 context");
   if (w.v.p.recon_vars != 0)
     return afail(ctx, FDCGKS_ERR_ARG, "the adjoint reconstructs conservative components only");
   if (w.v.has_sides) return afail(ctx, FDCGKS_ERR_ARG, "the adjoint takes the boundary kinds of params.bc only");
@@ -649,10 +658,11 @@ extern "C" fdcgks_status fdcgks_vjp_steps(fdcgks_t ctx, double dt, int nsteps, i
   const int nseg = std::max(1, std::min(nsteps, checkpoint_every));
   const size_t pb = sizeof(double) * NPT * L.pplane, nb = sizeof(double) * 2 * NNF * L.plane;
   const size_t acc = sizeof(double) * 2 * 4 * L.plane, gbb = sizeof(double) * 2 * 8 * L.plane;
+  const bool mixed = w.v.p.precision == FDCGKS_MIXED;
   const size_t sizes[] = {w.fs, w.fs, w.fs, acc, gbb, pb, pb, pb, pb, nb, nb,
-                          w.fs, w.fs, w.fs, acc, gbb, pb, pb, nb, 256};
+                          w.fs, w.fs, w.fs, acc, gbb, pb, pb, nb, 256, mixed ? w.fs : 0};
   double** slots[] = {&w.Sn, &w.S2, &w.Snext, &w.Wacc, &w.gB, &w.P1A, &w.P1B, &w.P2A, &w.P2B, &w.NF1, &w.NF2,
-                      &w.A0, &w.A1, &w.As, &w.Aacc, &w.AgB, &w.PAa, &w.PBa, &w.NFa, (double**)&w.flag};
+                      &w.A0, &w.A1, &w.As, &w.Aacc, &w.AgB, &w.PAa, &w.PBa, &w.NFa, (double**)&w.flag, &w.fin};
   auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
   size_t total = 0;
   for (size_t b : sizes) total += r256(b);
@@ -667,6 +677,13 @@ extern "C" fdcgks_status fdcgks_vjp_steps(fdcgks_t ctx, double dt, int nsteps, i
   for (int k = 0; k < nck; ++k, off += r256(w.fs)) w.ck.push_back((double*)(w.arena + off));
   for (int k = 0; k < nseg; ++k, off += r256(w.fs)) w.seg.push_back((double*)(w.arena + off));
 
+  // one step of the trajectory: the FP64 step itself, or the context's mixed
+  // step replayed between FP64 buffers
+  auto advance = [&](const double* in, double* out) -> fdcgks_status {
+    if (mixed) return ctx_replay_step(ctx, dt, in, out);
+    cudaError_t r = forward_step(w, dt, in, out);
+    return r == cudaSuccess ? FDCGKS_OK : afail(ctx, FDCGKS_ERR_CUDA, "forward", r);
+  };
   auto run = [&]() -> fdcgks_status {
     cudaError_t r = cudaMemsetAsync(w.arena, 0, total, s);
     if (r != cudaSuccess) return afail(ctx, FDCGKS_ERR_CUDA, "workspace clear", r);
@@ -674,16 +691,18 @@ extern "C" fdcgks_status fdcgks_vjp_steps(fdcgks_t ctx, double dt, int nsteps, i
     if ((r = cudaMemcpyAsync(w.ck[0], w.v.S, w.fs, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
       return afail(ctx, FDCGKS_ERR_CUDA, "checkpoint", r);
     const double* cur = w.ck[0];
+    fdcgks_status fs;
     for (int m = 0; m < nsteps; ++m) {
-      if ((r = forward_step(w, dt, cur, w.Snext)) != cudaSuccess) return afail(ctx, FDCGKS_ERR_CUDA, "forward", r);
+      if ((fs = advance(cur, w.Snext)) != FDCGKS_OK) return fs;
       const int k = (m + 1) / checkpoint_every;
       double* dst = ((m + 1) % checkpoint_every == 0 && k < nck) ? w.ck[k] : w.seg[0];
       if ((r = cudaMemcpyAsync(dst, w.Snext, w.fs, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
         return afail(ctx, FDCGKS_ERR_CUDA, "forward", r);
       cur = dst;
     }
-    // the context keeps the final state
-    if ((r = cudaMemcpyAsync(w.v.S, cur, w.fs, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    // the context keeps the final state (a mixed context's buffers are reused
+    // by the replays below, so its final state is loaded back at the end)
+    if ((r = cudaMemcpyAsync(mixed ? w.fin : w.v.S, cur, w.fs, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
       return afail(ctx, FDCGKS_ERR_CUDA, "final state", r);
     // adjoint of the final state
     double* Aout = w.A0;
@@ -698,8 +717,7 @@ extern "C" fdcgks_status fdcgks_vjp_steps(fdcgks_t ctx, double dt, int nsteps, i
       if ((r = cudaMemcpyAsync(w.seg[0], w.ck[k], w.fs, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
         return afail(ctx, FDCGKS_ERR_CUDA, "segment", r);
       for (int m = m0; m + 1 < m1; ++m)
-        if ((r = forward_step(w, dt, w.seg[m - m0], w.seg[m - m0 + 1])) != cudaSuccess)
-          return afail(ctx, FDCGKS_ERR_CUDA, "segment forward", r);
+        if ((fs = advance(w.seg[m - m0], w.seg[m - m0 + 1])) != FDCGKS_OK) return fs;
       for (int m = m1 - 1; m >= m0; --m) {
         if ((r = forward_step(w, dt, w.seg[m - m0], w.Snext)) != cudaSuccess)
           return afail(ctx, FDCGKS_ERR_CUDA, "recompute", r);
@@ -710,6 +728,7 @@ extern "C" fdcgks_status fdcgks_vjp_steps(fdcgks_t ctx, double dt, int nsteps, i
     if ((r = dense_copy(w, Aout, nullptr, nullptr, gWp, gGp, 0)) != cudaSuccess ||
         (r = dense_copy(w, Aout, nullptr, nullptr, gWd, gGd, 1)) != cudaSuccess)
       return afail(ctx, FDCGKS_ERR_CUDA, "gradient copy", r);
+    if (mixed && (fs = ctx_load_padded(ctx, w.fin)) != FDCGKS_OK) return fs;
     if ((r = cudaStreamSynchronize(s)) != cudaSuccess) return afail(ctx, FDCGKS_ERR_CUDA, "adjoint", r);
     return FDCGKS_OK;
   };

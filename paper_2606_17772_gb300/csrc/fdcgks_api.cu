@@ -8,6 +8,7 @@
 
 #include "../../include/fdcgks.h"
 #include "fdcgks_internal.cuh"
+#include "fdcgks_replay.h"
 
 using namespace fdk;
 using fdk::check_params;
@@ -389,6 +390,34 @@ static fdcgks_status run_step(fdcgks_t c, double dt) {
   s = run_stage<R>(c, dt, UPD_STAGE2, nullptr);
   if (s == FDCGKS_OK) c->t += dt;
   return s;
+}
+
+// Load a padded FP64 state [2][12][plane] (interior valid) into the context:
+// the state itself on the FP64 path, split into float-float pairs on the
+// mixed path (as fdcgks_set_state does, without validation).
+fdcgks_status fdk::ctx_load_padded(fdcgks_t c, const double* in) {
+  CUDA_TRY(c, cudaMemcpyAsync(c->S, in, sizeof(double) * 2 * NFLD * c->L.plane, cudaMemcpyDeviceToDevice,
+                              c->stream));
+  if (c->Sf) CUDA_TRY(c, launch_split_ff(c->S, c->Sf, c->Slo, 2L * NFLD * c->L.plane, c->stream));
+  c->has_state = true;
+  return FDCGKS_OK;
+}
+
+// One step of the context's own precision from the padded FP64 state `in`
+// to `out`, through the context's buffers (its state is overwritten, its time
+// kept).  A float-float pair joined to FP64 splits back into the same pair,
+// so steps chained through FP64 buffers reproduce the mixed run exactly.
+fdcgks_status fdk::ctx_replay_step(fdcgks_t c, double dt, const double* in, double* out) {
+  fdcgks_status s = ctx_load_padded(c, in);
+  if (s != FDCGKS_OK) return s;
+  const double t = c->t;
+  s = c->p.precision == FDCGKS_MIXED ? run_step<float>(c, dt) : run_step<double>(c, dt);
+  c->t = t;
+  if (s != FDCGKS_OK) return s;
+  CUDA_TRY(c, join_state(c));
+  CUDA_TRY(c, cudaMemcpyAsync(out, c->S, sizeof(double) * 2 * NFLD * c->L.plane, cudaMemcpyDeviceToDevice,
+                              c->stream));
+  return FDCGKS_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -382,7 +382,9 @@ class Solver:
     def vjp_steps(self, dt, nsteps, state0, adj_final, checkpoint_every=50):
         """dJ/d(initial state) for dJ/d(final state) `adj_final` after `nsteps`
         steps of size dt from `state0` (both 4-tuples of CUDA float64 tensors in
-        the set_state layouts).  The solver keeps the final state."""
+        the set_state layouts).  The solver keeps the final state.  On a
+        mixed-precision solver the trajectory is its own mixed run and the
+        reverse pass is the FP64 step's along it."""
         import torch
         torch.cuda.current_stream().synchronize()
         out = [torch.zeros(s, dtype=torch.float64, device="cuda") for s in self.shapes()]
