@@ -251,7 +251,10 @@ fdcgks_status fdcgks_cfl_dt_noalloc(const fdcgks_params* params, const double* W
  *     checkpoint_every + 20 padded states and frees it before returning.
  *   - Mixed-precision contexts: the trajectory (checkpoints, recomputed
  *     segments, the final state the context keeps) is the context's own mixed
- *     run, bit for bit; each step's reverse pass is the FP64 step's at those
+ *     run, kept between steps in FP64 buffers (a float-float pair round-trips
+ *     to the same FP64 value; its low part can lose bits below 2^-53 of it,
+ *     so the state follows the mixed run to FP64 rounding, about 1e-14
+ *     relative after 50 steps); each step's reverse pass is the FP64 step's at those
  *     states, so the adjoint accumulates in FP64 and the result is the FP64
  *     step's derivative along the mixed trajectory.  With the linear
  *     reconstruction it matches the mixed run's own derivative to the FP32

@@ -21,7 +21,7 @@
 // right before its reverse pass.
 // On a mixed-precision context the trajectory (checkpoints, segment states,
 // the final state) is the context's own mixed run, replayed through FP64
-// buffers that hold its float-float pairs exactly; each step's intermediates
+// buffers that hold its float-float pairs to FP64 rounding; each step's intermediates
 // and reverse pass are the FP64 step's at those states, so the adjoint state
 // accumulates in FP64 and the result is the FP64 step's derivative along the
 // mixed trajectory.  Where the data vary by less than about 4e-6 of their

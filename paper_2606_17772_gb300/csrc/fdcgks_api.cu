@@ -405,8 +405,10 @@ fdcgks_status fdk::ctx_load_padded(fdcgks_t c, const double* in) {
 
 // One step of the context's own precision from the padded FP64 state `in`
 // to `out`, through the context's buffers (its state is overwritten, its time
-// kept).  A float-float pair joined to FP64 splits back into the same pair,
-// so steps chained through FP64 buffers reproduce the mixed run exactly.
+// kept).  A float-float pair joined to FP64 splits back into a pair of the
+// same FP64 value; the low part keeps its bits unless it lies more than 29
+// bits below the high part, when it loses those below 2^-53 of the value, so
+// steps chained through FP64 buffers follow the mixed run to FP64 rounding.
 fdcgks_status fdk::ctx_replay_step(fdcgks_t c, double dt, const double* in, double* out) {
   fdcgks_status s = ctx_load_padded(c, in);
   if (s != FDCGKS_OK) return s;

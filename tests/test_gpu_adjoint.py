@@ -181,8 +181,10 @@ def test_adjoint_rejects_bad_arguments():
 @pytest.mark.parametrize("ck", [1, 3])
 def test_mixed_adjoint_keeps_the_mixed_run(ck):
     """The final state a mixed context keeps after the adjoint is the plain
-    mixed run's, bit for bit (the trajectory is replayed through FP64 buffers
-    that hold the float-float pairs exactly)."""
+    mixed run's to FP64 rounding: the trajectory is replayed through FP64
+    buffers, where a float-float pair keeps its FP64 value but its low part
+    can lose bits below 2^-53 of it (tests/test_float_float_host.py); on this
+    case the two runs were found identical."""
     case, dt = CASES["periodic_geno"]()
     S0 = case.initial_state()
     rng = np.random.default_rng(9)
@@ -192,7 +194,7 @@ def test_mixed_adjoint_keeps_the_mixed_run(ck):
         kept = [t.cpu().numpy() for t in s.get_state()]
         ref = run(s, S0, dt, 5)
     for a, b in zip(kept, ref):
-        assert np.array_equal(a, b)
+        assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
 
 
 def _grad(case, prec, dt, S0, seed, n=3):
