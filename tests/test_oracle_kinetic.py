@@ -196,3 +196,28 @@ def test_nodal_flux_fourier_heat_flux(Pr):
     q = -(mu / Pr) * GAMMA / (GAMMA - 1) * dT
     np.testing.assert_allclose(o["F"], [0.0, p, 0.0, q], rtol=1e-12, atol=1e-14)
     np.testing.assert_allclose(o["G"], [0.0, 0.0, p, 0.0], rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("Ux,Vy", [(0.3, 0.0), (0.3, 0.3), (0.25, -0.4)])
+def test_nodal_flux_normal_stresses(Ux, Vy):
+    """Navier-Stokes limit of the BGK gas with N = K + 2 degrees of freedom
+    (Chapman-Enskog): with tau = mu/p, uniform density and pressure and a
+    velocity field (U0 + Ux x, V0 + Vy y), the viscous stresses are
+    sigma_xx = mu (2 Ux - (2/N) div U), sigma_yy = mu (2 Vy - (2/N) div U),
+    sigma_xy = 0; the energy fluxes carry the work U0 sigma_xx, V0 sigma_yy
+    and no heat flux (the temperature is uniform), whatever Pr."""
+    rho, p, U0, V0, mu = 1.2, 0.85, 0.4, -0.3, 0.025
+    N = K2D + 2.0
+    E = p / (GAMMA - 1) + 0.5 * rho * (U0 * U0 + V0 * V0)
+    W = np.array([rho, rho * U0, rho * V0, E])
+    Wx = np.array([0.0, rho * Ux, 0.0, rho * U0 * Ux])
+    Wy = np.array([0.0, 0.0, rho * Vy, rho * V0 * Vy])
+    prm = oracle.make_params(8, 8, mu=mu, Pr=0.73)
+    o = oracle.nodal_flux(prm, 0.01, W, Wx, Wy)
+    div = Ux + Vy
+    sxx = mu * (2.0 * Ux - 2.0 / N * div)
+    syy = mu * (2.0 * Vy - 2.0 / N * div)
+    F = [rho * U0, rho * U0 * U0 + p - sxx, rho * U0 * V0, U0 * (E + p) - U0 * sxx]
+    G = [rho * V0, rho * U0 * V0, rho * V0 * V0 + p - syy, V0 * (E + p) - V0 * syy]
+    np.testing.assert_allclose(o["F"], F, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(o["G"], G, rtol=1e-12, atol=1e-14)
