@@ -290,6 +290,26 @@ def test_viscous_shear_stress_operator():
     assert proj / (-mu * k * k * A) == pytest.approx(1.0, abs=2e-5)
 
 
+def test_viscous_normal_stress_operator():
+    """U = A sin(k x) at uniform rho, p: at t = 0 the x-momentum operator is
+    -rho (U^2)_x + (sigma_xx)_x with the BGK gas's normal stress sigma_xx =
+    mu (2 - 2/N) U_x, N = K + 2 degrees of freedom (Chapman-Enskog); its sin(k x)
+    part is -mu (2 - 2/N) k^2 A on both grids (1.0000002 measured at 32 nodes;
+    the monatomic 4/3 would read 1.2)."""
+    A, k, mu, p, n = 1e-3, 2 * math.pi, 0.01, 100.0, 32
+    N = (4.0 - 2.0 * 1.4) / 0.4 + 2.0
+    c = inputs.density_wave_1d(n, ny=1, mu=mu, Pr=0.72)
+    c.x1, c.y1 = 1.0, 1.0 / n
+    c.prim = lambda x, y: (1.0, A * np.sin(k * x), 0.0, p)
+    prm = oracle.make_params(**c.oracle_kwargs())
+    o = oracle.stage(prm, 1e-3, *c.initial_state())
+    for key, dual in (("Lp", False), ("Ld", True)):
+        X, _ = c.node_xy(dual)
+        L = o[key].reshape(4, X.shape[0], X.shape[1])
+        proj = (L[1, 0] * np.sin(k * X[0])).sum() * 2 / X.shape[1]
+        assert proj / (-(2.0 - 2.0 / N) * mu * k * k * A) == pytest.approx(1.0, abs=2e-6), key
+
+
 def test_viscous_shear_wave_decay():
     """Over many steps the decay follows exp(-nu k^2 t).  The averaged gradient
     evolves with the Euler-level time derivative of the interface solution
