@@ -310,6 +310,28 @@ def test_viscous_normal_stress_operator():
         assert proj / (-(2.0 - 2.0 / N) * mu * k * k * A) == pytest.approx(1.0, abs=2e-6), key
 
 
+@pytest.mark.parametrize("Pr", [1.0, 0.72])
+def test_heat_conduction_operator(Pr):
+    """Gas at rest at uniform pressure with T = T0 + A sin(k x): at t = 0 the
+    energy operator is (kappa T_x)_x with kappa = (mu/Pr) gamma/(gamma - 1)
+    (Fourier's law; Pr enters through the Prandtl correction of the kinetic
+    heat flux), whose sin(k x) part is -kappa k^2 A on both grids (1.000001 and
+    1.0000014 measured at 32 nodes; without the correction Pr = 0.72 would
+    read 0.72)."""
+    A, k, mu, p, n, g = 1e-3, 2 * math.pi, 0.01, 100.0, 32, 1.4
+    c = inputs.density_wave_1d(n, ny=1, mu=mu, Pr=Pr)
+    c.x1, c.y1 = 1.0, 1.0 / n
+    c.prim = lambda x, y: (p / (1.0 + A * np.sin(k * x)), 0.0, 0.0, p)
+    prm = oracle.make_params(**c.oracle_kwargs())
+    o = oracle.stage(prm, 1e-4, *c.initial_state())
+    kappa = mu / Pr * g / (g - 1.0)
+    for key, dual in (("Lp", False), ("Ld", True)):
+        X, _ = c.node_xy(dual)
+        L = o[key].reshape(4, X.shape[0], X.shape[1])
+        proj = (L[3, 0] * np.sin(k * X[0])).sum() * 2 / X.shape[1]
+        assert proj / (-kappa * k * k * A) == pytest.approx(1.0, abs=5e-6), key
+
+
 def test_viscous_shear_wave_decay():
     """Over many steps the decay follows exp(-nu k^2 t).  The averaged gradient
     evolves with the Euler-level time derivative of the interface solution
