@@ -55,9 +55,12 @@
 //     interface state with non-positive density or pressure falls back to the
 //     adjacent node's state with zero normal slope, and chi = 0 there.
 //
-// Parity unpinned: the form and constants of the collision time tau and the
-// choice tau_0 = tau are exercised by no number the paper prints (its
-// accuracy tables use tau = 0); the no-slip wall treatment is pinned only by
+// Parity unpinned: the numerical constants c1, c2 of the collision time tau
+// and the choice tau_0 = tau are exercised by no number the paper prints (its
+// accuracy tables use tau = 0); tau's physical part mu/p and the Prandtl
+// correction are pinned by the Navier-Stokes limits of the kinetic flux and
+// of the stage operator (shear and normal stress, heat conduction, against
+// their Chapman-Enskog closed forms); the no-slip wall treatment is pinned only by
 // symmetry, free-stream and conservation-bound tests; split sides are pinned
 // by reduction to the unsplit kinds, free streams and the exact speed of a
 // tracked oblique Mach 10 shock, not by a number the paper prints (its
