@@ -60,8 +60,9 @@
 // accuracy tables use tau = 0); tau's physical part mu/p and the Prandtl
 // correction are pinned by the Navier-Stokes limits of the kinetic flux and
 // of the stage operator (shear and normal stress, heat conduction, against
-// their Chapman-Enskog closed forms); the no-slip wall treatment is pinned only by
-// symmetry, free-stream and conservation-bound tests; split sides are pinned
+// their Chapman-Enskog closed forms); the no-slip wall treatment is pinned by
+// symmetry, free-stream and conservation-bound tests and by the exact operator
+// of viscous channel flow between two walls; split sides are pinned
 // by reduction to the unsplit kinds, free streams and the exact speed of a
 // tracked oblique Mach 10 shock, not by a number the paper prints (its
 // double Mach reflection results are figures).  Dual nodes on a no-slip wall
