@@ -264,7 +264,11 @@ fdcgks_status fdcgks_cfl_dt_noalloc(const fdcgks_params* params, const double* W
  *     smoothness indicators), the FP64 step's weights follow them.
  *   - Conservative reconstruction (recon_vars 0) and the boundary kinds of
  *     params.bc only (no fdcgks_set_sides); FDCGKS_ERR_ARG otherwise.
- *     Synchronizes the context stream. */
+ *     A non-physical initial state returns FDCGKS_ERR_NONPHYSICAL (as
+ *     fdcgks_set_state); FDCGKS_ERR_NOMEM when the workspace cannot be
+ *     allocated; FDCGKS_ERR_CUDA on a failed launch or copy, after which the
+ *     gradient arrays and the context's state are unspecified (load a state
+ *     again with fdcgks_set_state).  Synchronizes the context stream. */
 fdcgks_status fdcgks_vjp_steps(fdcgks_t ctx, double dt, int nsteps, int checkpoint_every, const double* Wp0,
                                const double* Gp0, const double* Wd0, const double* Gd0, const double* aWp,
                                const double* aGp, const double* aWd, const double* aGd, double* gWp, double* gGp,
