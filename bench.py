@@ -208,6 +208,31 @@ def oracle_rate(n_sample, nsteps):
     return 2 * n_sample * n_sample * nsteps / el, el
 
 
+def _oracle_rate_task(sample):
+    return oracle_rate(*sample)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_rate_all_cores(n_sample, nsteps, ncores=None):
+    """The same bounded sample run concurrently by one spawned process per host
+    core, each on its own copy (independent runs, the oracle unchanged):
+    aggregate node-updates/s over the wall time of the concurrent runs."""
+    import multiprocessing as mp
+    ncores = ncores or host_cores()
+    with mp.get_context("spawn").Pool(ncores) as pool:
+        pool.map(_oracle_rate_task, [(8, 1)] * (2 * ncores), chunksize=1)   # start workers, load the library
+        t0 = time.perf_counter()
+        pool.map(_oracle_rate_task, [(n_sample, nsteps)] * ncores, chunksize=1)
+        wall = time.perf_counter() - t0
+    return ncores * 2 * n_sample * n_sample * nsteps / wall, wall, ncores
+
+
 def run_reference(args):
     """CPU oracle as the reference arm: K timed steps of a bounded sample."""
     world, rank = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0"))
@@ -691,6 +716,12 @@ def main():
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "isentropic vortex %d^2 (+dual), %d steps, %.1f s, single thread" %
                                           (ns, nst, el)}
+        ns_all = 64
+        arate, wall, ncores = oracle_rate_all_cores(ns_all, nst)
+        line["cpu_baseline"]["all_cores"] = {
+            "value": arate, "unit": UNIT, "cores": ncores, "kind": "oracle",
+            "sample": "isentropic vortex %d^2 (+dual), %d steps, one independent copy per core, %.1f s wall" %
+                      (ns_all, nst, wall)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

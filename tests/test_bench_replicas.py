@@ -75,3 +75,17 @@ def test_reference_arm_prints_on_rank_zero_only():
     assert len(lines[0]) == 1 and len(lines[1]) == 0
     line = json.loads(lines[0][0])
     assert line["impl"] == "reference" and line["value"] > 0 and line["n_gpus"] == 2
+
+
+def test_oracle_all_cores_leg():
+    """The all-cores CPU baseline: one spawned process per core, each running
+    its own copy of the bounded oracle sample; the aggregate rate counts every
+    copy over the wall time of the concurrent runs."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench\n"
+            "r, wall, n = bench.oracle_rate_all_cores(8, 1, ncores=2)\n"
+            "print(json.dumps({'rate': r, 'wall': wall, 'n': n}))\n" % ROOT)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    res = json.loads(out.stdout.strip().splitlines()[-1])
+    assert res["n"] == 2 and res["wall"] > 0
+    assert res["rate"] == pytest.approx(2 * 2 * 8 * 8 * 1 / res["wall"], rel=1e-12)
