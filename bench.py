@@ -717,11 +717,14 @@ def main():
                                 "sample": "isentropic vortex %d^2 (+dual), %d steps, %.1f s, single thread" %
                                           (ns, nst, el)}
         ns_all = 64
-        arate, wall, ncores = oracle_rate_all_cores(ns_all, nst)
-        line["cpu_baseline"]["all_cores"] = {
-            "value": arate, "unit": UNIT, "cores": ncores, "kind": "oracle",
-            "sample": "isentropic vortex %d^2 (+dual), %d steps, one independent copy per core, %.1f s wall" %
-                      (ns_all, nst, wall)}
+        try:
+            arate, wall, ncores = oracle_rate_all_cores(ns_all, nst)
+            line["cpu_baseline"]["all_cores"] = {
+                "value": arate, "unit": UNIT, "cores": ncores, "kind": "oracle",
+                "sample": "isentropic vortex %d^2 (+dual), %d steps, one independent copy per core, %.1f s wall" %
+                          (ns_all, nst, wall)}
+        except Exception as e:                   # the auxiliary leg never costs the line
+            line["cpu_baseline"]["all_cores"] = {"error": "%s: %s" % (type(e).__name__, e)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
