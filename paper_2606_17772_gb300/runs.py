@@ -12,11 +12,14 @@ JSON summary:
   * Woodward-Colella blast waves (Sec. 5.3) to t = 0.038 with the
     one-dimensional scheme: density and pressure along the tube;
   * the isentropic vortex once around the periodic box on 128^2 ... 1024^2:
-    errors against the exact solution and the observed order.
+    errors against the exact solution and the observed order;
+  * the adjoint workload: the gradient of a density misfit through 500 steps
+    of the 256^2 vortex, checked along 16 directions by central differences.
 
     python -m paper_2606_17772_gb300.runs --case viscous_tube --nx 1000 --ny 500 --precision mixed
     python -m paper_2606_17772_gb300.runs --case double_mach --nx 960 --ny 240 --precision fp64
     python -m paper_2606_17772_gb300.runs --case vortex_convergence
+    python -m paper_2606_17772_gb300.runs --case adjoint --precision fp64
 """
 import argparse
 import json
@@ -174,10 +177,77 @@ def woodward_colella(nx=400, t_end=0.038, cfl=0.4, flux_variant=62, recon_vars=0
     }
 
 
+def adjoint_window(n=256, nsteps=500, ndir=16, checkpoint_every=50, variant="linear", precision=fdcgks.FP64,
+                   cfl=0.2, strength=5.0):
+    """Gradient of a density misfit through nsteps steps of the n^2 isentropic
+    vortex: J = 1/2 sum (rho - rho_target)^2 h^2 on the primary grid, the
+    target a run from rho plus 8 seeded Gaussian bumps (sigma 0.5, amplitude
+    1e-3), differentiated with respect to the primary W^0 by fdcgks_vjp_steps
+    (checkpoints every checkpoint_every steps), and checked along ndir seeded
+    random unit directions against central differences of J.  variant
+    "linear": linear reconstruction with tau = 0.05 dt, where the differences
+    are in their linear regime; "geno": the App. D GENO constants, where the
+    vortex's far field puts them out of it (the errors are reported, not a
+    check).  On a mixed-precision solver the trajectory is the mixed run."""
+    import torch
+    kw = dict(geno_variant=2, tau_c1=0.05, tau_c2=0.0) if variant == "linear" else dict(geno_variant=1)
+    case = inputs.vortex(n, strength=strength, **kw)
+    S0 = [torch.from_numpy(a).cuda() for a in case.initial_state()]
+    rng = np.random.default_rng(1)
+    X, Y = case.node_xy(False)
+    bump = np.zeros_like(X)
+    for _ in range(8):
+        cx, cy = rng.uniform(0, 10, 2)
+        bump += np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (2 * 0.5 ** 2))
+    h2 = case.hx * case.hy
+    with fdcgks.Solver.from_case(case, precision) as s:
+        s.set_state(*S0)
+        dt = s.cfl_dt(cfl)
+        Wt = S0[0].clone()
+        Wt[0] += torch.from_numpy(1e-3 * bump).cuda()
+        s.set_state(Wt, *S0[1:])
+        s.steps(dt, nsteps)
+        target = s.get_state()[0][0].clone()
+
+        def J(Wp0):
+            s.set_state(Wp0, *S0[1:])
+            s.steps(dt, nsteps)
+            return 0.5 * float(((s.get_state()[0][0] - target) ** 2).sum()) * h2
+
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J0 = J(S0[0])
+        torch.cuda.synchronize()
+        t_forward = time.perf_counter() - t0
+        fin = s.get_state()
+        seed = [torch.zeros_like(t) for t in S0]
+        seed[0][0] = (fin[0][0] - target) * h2
+        t0 = time.perf_counter()
+        g = s.vjp_steps(dt, nsteps, S0, seed, checkpoint_every=checkpoint_every)
+        torch.cuda.synchronize()
+        t_adjoint = time.perf_counter() - t0
+        drng = np.random.default_rng(2)
+        rel = []
+        for _ in range(ndir):
+            d = torch.from_numpy(drng.standard_normal(S0[0].shape)).cuda()
+            d /= d.norm()
+            eps = 1e-8 * n
+            fd = (J(S0[0] + eps * d) - J(S0[0] - eps * d)) / (2 * eps)
+            ad = float((g[0] * d).sum())
+            rel.append(abs(ad - fd) / abs(fd))
+    return {"case": "adjoint", "n": n, "steps": nsteps, "checkpoint_every": checkpoint_every, "variant": variant,
+            "precision": "mixed" if precision == fdcgks.MIXED else "fp64", "dt": dt, "J": J0,
+            "forward_s": t_forward, "adjoint_s": t_adjoint, "gradient_norm": float(g[0].norm()),
+            "fd_rel_err": rel, "fd_rel_err_max": max(rel) if rel else None}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
-    ap.add_argument("--case", choices=["viscous_tube", "double_mach", "woodward_colella", "vortex_convergence"],
-                    default="viscous_tube")
+    ap.add_argument("--case", choices=["viscous_tube", "double_mach", "woodward_colella", "vortex_convergence",
+                                       "adjoint"], default="viscous_tube")
+    ap.add_argument("--steps", type=int, default=500, help="adjoint: steps through which J is differentiated")
+    ap.add_argument("--dirs", type=int, default=16, help="adjoint: directions checked by central differences")
+    ap.add_argument("--variant", choices=["linear", "geno"], default="linear", help="adjoint: reconstruction")
     ap.add_argument("--nx", type=int, default=None)
     ap.add_argument("--ny", type=int, default=None)
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
@@ -196,7 +266,10 @@ def main():
     prec = fdcgks.MIXED if a.precision == "mixed" else fdcgks.FP64
     opt = {k: v for k, v in (("flux_variant", a.flux), ("recon_vars", a.recon_vars), ("tau_c1", a.tau_c1),
                              ("tau_c2", a.tau_c2), ("geno_variant", a.geno)) if v is not None}
-    if a.case == "vortex_convergence":
+    if a.case == "adjoint":
+        res = adjoint_window(a.nx or 256, a.steps, a.dirs, variant=a.variant, precision=prec,
+                             cfl=a.cfl if a.cfl != 0.4 else 0.2)
+    elif a.case == "vortex_convergence":
         res = vortex_convergence(t_end=a.t_end or 10.0, cfl=a.cfl if a.cfl != 0.4 else 0.2, **opt)
     elif a.case == "viscous_tube":
         res = viscous_shock_tube(a.nx or 1000, a.ny or 500, prec, a.t_end or 1.0, a.cfl, **opt)
