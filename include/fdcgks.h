@@ -12,7 +12,12 @@
  *
  * Conventions for every entry point:
  *   - Status codes; nothing aborts, exits or traps on the device.  A failed
- *     call leaves a message readable with fdcgks_last_error().
+ *     call leaves a message readable with fdcgks_last_error().  Unless an
+ *     entry point says otherwise: FDCGKS_ERR_ARG for a NULL context or array
+ *     or an out-of-range argument (nothing is changed then); FDCGKS_ERR_STATE
+ *     for a call that needs a state before fdcgks_set_state; FDCGKS_ERR_NOMEM
+ *     when a device allocation fails; FDCGKS_ERR_CUDA for a failed launch or
+ *     copy, after which the context's state is unspecified (load one again).
  *   - Arrays are float64, C order.  Conservative fields W: [4][ny][nx];
  *     gradients: [2][4][ny][nx] (averaged x-gradient, then y-gradient).
  *     Dual-grid arrays use (nyd, nxd) from fdcgks_dims().
