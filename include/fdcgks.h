@@ -210,10 +210,10 @@ fdcgks_status fdcgks_recon_batch(const fdcgks_params* params, int kind, double h
 
 /* Allocation-free CFL time step.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory when they need
- * a time step, e.g. code running while a stream is captured into a CUDA graph
- * (allocation calls are not allowed there), hosts that give the library a
- * fixed memory budget, or loops that must not risk an allocation failure or
- * the synchronisation cudaMalloc/cudaFree can imply.  It computes the same
+ * a time step, e.g. an application that gives the library a fixed share of
+ * the GPU's memory and forbids further allocations, or a time loop that must
+ * not risk an allocation failure or the synchronisation cudaMalloc/cudaFree
+ * can imply.  It computes the same
  * time step as fdcgks_cfl_dt, from the caller's device arrays Wp [4][ny][nx]
  * and Wd [4][nyd][nxd] (float64, read only), without a context and without
  * allocating: its partial maxima live in a fixed device array of the library
@@ -225,7 +225,10 @@ fdcgks_status fdcgks_recon_batch(const fdcgks_params* params, int kind, double h
  *     primary plus dual nodes are rejected with FDCGKS_ERR_ARG.
  *   - The first call on each device looks up the device address of the
  *     library's array (once per device, with that device current); make that
- *     first call before any stream capture.
+ *     first call before any stream capture.  The address is kept for the rest
+ *     of the process: it belongs to the device's primary context, so the
+ *     caller must not reset the device (cudaDeviceReset) or make another
+ *     context current between calls.
  *   - All calls share the one array and it keeps the last call's contents;
  *     each call writes every entry it reads, so nothing needs clearing, but
  *     calls that overlap on the GPU (other streams, other host threads) race

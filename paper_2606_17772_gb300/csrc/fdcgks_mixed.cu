@@ -1,6 +1,7 @@
 // Mixed-precision instantiation of the FD-CGKS stage kernels: FP32
-// reconstruction and flux arithmetic; the state, the S2O4 accumulation and
-// the collision-time coefficients stay FP64.
+// reconstruction and flux arithmetic; the state and the S2O4 accumulation as
+// float-float pairs; the time coefficients of the interface solution in FP64
+// (with expm1) where dt/tau <= 4, where they cancel, and in FP32 above.
 #include "fdcgks_kernels.cuh"
 
 namespace fdk {

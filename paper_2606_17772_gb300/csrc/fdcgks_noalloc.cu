@@ -4,13 +4,11 @@
 // instead of memory obtained from cudaMalloc.
 //
 // Some callers cannot allocate device memory at the moment they need a time
-// step: code that runs while a stream is being captured into a CUDA graph
-// (allocation calls are not allowed there), hosts that hand the library a
-// fixed memory budget and forbid further allocations, or loops that must not
-// risk an allocation failure or the implicit synchronisation that cudaMalloc
-// and cudaFree can cause.  They keep their state in their own buffers and
-// call fdcgks_cfl_dt_noalloc, which needs neither a context nor any
-// allocation.
+// step: applications that hand the library a fixed share of the GPU's memory
+// and forbid further allocations, or time loops that must not risk an
+// allocation failure or the implicit synchronisation that cudaMalloc and
+// cudaFree can cause.  They keep their state in their own buffers and call
+// fdcgks_cfl_dt_noalloc, which needs neither a context nor any allocation.
 #include <cmath>
 #include <cstdio>
 #include <mutex>
@@ -31,6 +29,7 @@ const int MAX_TILES = FDCGKS_NOALLOC_MAX_TILES;
 static __device__ __align__(256) double g_cfl_scratch[2 * MAX_TILES + 2];
 
 // host-side addresses of g_cfl_scratch, one per device, filled on first use
+// and kept for the process (valid while the device's primary context lives)
 const int MAX_DEVICES = 64;
 static void* g_scratch_addr[MAX_DEVICES];
 static std::mutex g_scratch_lock;

@@ -217,6 +217,15 @@ def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
+def _on_current_stream(params):
+    """A copy of params whose stream is torch's current stream where the caller
+    left it unset; the caller's own params object is not modified."""
+    p = type(params).from_buffer_copy(params)
+    if p.stream is None:
+        p.stream = _stream().value
+    return p
+
+
 def make_params(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, mu=0.0, Pr=1.0, bc=(0, 0, 0, 0),
                 flux_variant=64, geno_variant=0, grad_base=0, precision=FP64, tau_c1=0.0, tau_c2=0.0,
                 stream=None, recon_vars=0):
@@ -273,9 +282,8 @@ class Solver:
 
     def __init__(self, params):
         lib = load()
+        params = _on_current_stream(params)
         self._p = params
-        if params.stream is None:
-            params.stream = _stream().value
         h = _VP()
         _check(lib.fdcgks_create(ctypes.byref(params), ctypes.byref(h)))
         self._h = h
@@ -412,8 +420,7 @@ def iface_batch(params, normal, dt, inp, out=None):
     n = inp.shape[0]
     if out is None:
         out = torch.empty((n, 24), dtype=torch.float64, device=inp.device)
-    if params.stream is None:
-        params.stream = _stream().value
+    params = _on_current_stream(params)
     _check(load().fdcgks_iface_batch(ctypes.byref(params), int(normal), ctypes.c_double(dt), n,
                                      _dptr(inp, 20 * n), _dptr(out, 24 * n)))
     return out
@@ -425,8 +432,7 @@ def nodal_batch(params, dt, inp, out=None):
     n = inp.shape[0]
     if out is None:
         out = torch.empty((n, 16), dtype=torch.float64, device=inp.device)
-    if params.stream is None:
-        params.stream = _stream().value
+    params = _on_current_stream(params)
     _check(load().fdcgks_nodal_batch(ctypes.byref(params), ctypes.c_double(dt), n, _dptr(inp, 12 * n),
                                      _dptr(out, 16 * n)))
     return out
@@ -438,8 +444,7 @@ def recon_batch(params, kind, h, inp, out=None):
     n = inp.shape[0]
     if out is None:
         out = torch.empty((n, 6), dtype=torch.float64, device=inp.device)
-    if params.stream is None:
-        params.stream = _stream().value
+    params = _on_current_stream(params)
     _check(load().fdcgks_recon_batch(ctypes.byref(params), int(kind), ctypes.c_double(h), n,
                                      _dptr(inp, (8 if kind == 0 else 6) * n), _dptr(out, 6 * n)))
     return out
@@ -448,16 +453,19 @@ def recon_batch(params, kind, h, inp, out=None):
 def cfl_dt_noalloc(params, Wp, Wd, cfl):
     """CFL time step from caller-owned device arrays without any allocation.
 
-    For callers that cannot allocate device memory when they need a time step
-    (stream capture in progress, a fixed memory budget, no allocation allowed in
-    the loop).  Wp: [4, ny, nx], Wd: [4, nyd, nxd] contiguous float64 CUDA
-    tensors.  The library keeps the partial maxima in a fixed device array
-    shared by all calls; calls that overlap on the GPU race on it.  The first
-    call on a device looks up that array's address, so make it before any
-    stream capture.
+    For callers that cannot allocate device memory when they need a time step:
+    an application that hands this library a fixed share of the GPU's memory
+    and forbids further allocations, or a time loop that must not risk an
+    allocation failure or the synchronisation that cudaMalloc and cudaFree can
+    cause.  Wp: [4, ny, nx], Wd: [4, nyd, nxd] contiguous float64 CUDA
+    tensors.  The call synchronizes the stream to return dt to the host.  The
+    library keeps the partial maxima in a fixed device array shared by all
+    calls; calls that overlap on the GPU race on it.  The first call on a
+    device looks up that array's address, so make it before any stream
+    capture.  params is not modified (an unset stream means torch's current
+    stream for this call).
     """
-    if params.stream is None:
-        params.stream = _stream().value
+    params = _on_current_stream(params)
     nxd = params.nx + (0 if params.bc[0] == BC_PERIODIC else 1)
     nyd = params.ny + (0 if params.bc[2] == BC_PERIODIC else 1)
     out = ctypes.c_double()
@@ -612,9 +620,8 @@ class Lines:
 
     def __init__(self, params):
         lib = load()
+        params = _on_current_stream(params)
         self._p = params
-        if params.stream is None:
-            params.stream = _stream().value
         h = _VP()
         _lcheck(lib.fdcgks_line_create(ctypes.byref(params), ctypes.byref(h)), None)
         self._h = h

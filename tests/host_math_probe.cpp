@@ -1,10 +1,9 @@
 // Host instantiation of the device arithmetic in fdcgks_math.cuh.
 //
-// Instrumentation only: lets the CPU test suite check the kernels' formulas
-// (reconstruction, kinetic interface solve, nodal flux) against the oracle
-// without a GPU, and is the base of the operation-counting build.  The
-// library and its Python binding never call it; the product path runs only
-// in the CUDA kernels.
+// Test instrumentation only: lets the CPU test suite check the kernels'
+// formulas (reconstruction, kinetic interface solve, nodal flux) against the
+// oracle without a GPU.  The library and its Python binding never call it;
+// the product path runs only in the CUDA kernels.
 #include <cmath>
 
 #include "fdcgks_math.cuh"

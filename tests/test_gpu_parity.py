@@ -82,6 +82,10 @@ def test_reconstruction_matches_oracle(variant):
     ref = np.array([np.concatenate([oracle.recon_left(variant, Q[t], Qx[t, :3], h),
                                     oracle.recon_right(variant, Q[t], Qx[t, 1:], h)]) for t in range(n)])
     np.testing.assert_allclose(out, ref, rtol=1e-12, atol=1e-12)
+    if variant != 2:
+        # the path function is compared inside its intermediate regime too, not only at its limits
+        chi = np.concatenate([ref[:, 2], ref[:, 5]])
+        assert ((chi > 0.01) & (chi < 0.99)).sum() >= 100
     inp = torch.from_numpy(np.ascontiguousarray(np.concatenate([Q[:, :3], Qx[:, :3]], 1))).cuda()
     out = fdcgks.recon_batch(prm, 1, h, inp).cpu().numpy()[:, 0]
     ref = np.array([oracle.recon_node(variant, Q[t, :3], Qx[t, :3], h)[0] for t in range(n)])

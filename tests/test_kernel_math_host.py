@@ -22,7 +22,7 @@ D = ctypes.POINTER(ctypes.c_double)
 def probe(tmp_path_factory):
     out = str(tmp_path_factory.mktemp("probe") / "libprobe.so")
     subprocess.run(["g++", "-std=c++17", "-O2", "-fPIC", "-shared", "-I", CSRC, "-o", out,
-                    os.path.join(CSRC, "host_math_probe.cpp")], check=True)
+                    os.path.join(os.path.dirname(os.path.abspath(__file__)), "host_math_probe.cpp")], check=True)
     return ctypes.CDLL(out)
 
 

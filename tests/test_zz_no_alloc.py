@@ -1,11 +1,14 @@
 """The allocation-free CFL entry point against the context-based one.
 
 fdcgks_cfl_dt_noalloc serves callers that cannot allocate device memory when
-they need a time step (a stream being captured, a fixed memory budget, a loop
-that must not allocate); it keeps its partial maxima in a fixed device array
-of the library.  Its result must equal fdcgks_cfl_dt's on the same state, on
-consecutive calls (the shared array keeps the previous call's contents), and
-grids beyond its stated limit must be refused.  This file is collected last.
+they need a time step (an application that gives the library a fixed share of
+the GPU's memory, a time loop that must not risk an allocation failure or the
+synchronisation of cudaMalloc/cudaFree); it keeps its partial maxima in a fixed
+device array of the library.  Its result must equal fdcgks_cfl_dt's on the
+same state, on consecutive calls (the shared array keeps the previous call's
+contents: a larger rate or more tiles left by one call must not reach the
+next), and grids beyond its stated limit must be refused.  This file is
+collected last.
 """
 import numpy as np
 import pytest
@@ -36,12 +39,28 @@ def test_noalloc_cfl_equals_context_cfl_on_consecutive_calls(name):
     S2[0][1] *= 1.5
     S2[0][3] += 0.5 * (S2[0][1] ** 2 - S[0][1] ** 2) / S2[0][0]
     params = fdcgks.params_for_case(case)
-    for state in (S, S, S2, S2):
+    # S2 has the larger wave rate: run it both before and after S
+    for state in (S, S, S2, S2, S, S2, S):
         ref = _context_dt(case, state, cfl)
         Wp = torch.from_numpy(state[0]).cuda()
         Wd = torch.from_numpy(state[2]).cuda()
         got = fdcgks.cfl_dt_noalloc(params, Wp, Wd, cfl)
         assert got == pytest.approx(ref, rel=1e-12)
+
+
+def test_noalloc_cfl_after_a_larger_grid():
+    """A multi-tile call with a fast state, then a one-tile call with a slow
+    one: the second must see neither the first's tiles nor its maxima."""
+    cfl = 0.4
+    big = inputs.vortex(96, strength=5.0)          # 2 * 96^2 nodes: 5 tiles
+    small = inputs.vortex(16, strength=1.0)        # 512 nodes: 1 tile
+    Sb, Ss = big.initial_state(), small.initial_state()
+    Sb[0][1] *= 3.0                                # faster flow in the big grid
+    Sb[0][3] += 0.5 * (Sb[0][1] ** 2 - (Sb[0][1] / 3.0) ** 2) / Sb[0][0]
+    pb, ps = fdcgks.params_for_case(big), fdcgks.params_for_case(small)
+    for case, S, prm in ((big, Sb, pb), (small, Ss, ps), (big, Sb, pb), (small, Ss, ps)):
+        got = fdcgks.cfl_dt_noalloc(prm, torch.from_numpy(S[0]).cuda(), torch.from_numpy(S[2]).cuda(), cfl)
+        assert got == pytest.approx(_context_dt(case, S, cfl), rel=1e-12)
 
 
 def test_noalloc_cfl_rejects_grids_beyond_its_limit():
