@@ -7,11 +7,18 @@ primary nodes (plus 1024^2 dual nodes), strength 5 at (5,5), free stream
 A step is one full S2O4 step (two stages) of both grids; a node update is
 one step of one primary or dual node (2 * 1024^2 per step).
 
-Prints one JSON line.  `value` is the FP64 path's node-updates/s with the
-state resident in HBM (all N ranks together); the mixed FP32/FP64 path is
-reported beside it with its L1 error against the FP64 path.  `e2e` is the
-same metric through the C ABI with host state: every step copies the state
-in from pinned host memory, steps, and copies it back out.
+Prints one JSON line, kept short (the figures that explain it are in the
+`--detail` file).  `value` is the FP64 path's node-updates/s with the state
+resident in HBM (all N ranks together); `mixed` is the mixed FP32/FP64 path
+on the same workload with its error against the FP64 path; `err_vs_oracle`
+states the error of both paths against the FP64 CPU oracle on oracle-sized
+samples of the vortex, the viscous shock tube and an ensemble member (those
+oracle runs are the CPU-baseline leg, timed as `cpu_baseline`).  `e2e` is the
+same metric through the C ABI with host state: every step copies the state in
+from pinned host memory, steps, and copies it back out.  `roofline` is the
+dominant kernel's; `kernel_frac` gives every kernel's fraction of its bound
+(FP64 / FP32 FMA pipe peaks measured in this run by csrc/pipe_peak.cu, HBM
+copy bandwidth from the driver's measurement).
 
 --impl reference times the CPU oracle (the plain FP64 C++ implementation
 the tests compare against) on a bounded sample of the same workload.
@@ -31,36 +38,66 @@ if ROOT not in sys.path:
 
 METRIC = "2D node-updates/s, FP64 vs mixed-FP32 at stated L1 error; % of roofline"
 UNIT = "node-updates/s"
-# FP64 peak derived from unit counts and clocks: 152 SMs x 4 FP64 flop/clk/SM
-# (2 DFMA per clock per SM on GB300) x 2.07 GHz maximum SM clock
-FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
-# FP32: 152 SMs x 128 lanes x 2 flop/FMA x 2.07 GHz
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# derived peaks, for context beside the measured ones: 152 SMs x 4 FP64
+# flop/clk (2 DFMA per clock per SM) x 2.07 GHz; 152 x 128 FP32 lanes x 2 x 2.07 GHz
+FP64_DERIVED_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+FP32_DERIVED_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+HBM_FALLBACK_GBS = 6800.0
 
 
 def kernel_hash():
-    """Hash of the kernel sources; profiles/ summaries record the hash they were taken on."""
+    """Hash of the kernel sources; profiles/dram_traffic.json records the hash
+    its counters were taken on."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("fdcgks_math.cuh", "fdcgks_kernels.cuh", "fdcgks_internal.cuh"):
+    for f in ("fdcgks_math.cuh", "fdcgks_kernels.cuh", "fdcgks_internal.cuh", "fdcgks_api.cu"):
         with open(os.path.join(ROOT, "paper_2606_17772_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(name, n):
-    """DRAM bytes per launch from a committed ncu summary, if it matches this
-    kernel source and grid (otherwise None)."""
-    path = os.path.join(ROOT, "profiles", name)
-    if n != 1024 or not os.path.exists(path):
+def profiled_traffic(kernel, n):
+    """DRAM bytes per launch of `kernel` at n^2 from profiles/dram_traffic.json
+    (ncu dram__bytes_read.sum + dram__bytes_write.sum), if it was taken on
+    this kernel source at this grid; otherwise None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(path):
         return None
-    text = open(path).read()
-    if "kernel_hash: " + kernel_hash() not in text:
+    with open(path) as fh:
+        rec = json.load(fh)
+    if rec.get("kernel_hash") != kernel_hash():
         return None
-    for line in text.splitlines():
-        if line.startswith("traffic_bytes_per_launch:"):
-            return int(line.split(":")[1])
-    return None
+    ent = rec.get("kernels", {}).get(kernel)
+    if not ent or ent.get("n") != n:
+        return None
+    return ent.get("bytes_per_launch")
+
+
+def hbm_peak():
+    """Measured copy bandwidth (GB/s) from MEASURED_PEAKS.json, else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            v = float(json.load(fh)["hbm_gbs"])
+        return v, "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback 6.8 TB/s"
+
+
+def pipe_peaks():
+    """FP64 and FP32 FMA-pipe peaks (TFLOP/s) measured now on this GPU by
+    csrc/pipe_peak.cu: chains of independent FMAs over all SMs, best of 5."""
+    import ctypes
+    from paper_2606_17772_gb300 import build as fbuild
+    lib = ctypes.CDLL(fbuild.build_pipe_peak())
+    out = {}
+    for name, prec, iters in (("fp64", 0, 1000), ("fp32", 1, 40000)):
+        tf, ms = ctypes.c_double(), ctypes.c_double()
+        rc = lib.pipe_peak_tflops(prec, 8, iters, 5, ctypes.byref(tf), ctypes.byref(ms))
+        if rc != 0:
+            raise RuntimeError("pipe peak measurement failed (%d)" % rc)
+        out[name] = tf.value
+    return out
 
 
 def parse():
@@ -71,6 +108,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1024, help="primary nodes per direction")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-peaks", action="store_true", help="derived pipe peaks instead of measured (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
@@ -87,6 +125,7 @@ def parse():
     ap.add_argument("--adj-steps", type=int, default=20, help="steps of the adjoint window")
     ap.add_argument("--ensemble-only", action="store_true",
                     help="run only the ensemble workload and print its object (profiling runs)")
+    ap.add_argument("--detail", default=None, help="also write every measured figure to this JSON file")
     return ap.parse_args()
 
 
@@ -290,7 +329,7 @@ def timed_steps(solver, dt, steps, warmup, world, device_index, sample_clocks):
     return ms, prof_ms, prof_n, launches1 - launches0, clocks
 
 
-def run_ensemble(args, world, rank, local):
+def run_ensemble(args, world, rank, local, peaks=None):
     """Batched ensemble workload: seeded periodic isentropic vortices on uneven
     grids (N log-uniform in [32, 512], strength U[1, 5], centre uniform),
     mixed precision, every member taking its own CFL-0.2 step each step,
@@ -337,6 +376,8 @@ def run_ensemble(args, world, rank, local):
         pt_flops = 2 * npts * (cnt["point_stage1"]["fp32"] + cnt["point_stage2"]["fp32"])
         pt_ms = phases["points"] / 3
         ach = pt_flops / (pt_ms / 1e3) / 1e12
+        p32 = peaks["fp32"] if peaks else FP32_DERIVED_TFLOPS
+        p32_src = "measured FP32 FMA pipe peak (csrc/pipe_peak.cu)" if peaks else "derived"
     sizes = sorted(c.nx for c in cases)
     return {
         "value": nodes * args.ens_steps * world / (ms / 1e3), "unit": UNIT, "dtype": "f32+f64",
@@ -353,9 +394,9 @@ def run_ensemble(args, world, rank, local):
         "tune": {"seconds": tune_s, "best_ms_per_step": tune_ms},
         "phase_ms_per_step": {k: v / 3 for k, v in phases.items()},
         "members_time_range": [float(t.min()), float(t.max())], "members_flagged": int((st != 0).sum()),
-        "roofline": {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": ach / FP32_PEAK_TFLOPS, "kernel": "ens_phase_kernel<float, points>",
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "traffic": None},
+        "roofline": {"bound": "alu", "achieved": ach, "peak": p32, "unit": "TFLOP/s",
+                     "frac": ach / p32, "kernel": "ens_phase_kernel<float, points>",
+                     "peak_source": p32_src, "traffic": None},
         "clocks": clocks, "gpu_launches": launches * world,
     }
 
@@ -583,6 +624,148 @@ def run_adjoint(args, world):
     return out
 
 
+GH = 3   # ghost layers of every state plane
+
+
+def kernel_work(case, cnt, precision):
+    """Algorithmic work of one full step (both stages) per kernel class:
+    (FP64 flops, FP32 flops, bytes).  Units are the grid's own nodes and
+    interface points (the kernels' extra halo units are not counted); bytes
+    count each value a kernel must read or write once (r = 8 B FP64, 4 B for
+    the mixed path's FP32 arrays and float-float halves):
+      points  reads W and the line's averaged gradient of both grids (16 r),
+              writes 25 values per solve at stage 1, 13 at stage 2;
+      nodal   reads W and both gradients (12 r), writes F, G, F_t, G_t (16 r);
+      update  stage 1 reads 25 + 25 point values, 16 nodal fluxes and W^n,
+              writes the stage state (12), the S2O4 accumulator (4) and the
+              gradient base (8); stage 2 reads 13 + 13, 8, the accumulator and
+              base, writes the state (12) (float-float pairs count both halves);
+      ghost   3 ghost layers of 12 fields of both grids, read and write;
+      cfl     4 conservative fields of every node (FP64, or both halves)."""
+    r = 8 if precision == 0 else 4
+    nodes = case.nx * case.ny + case.nxd * case.nyd
+    pts = case.nx * case.nyd + case.nxd * case.ny
+    def fl(name):
+        c = cnt[name]
+        return c["fp64"], c["fp32"]
+    p1, p2 = fl("point_stage1"), fl("point_stage2")
+    nd = fl("node")
+    u1, u2 = fl("update_stage1"), fl("update_stage2")
+    # FP64: stage 1 reads 50 + 16 + 4, writes 24; stage 2 reads 26 + 8 + 4 + 8, writes 12.
+    # mixed: stage 1 reads 66 floats and the W^n pairs (8), writes the stage state's high
+    # parts (12) and the accumulator and base pairs (24); stage 2 reads 34 floats and
+    # those pairs (24), writes the state pairs (24)
+    upd_bytes = (94 + 58) * 8 if precision == 0 else ((66 + 8 + 36) + (34 + 24 + 24)) * 4
+    ghosts = sum(2 * GH * ny + 2 * GH * (nx + 2 * GH) for nx, ny in ((case.nx, case.ny), (case.nxd, case.nyd)))
+    work = {
+        "points": (pts * (p1[0] + p2[0]), pts * (p1[1] + p2[1]), pts * (16 + 50 + 16 + 26) * r),
+        "nodal": (2 * nodes * nd[0], 2 * nodes * nd[1], 2 * nodes * 28 * r),
+        "update": (nodes * (u1[0] + u2[0]), nodes * (u1[1] + u2[1]), nodes * upd_bytes),
+        "ghost": (0.0, 0.0, 2 * ghosts * 12 * 2 * r),
+        "cfl": (0.0, 0.0, nodes * 32.0),
+    }
+    return work
+
+
+def kernel_fractions(work, ms_total, n_groups, steps_equiv, peaks, hbm_gbs):
+    """Per kernel class: time per launch group, and the fraction of its
+    roofline: ALU time at the measured FP64/FP32 pipe peaks (the two added)
+    and byte time at the HBM copy bandwidth, each over the measured time; the
+    larger names the bound."""
+    out = {}
+    for k, (f64, f32, b) in work.items():
+        t = ms_total.get(k, 0.0) / 1e3
+        if t <= 0:
+            continue
+        units = steps_equiv[k]
+        alu = units * (f64 / (peaks["fp64"] * 1e12) + f32 / (peaks["fp32"] * 1e12)) / t
+        mem = units * b / (hbm_gbs * 1e9) / t
+        out[k] = {"ms_per_launch_group": 1e3 * t / max(n_groups.get(k, 1), 1),
+                  "bound": "alu" if alu >= mem else "hbm", "frac": max(alu, mem), "alu_frac": alu, "hbm_frac": mem,
+                  "achieved_tflops": units * (f64 + f32) / t / 1e12, "achieved_gbs": units * b / t / 1e9}
+    return out
+
+
+def rho_errors(got, ref):
+    """L1 (mean |e| / mean |rho|) and L-infinity (max |e| / max |rho|) of the
+    density over the nodes of both grids."""
+    import numpy as np
+    a = np.concatenate([got[0][0].ravel(), got[2][0].ravel()])
+    b = np.concatenate([ref[0][0].ravel(), ref[2][0].ravel()])
+    return [float(np.abs(a - b).mean() / np.abs(b).mean()), float(np.abs(a - b).max() / np.abs(b).max())]
+
+
+def cpu_baseline_leg(args):
+    """The CPU-baseline leg: the oracle as it stands, single thread, on
+    oracle-sized samples of the bench's workloads (timed: the baseline), and
+    the same samples on the GPU in FP64 and mixed precision, so that each
+    path's error against the FP64 oracle is stated per workload."""
+    import numpy as np
+    import oracle
+    import torch
+    from paper_2606_17772_gb300 import fdcgks, inputs
+
+    def gpu(case, dts, precision):
+        with fdcgks.Solver.from_case(case, precision) as s:
+            s.set_state(*case.initial_state())
+            for dt in dts:
+                s.step(dt)
+            out = s.get_state(device=False)
+            return out, bool(s.check())
+
+    warm = inputs.vortex(16)            # load the library outside the timing
+    oracle.steps(oracle.make_params(**warm.oracle_kwargs()), 0.01, 1, *warm.initial_state())
+    res, timing = {}, {}
+    # isentropic vortex (bench constants), fixed CFL-0.2 step from the initial state
+    v = inputs.vortex(64)
+    pv = oracle.make_params(**v.oracle_kwargs())
+    S = v.initial_state()
+    nv = 20
+    dt = oracle.cfl_dt(pv, 0.2, S[0], S[2])
+    t0 = time.perf_counter()
+    ref = oracle.steps(pv, dt, nv, *S)
+    el = time.perf_counter() - t0
+    timing["vortex"] = ((v.nx * v.ny + v.nxd * v.nyd) * nv, el)
+    for name, prec in (("fp64", fdcgks.FP64), ("mixed", fdcgks.MIXED)):
+        got, bad = gpu(v, [dt] * nv, prec)
+        res.setdefault("vortex64", {})[name] = rho_errors(got, ref)
+    # viscous shock tube (Sec. 5.8 constants, no-slip walls): the oracle's own CFL-0.4 steps
+    tb = inputs.viscous_shock_tube(40, 20)
+    pt = oracle.make_params(**tb.oracle_kwargs())
+    S = tb.initial_state()
+    dts = []
+    t0 = time.perf_counter()
+    for _ in range(20):
+        dts.append(oracle.cfl_dt(pt, 0.4, S[0], S[2]))
+        S = oracle.steps(pt, dts[-1], 1, *S)
+    timing["tube"] = ((tb.nx * tb.ny + tb.nxd * tb.nyd) * 20, time.perf_counter() - t0)
+    for name, prec in (("fp64", fdcgks.FP64), ("mixed", fdcgks.MIXED)):
+        got, bad = gpu(tb, dts, prec)
+        res.setdefault("tube40x20", {})[name] = rho_errors(got, S)
+    # smallest member of the bench ensemble, through the ensemble (mixed) path
+    cases = inputs.ensemble_members(count=args.ens_members, seed=0, nmax=args.ens_nmax)
+    m = min(cases, key=lambda c: c.nx)
+    pm = oracle.make_params(**m.oracle_kwargs())
+    S = m.initial_state()
+    dt = oracle.cfl_dt(pm, 0.2, S[0], S[2])
+    t0 = time.perf_counter()
+    ref = oracle.steps(pm, dt, 20, *S)
+    timing["member"] = ((m.nx * m.ny + m.nxd * m.nyd) * 20, time.perf_counter() - t0)
+    with fdcgks.Ensemble.from_cases([m], fdcgks.MIXED) as ens:
+        ens.set_state(0, *m.initial_state())
+        ens.run(20, dt=[dt])
+        ens.synchronize()
+        got = ens.get_state(0, device=False)
+    res["member%d" % m.nx] = {"mixed": rho_errors(got, ref)}
+    torch.cuda.synchronize()
+    units, secs = timing["vortex"]
+    base = {"value": units / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "isentropic vortex 64^2 (+dual), 20 steps, %.1f s, single thread" % secs,
+            "sample_short": "vortex 64^2 x20",
+            "other_samples": {k: {"value": u / t, "seconds": t} for k, (u, t) in timing.items() if k != "vortex"}}
+    return base, res
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -599,6 +782,8 @@ def main():
         if rank == 0:
             print(json.dumps({"metric": METRIC, "ensemble": ens}), flush=True)
         return 0
+    peaks = pipe_peaks() if not args.no_peaks else {"fp64": FP64_DERIVED_TFLOPS, "fp32": FP32_DERIVED_TFLOPS}
+    hbm, hbm_src = hbm_peak()
     n = args.n
     case = inputs.vortex(n)
     S_host = case.initial_state()
@@ -616,63 +801,61 @@ def main():
                                                         sample_clocks=(name == "fp64" and rank == 0))
             out = s.get_state()
             assert not s.check(), "non-physical state during the benchmark"
+            # the CFL reduction, timed apart (it is not part of a fixed-dt step)
+            s.set_profiling(True)
+            for _ in range(5):
+                s.cfl_dt(0.2)
+            cms, cn, _ = s.get_profile()
+            s.set_profiling(False)
+            pms["cfl"], pn["cfl"] = cms["cfl"], cn["cfl"]
         ms_max = max_over_ranks(ms, world)
-        results[name] = dict(ms=ms_max, prof_ms=pms, prof_n=pn, launches=launches, clocks=clocks, dt=dt,
-                             state=[t.cpu().numpy() for t in out] if rank == 0 else None)
+        cnt = flops.step_counts(case, S_host, dt, precision=0 if name == "fp64" else 1)
+        work = kernel_work(case, cnt, 0 if name == "fp64" else 1)
+        equiv = {k: args.steps for k in ("points", "nodal", "update", "ghost")}
+        equiv["cfl"] = 5
+        kf = kernel_fractions(work, pms, pn, equiv, peaks, hbm)
+        results[name] = dict(ms=ms_max, prof_ms=pms, prof_n=pn, launches=launches, clocks=clocks, dt=dt, cnt=cnt,
+                             kernels=kf, state=[t.cpu().numpy() for t in out] if rank == 0 else None)
 
     fp = results["fp64"]
     value = nodes * args.steps * world / (fp["ms"] / 1e3)
+    wset = nodes * 8 * (24 + 24 + 12) / 1e9 + nodes * 8 * 66 / 1e9
+    step_ms = {k: v for k, v in fp["prof_ms"].items() if k != "cfl"}
+    pk = fp["kernels"]["points"]
+    roof = {"bound": "alu", "achieved": pk["achieved_tflops"], "peak": peaks["fp64"], "unit": "TFLOP/s",
+            "frac": pk["alu_frac"], "traffic": profiled_traffic("point_kernel<double>", n),
+            "kernel": "point_kernel<double> (Type A + B interface points)",
+            "peak_source": "measured FP64 FMA pipe (csrc/pipe_peak.cu), this run",
+            "step_share": step_ms["points"] / max(sum(step_ms.values()), 1e-9)}
 
-    # roofline of the dominant kernel class (the interface-point kernels), FP64 pipe
-    cnt = flops.step_counts(case, S_host, fp["dt"], precision=0)
-    pt_flops = 2 * n * n * (cnt["point_stage1"]["fp64"] + cnt["point_stage2"]["fp64"]) / 2   # per launch group
-    pt_ms = fp["prof_ms"]["points"] / max(fp["prof_n"]["points"], 1)
-    achieved = pt_flops / (pt_ms / 1e3) / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS,
-            "traffic": profiled_traffic("point_kernel_fp64_vortex1024.md", n),
-            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch (profiles/)",
-            "kernel": "point_kernel (Type A + Type B interface points, FP64)",
-            "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
-            "step_share": fp["prof_ms"]["points"] / max(sum(fp["prof_ms"].values()), 1e-9),
-            "flops_per_node_update": cnt["per_node_update_total"]["fp64"],
-            "step_achieved_tflops": cnt["per_node_update_total"]["fp64"] * nodes * args.steps / (fp["ms"] / 1e3) / 1e12}
-
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    full = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": fp["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "isentropic vortex %d^2 primary + %d^2 dual, periodic [0,10]^2, strength 5, "
-                                   "FD-CGKS(6-4), GENO (App. D constants), CFL 0.2" % (n, n),
-                       "grid": [n, n], "node_updates_per_step": nodes,
-                       "primary_node_updates_per_step": n * n, "parallelism": "replicas",
-                       "l2": "working set %.2f GB > 129 MB L2 (no flush needed)" %
-                             (nodes * 8 * (24 + 24 + 12) / 1e9 + nodes * 8 * 66 / 1e9)},
+            "config": {"workload": "isentropic vortex %d^2 (+%d^2 dual), periodic [0,10]^2, strength 5, "
+                                   "FD-CGKS(6-4), GENO App. D, CFL 0.2" % (n, n),
+                       "workload_short": "isentropic vortex %d^2+dual, FD-CGKS(6-4), App.D GENO, CFL 0.2" % n,
+                       "l2": "working set %.1f GB > 129 MB L2, no flush" % wset,
+                       "l2_short": "%.1f GB > L2, no flush" % wset},
             "roofline": roof, "clocks": fp["clocks"], "gpu_launches": fp["launches"] * world,
-            "primary_node_updates_per_s": value * n * n / nodes}
+            "peaks": {"fp64_tflops": peaks["fp64"], "fp32_tflops": peaks["fp32"], "hbm_gbs": hbm,
+                      "hbm_source": hbm_src, "fp64_derived": FP64_DERIVED_TFLOPS,
+                      "fp32_derived": FP32_DERIVED_TFLOPS},
+            "kernels": {"fp64": fp["kernels"]},
+            "flops_per_node_update": {"fp64": fp["cnt"]["per_node_update_total"]}}
 
     if "mixed" in results:
         mx = results["mixed"]
         mval = nodes * args.steps * world / (mx["ms"] / 1e3)
-        mcnt = flops.step_counts(case, S_host, mx["dt"], precision=1)
-        mpt = 2 * n * n * (mcnt["point_stage1"]["fp32"] + mcnt["point_stage2"]["fp32"]) / 2
-        mpt_ms = mx["prof_ms"]["points"] / max(mx["prof_n"]["points"], 1)
-        mach = mpt / (mpt_ms / 1e3) / 1e12
         err = None
         if rank == 0:
-            a, b = mx["state"][0], fp["state"][0]
-            err = {"L1_rel_rho_vs_fp64": float(np.abs(a[0] - b[0]).mean() / np.abs(b[0]).mean()),
-                   "Linf_rel_rho_vs_fp64": float(np.abs(a[0] - b[0]).max() / np.abs(b[0]).max()),
-                   "after_steps": args.warmup + args.steps}
-        line["mixed"] = {"value": mval, "unit": UNIT, "dtype": "f32+f64", "ms_per_step": mx["ms"] / args.steps,
-                         "primary_node_updates_per_s": mval * n * n / nodes,
-                         "error": err,
-                         "roofline": {"bound": "alu", "achieved": mach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                                      "frac": mach / FP32_PEAK_TFLOPS,
-                                      "kernel": "point_kernel (FP32 arithmetic, FP64 time coefficients)",
-                                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                                      "fp64_flops_per_node_update": mcnt["per_node_update_total"]["fp64"],
-                                      "fp32_flops_per_node_update": mcnt["per_node_update_total"]["fp32"]},
-                         "gpu_launches": mx["launches"] * world}
+            a, b = mx["state"], fp["state"]
+            err = {"rho_L1_Linf": rho_errors(a, b), "after_steps": args.warmup + args.steps}
+        mk = mx["kernels"]["points"]
+        full["mixed"] = {"value": mval, "unit": UNIT, "dtype": "f32+f64", "ms_per_step": mx["ms"] / args.steps,
+                         "err_vs_fp64_gpu": err, "points_frac": mk["alu_frac"],
+                         "points_tflops": mk["achieved_tflops"], "gpu_launches": mx["launches"] * world}
+        full["kernels"]["mixed"] = mx["kernels"]
+        full["flops_per_node_update"]["mixed"] = mx["cnt"]["per_node_update_total"]
 
     if not args.no_e2e:
         # end to end through the C ABI with host state in pinned memory
@@ -695,42 +878,101 @@ def main():
             torch.cuda.synchronize()
             el = max_over_ranks(time.perf_counter() - t0, world)
         nbytes = sum(t.numel() * 8 for t in pin)
-        line["e2e"] = {"value": nodes * args.steps * world / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-                       "d2h_bytes_per_step": nbytes, "ms_per_step": 1e3 * el / args.steps,
-                       "path": "fdcgks_set_state(host pinned) + fdcgks_step + fdcgks_get_state(host pinned)"}
+        full["e2e"] = {"value": nodes * args.steps * world / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                       "d2h_bytes_per_step": nbytes, "ms_per_step": 1e3 * el / args.steps}
 
     if not args.no_ensemble:
-        line["ensemble"] = run_ensemble(args, world, rank, local)
+        full["ensemble"] = run_ensemble(args, world, rank, local, peaks)
     if not args.no_viscous_tube:
-        line["viscous_tube"] = run_viscous_tube(args, world)
+        full["viscous_tube"] = run_viscous_tube(args, world)
     if not args.no_double_mach:
-        line["double_mach"] = run_double_mach(args, world)
+        full["double_mach"] = run_double_mach(args, world)
     if not args.no_lines:
-        line["lines_1d"] = run_lines(args, world)
+        full["lines_1d"] = run_lines(args, world)
     if not args.no_adjoint:
-        line["adjoint"] = run_adjoint(args, world)
+        full["adjoint"] = run_adjoint(args, world)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ns, nst = 128, 2
-        rate, el = oracle_rate(ns, nst)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": "isentropic vortex %d^2 (+dual), %d steps, %.1f s, single thread" %
-                                          (ns, nst, el)}
-        ns_all = 64
+        base, errs = cpu_baseline_leg(args)
+        full["cpu_baseline"] = base
+        full["err_vs_oracle"] = errs
         try:
-            arate, wall, ncores = oracle_rate_all_cores(ns_all, nst)
-            line["cpu_baseline"]["all_cores"] = {
+            arate, wall, ncores = oracle_rate_all_cores(64, 2)
+            full["cpu_baseline"]["all_cores"] = {
                 "value": arate, "unit": UNIT, "cores": ncores, "kind": "oracle",
-                "sample": "isentropic vortex %d^2 (+dual), %d steps, one independent copy per core, %.1f s wall" %
-                          (ns_all, nst, wall)}
+                "sample": "isentropic vortex 64^2 (+dual), 2 steps, one copy per core, %.1f s wall" % wall}
         except Exception as e:                   # the auxiliary leg never costs the line
-            line["cpu_baseline"]["all_cores"] = {"error": "%s: %s" % (type(e).__name__, e)}
+            full["cpu_baseline"]["all_cores"] = {"error": "%s: %s" % (type(e).__name__, e)}
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        if args.detail:
+            with open(args.detail, "w") as fh:
+                json.dump(full, fh, indent=1)
+        print(json.dumps(compact(full), separators=(",", ":")), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def _r(x, d=4):
+    """x rounded to d significant digits (JSON line length); large values as integers."""
+    if isinstance(x, float) and math.isfinite(x) and x != 0.0:
+        v = float("%.*g" % (d, x))
+        return int(v) if abs(v) >= 1e5 else v
+    return x
+
+
+def _rl(v):
+    return [_r(x, 3) for x in v]
+
+
+def compact(full):
+    """The printed line: the contract's keys and the figures the metric names,
+    rounded, in an order that puts the headline numbers first (every figure is
+    in the --detail file)."""
+    line = {k: full[k] for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                                 "higher_is_better", "scaling", "vs_baseline", "dtype", "data")}
+    line["value"], line["ms_per_step"] = _r(line["value"]), _r(line["ms_per_step"])
+    line["config"] = {"workload": full["config"]["workload_short"], "l2": full["config"]["l2_short"]}
+    ro = full["roofline"]
+    line["roofline"] = {"bound": ro["bound"], "achieved": _r(ro["achieved"]), "peak": _r(ro["peak"]),
+                        "unit": ro["unit"], "frac": _r(ro["frac"], 3), "traffic": ro["traffic"],
+                        "kernel": "points fp64"}
+    c = full.get("clocks") or {}
+    line["clocks"] = {"sm_mhz": c.get("sm_mhz"), "sm_max_mhz": c.get("sm_max_mhz"), "reasons": c.get("reasons")}
+    line["gpu_launches"] = full["gpu_launches"]
+    if "e2e" in full:
+        e = full["e2e"]
+        line["e2e"] = {"value": _r(e["value"]), "unit": e["unit"], "h2d_bytes_per_step": e["h2d_bytes_per_step"],
+                       "d2h_bytes_per_step": e["d2h_bytes_per_step"]}
+    if "mixed" in full:
+        m = full["mixed"]
+        line["mixed"] = {"value": _r(m["value"]), "frac": _r(m["points_frac"], 3),
+                         "err_fp64": _rl(m["err_vs_fp64_gpu"]["rho_L1_Linf"]) if m["err_vs_fp64_gpu"] else None}
+    if "err_vs_oracle" in full:
+        line["err_vs_oracle"] = {k: {p: _rl(v) for p, v in d.items()} for k, d in full["err_vs_oracle"].items()}
+    # per kernel class its fraction of its own bound, suffixed a (FP64/FP32 FMA
+    # pipe) or h (HBM bandwidth), e.g. "points 0.52a update 0.12h"
+    line["kernel_frac"] = {p: " ".join("%s %.2f%s" % (k, v["frac"], "h" if v["bound"] == "hbm" else "a")
+                                       for k, v in kk.items()) for p, kk in full["kernels"].items()}
+    pk = full["peaks"]
+    line["peaks"] = [_r(pk["fp64_tflops"], 3), _r(pk["fp32_tflops"], 3), _r(pk["hbm_gbs"], 4)]
+    if "ensemble" in full:
+        en = full["ensemble"]
+        line["ensemble"] = {"value": _r(en["value"]), "frac": _r(en["roofline"]["frac"], 3)}
+    if "viscous_tube" in full:
+        vt = full["viscous_tube"]
+        # [FP64 value, mixed value, every run physical]
+        line["viscous_tube"] = [_r(vt["fp64"]["value"], 3), _r(vt["mixed"]["value"], 3),
+                                not (vt["fp64"]["nonphysical"] or vt["mixed"]["nonphysical"])]
+    if "cpu_baseline" in full:
+        b = full["cpu_baseline"]
+        line["cpu_baseline"] = {"value": _r(b["value"]), "unit": b["unit"], "cores": b["cores"], "kind": b["kind"],
+                                "sample": b["sample_short"]}
+        ac = b.get("all_cores", {})
+        if "value" in ac:
+            line["cpu_baseline"]["all_cores"] = [_r(ac["value"]), ac["cores"]]
+    return line
 
 
 if __name__ == "__main__":

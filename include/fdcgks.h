@@ -156,12 +156,14 @@ fdcgks_status fdcgks_stage_operator(fdcgks_t ctx, double dt, double* Lp, double*
 
 /* Kernel-class timing: with profiling enabled, every stage records CUDA
  * events on the context stream around its ghost fill, nodal kernel, point
- * kernels (Type A and B) and update kernel.  fdcgks_get_profile waits for
+ * kernels (Type A and B) and update kernel, and fdcgks_cfl_dt /
+ * fdcgks_cfl_dt_sum around their reduction kernel (with the float-float to
+ * FP64 join of the state on mixed contexts).  fdcgks_get_profile waits for
  * the recorded events, returns the summed milliseconds and the number of
- * launch groups per class in ms[4] / count[4] (order: ghost, nodal, points,
- * update; either may be NULL), clears the record, and returns in *launches
- * (may be NULL) the total number of kernels the stepping path has launched
- * on this context. */
+ * launch groups per class in ms[5] / count[5] (order: ghost, nodal, points,
+ * update, cfl; either may be NULL), clears the record, and returns in
+ * *launches (may be NULL) the total number of kernels the stepping path has
+ * launched on this context. */
 fdcgks_status fdcgks_set_profiling(fdcgks_t ctx, int enable);
 fdcgks_status fdcgks_get_profile(fdcgks_t ctx, double* ms, int* count, long long* launches);
 

@@ -2,6 +2,8 @@
 
 Each translation unit is compiled by nvcc in parallel, then linked into one
 shared library.  No torch or Python types cross the library boundary.
+The benchmark's FMA-pipe peak measurement (csrc/pipe_peak.cu) is built as a
+separate small library, libpipepeak.so, beside it.
 """
 import concurrent.futures
 import os
@@ -70,5 +72,24 @@ def build(force=False, verbose=False, out_dir=None, defines=()):
     return lib
 
 
+PEAK_SRC = os.path.join(CSRC, "pipe_peak.cu")
+PEAK_LIB = os.path.join(OUT, "libpipepeak.so")
+
+
+def build_pipe_peak(force=False):
+    """Compile the FMA-pipe peak measurement used by the benchmark."""
+    if not force and os.path.exists(PEAK_LIB) and os.path.getmtime(PEAK_LIB) >= os.path.getmtime(PEAK_SRC):
+        return PEAK_LIB
+    os.makedirs(OUT, exist_ok=True)
+    tmp = PEAK_LIB + ".tmp.%d" % os.getpid()
+    cmd = [_nvcc()] + NVCC_FLAGS + ["-shared", PEAK_SRC, "-o", tmp, "-lcudart"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed for pipe_peak.cu:\n%s\n%s" % (r.stdout, r.stderr))
+    os.replace(tmp, PEAK_LIB)
+    return PEAK_LIB
+
+
 if __name__ == "__main__":
     print(build(force=True, verbose=True))
+    print(build_pipe_peak(force=True))

@@ -242,8 +242,20 @@ __device__ void cfl_rates_sum(double r, double ru, double rv, double E, double g
   numax = fmax(numax, mu * ir);
 }
 
-__global__ void cfl_kernel(const double* S, Layout L, double gamma, double mu, double ihx, double ihy, int sum,
-                           double* out) {
+// the state the CFL reduction reads: FP64 entries, or the mixed path's
+// float-float pairs joined in FP64 (no FP64 copy of the state is made)
+struct StateF64 {
+  const double* S;
+  __device__ double operator()(long k) const { return S[k]; }
+};
+struct StatePair {
+  const float* hi;
+  const float* lo;
+  __device__ double operator()(long k) const { return (double)hi[k] + (double)lo[k]; }
+};
+
+template <class ST>
+__global__ void cfl_kernel(ST S, Layout L, double gamma, double mu, double ihx, double ihy, int sum, double* out) {
   double rate = 0.0, numax = 0.0;
   const long n0 = (long)L.nx * L.ny, n1 = (long)L.nxd * L.nyd;
   for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n0 + n1; t += (long)gridDim.x * blockDim.x) {
@@ -251,14 +263,12 @@ __global__ void cfl_kernel(const double* S, Layout L, double gamma, double mu, d
     long q = g == 0 ? t : t - n0;
     int nxg = g == 0 ? L.nx : L.nxd;
     int i = (int)(q % nxg), j = (int)(q / nxg);
-    const double* Sg = S + (long)g * NFLD * L.plane;
-    const long c0 = cell(L, i, j);
+    const long c0 = (long)g * NFLD * L.plane + cell(L, i, j);
+    const double r = S(c0), ru = S(L.plane + c0), rv = S(2 * L.plane + c0), E = S(3 * L.plane + c0);
     if (sum)
-      cfl_rates_sum(Sg[c0], Sg[L.plane + c0], Sg[2 * L.plane + c0], Sg[3 * L.plane + c0], gamma, mu, ihx, ihy, rate,
-                    numax);
+      cfl_rates_sum(r, ru, rv, E, gamma, mu, ihx, ihy, rate, numax);
     else
-      cfl_rates(Sg[c0], Sg[L.plane + c0], Sg[2 * L.plane + c0], Sg[3 * L.plane + c0], gamma, mu, ihx, ihy, rate,
-                numax);
+      cfl_rates(r, ru, rv, E, gamma, mu, ihx, ihy, rate, numax);
   }
   // warp-shuffle max, then across warps in shared memory
   for (int o = 16; o > 0; o >>= 1) {
@@ -284,7 +294,7 @@ __global__ void cfl_kernel(const double* S, Layout L, double gamma, double mu, d
 // ---------------------------------------------------------------------------
 // optional timing of kernel classes (events recorded around each launch group)
 // ---------------------------------------------------------------------------
-enum { KC_GHOST = 0, KC_NODAL = 1, KC_POINTS = 2, KC_UPDATE = 3, KC_N = 4 };
+enum { KC_GHOST = 0, KC_NODAL = 1, KC_POINTS = 2, KC_UPDATE = 3, KC_CFL = 4, KC_N = 5 };
 
 static cudaError_t prof_mark(fdcgks_t c, int cls, bool begin) {
   if (!c->profiling) return cudaSuccess;
@@ -621,10 +631,15 @@ static fdcgks_status cfl_dt_impl(fdcgks_t c, double cfl, int sum, double* dt_out
   if (!c || !dt_out) return fail(c, FDCGKS_ERR_ARG, "NULL argument");
   if (!c->has_state) return fail(c, FDCGKS_ERR_STATE, "no state loaded");
   if (!(cfl > 0.0) || !std::isfinite(cfl)) return fail(c, FDCGKS_ERR_ARG, "cfl must be positive and finite");
-  CUDA_TRY(c, join_state(c));
-  cfl_kernel<<<c->red_blocks, 256, 0, c->stream>>>(c->S, c->L, c->p.gamma, c->p.mu, 1.0 / c->hx, 1.0 / c->hy, sum,
-                                                   c->red);
+  CUDA_TRY(c, prof_mark(c, KC_CFL, true));
+  if (c->Sf)
+    cfl_kernel<<<c->red_blocks, 256, 0, c->stream>>>(StatePair{c->Sf, c->Slo}, c->L, c->p.gamma, c->p.mu, 1.0 / c->hx,
+                                                     1.0 / c->hy, sum, c->red);
+  else
+    cfl_kernel<<<c->red_blocks, 256, 0, c->stream>>>(StateF64{c->S}, c->L, c->p.gamma, c->p.mu, 1.0 / c->hx,
+                                                     1.0 / c->hy, sum, c->red);
   CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, prof_mark(c, KC_CFL, false));
   double* h = new double[2 * c->red_blocks];
   cudaError_t e = cudaMemcpyAsync(h, c->red, sizeof(double) * 2 * c->red_blocks, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

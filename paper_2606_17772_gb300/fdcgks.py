@@ -376,12 +376,12 @@ class Solver:
         _check(load().fdcgks_set_profiling(self._h, int(bool(enable))), self._h)
 
     def get_profile(self):
-        """(ms per class, launch groups per class, total launches); classes: ghost, nodal, points, update."""
-        ms = (ctypes.c_double * 4)()
-        cn = (ctypes.c_int * 4)()
+        """(ms per class, launch groups per class, total launches); classes: ghost, nodal, points, update, cfl."""
+        ms = (ctypes.c_double * 5)()
+        cn = (ctypes.c_int * 5)()
         n = ctypes.c_longlong()
         _check(load().fdcgks_get_profile(self._h, ms, cn, ctypes.byref(n)), self._h)
-        names = ("ghost", "nodal", "points", "update")
+        names = ("ghost", "nodal", "points", "update", "cfl")
         return dict(zip(names, list(ms))), dict(zip(names, list(cn))), n.value
 
     def launches(self):

@@ -105,8 +105,10 @@ def step_counts(case, state, dt, precision=0, nsample=4000, seed=0):
     """Flops of one full S2O4 step, per node update and per point-kernel launch group.
 
     Returns a dict with 'per_node_update' (fp64 / fp32 kind dicts and totals),
-    'points_per_unit' (flops of one interface point, stage 1 and 2) and the
-    unit counts used.
+    'point_stage1' / 'point_stage2' (flops of one interface point), 'node'
+    (one node of the nodal kernel), 'update_stage1' / 'update_stage2' (one
+    node of the update kernel), each split into fp64 / fp32, and the unit
+    counts used.
     """
     rng = np.random.default_rng(seed)
     gas = (case.gamma, case.mu, case.Pr, case.tau_c1, case.tau_c2, dt)
@@ -161,6 +163,9 @@ def step_counts(case, state, dt, precision=0, nsample=4000, seed=0):
         "per_node_update_total": {p: _total(per_node[p]) for p in per_node},
         "point_stage1": {p: _total(point1[p]) for p in point1},
         "point_stage2": {p: _total(point2[p]) for p in point2},
+        "node": {p: _total(node[p]) for p in node},
+        "update_stage1": {p: _total(upd1[p]) for p in upd1},
+        "update_stage2": {p: _total(upd2[p]) for p in upd2},
         "units": {"recon_interface": rec_i, "recon_node": rec_n, "iface_solve": solve, "nodal_flux": nodal,
                   "compact_flux": cflux},
     }
