@@ -45,6 +45,22 @@
 #ifndef FDK_RECON_NOINLINE_F64
 #define FDK_RECON_NOINLINE_F64 1
 #endif
+// FDK_POINT_PAIR_F32 / _F64  1: two threads per interface point (one line and
+//                  one solve each, coupled by warp shuffles; point_pair_kernel),
+//                  0: one thread per point (point_kernel)
+// FDK_POINT_PAIR_MINB_F32 / _F64  minimum resident blocks per SM of the pair kernel
+#ifndef FDK_POINT_PAIR_F32
+#define FDK_POINT_PAIR_F32 1
+#endif
+#ifndef FDK_POINT_PAIR_F64
+#define FDK_POINT_PAIR_F64 0
+#endif
+#ifndef FDK_POINT_PAIR_MINB_F32
+#define FDK_POINT_PAIR_MINB_F32 4
+#endif
+#ifndef FDK_POINT_PAIR_MINB_F64
+#define FDK_POINT_PAIR_MINB_F64 1
+#endif
 
 namespace fdk {
 
@@ -54,12 +70,16 @@ template <> struct PointTune<double> {
   static constexpr int update_minb = 1;
   static constexpr int nodal_minb = 1;
   static constexpr bool noinline = FDK_SOLVE_NOINLINE_F64;
+  static constexpr bool pair = FDK_POINT_PAIR_F64;
+  static constexpr int pair_minb = FDK_POINT_PAIR_MINB_F64;
 };
 template <> struct PointTune<float> {
   static constexpr int minb = FDK_POINT_MINB_F32;
   static constexpr int update_minb = FDK_UPDATE_MINB_F32;
   static constexpr int nodal_minb = FDK_NODAL_MINB_F32;
   static constexpr bool noinline = FDK_SOLVE_NOINLINE_F32;
+  static constexpr bool pair = FDK_POINT_PAIR_F32;
+  static constexpr int pair_minb = FDK_POINT_PAIR_MINB_F32;
 };
 
 // interface reconstruction of one component, inlined or out of line (the
@@ -385,6 +405,77 @@ __global__ void __launch_bounds__(128, PointTune<R>::minb) point_kernel(KArgs<R>
 }
 
 // ---------------------------------------------------------------------------
+// The same point with two threads (lanes 2k and 2k + 1 of a warp): lane
+// parity l reconstructs line l and runs solve l (l = 0 the primary-grid solve
+// with normal TYPE, l = 1 the dual-grid solve).  What couples the two solves
+// of a point travels between the partner lanes by warp shuffles: the
+// tangential derivative of each solve (the mean of the other line's l/r
+// derivatives) and the other solve's quarter in W~ (Eq. eq:W-model-2d).
+// Each thread holds one line and one solve instead of two, so the solve runs
+// inline without a local-memory call frame; the arithmetic is point_compute's,
+// in the same order.  mask: the lanes of the warp that take part (pairs are
+// valid together).
+// ---------------------------------------------------------------------------
+template <class R, int TYPE, bool CHAR, class LD, class ST>
+__device__ __forceinline__ void point_compute_pair(const GenoK<R>& geno, const GasK<R>& gas, const R h[2],
+                                                   const R ih[2], bool wn, int l, unsigned mask, LD ld, ST st) {
+  const int n = l == 0 ? TYPE : 1 - TYPE;   // normal of this lane's solve
+  R lv[4], ldv[4], rv[4], rdv[4], chi;
+  if constexpr (CHAR)
+    recon_line_char(geno, gas.gm1, n, ld, l, h[n], ih[n], lv, ldv, rv, rdv, chi);
+  else
+    recon_line_ld(geno, ld, l, h[n], ih[n], lv, ldv, rv, rdv, chi);
+  R t[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) t[c] = R(0.5) * __shfl_xor_sync(mask, ldv[c] + rdv[c], 1);
+  IfaceOut<R> o;
+  iface_solve(gas, n, lv, rv, ldv, rdv, t, wn, o);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const R mt = R(0.25) * __shfl_xor_sync(mask, o.Wlt[c] + o.Wrt[c], 1);
+    st(PO_FT + c, o.Ft[c]);
+    st(PO_WLT + c, R(0.5) * o.Wlt[c] + mt);
+    st(PO_WRT + c, R(0.5) * o.Wrt[c] + mt);
+    if (wn) {
+      const R m = R(0.25) * __shfl_xor_sync(mask, o.Wl[c] + o.Wr[c], 1);
+      st(PO_F + c, o.F[c]);
+      st(PO_WL + c, R(0.5) * o.Wl[c] + m);
+      st(PO_WR + c, R(0.5) * o.Wr[c] + m);
+    }
+  }
+  st(PO_CHI, chi);
+}
+
+// one thread of a point pair: point (i, j), line / solve l
+template <class R, int TYPE, bool CHAR>
+__device__ __forceinline__ void point_pair_body(const KArgs<R>& a, int i, int j, int l) {
+  const Layout& L = a.L;
+  const int imax = TYPE == 0 ? L.nx : L.nxd;
+  const int jmax = TYPE == 0 ? L.nyd : L.ny;
+  const bool valid = !(i < -2 || j < -2 || i > imax || j > jmax);
+  const unsigned mask = __ballot_sync(0xffffffffu, valid);
+  if (!valid) return;
+  const PointLines pl = point_lines<TYPE>(L, i, j);
+  const R* S = a.Sr;
+  R* P = (TYPE == 0 ? a.PA : a.PB) + pcell(L, i, j) + (long)l * NPS * L.pplane;
+  const long pp = L.pplane;
+  point_compute_pair<R, TYPE, CHAR>(
+      a.geno, a.gas, a.h, a.ih, a.want_n != 0, l, mask,
+      [&](int ll, int e, int f) -> R {
+        const int field = f < 4 ? f : pl.gfield[ll] + (f - 4);
+        return S[((long)ll * NFLD + field) * L.plane + pl.base[ll] + e * pl.stride[ll]];
+      },
+      [&](int k, R v) { P[(long)k * pp] = v; });
+}
+
+// block (32, 4): 16 points per warp row, two lanes each
+template <class R, int TYPE, bool CHAR>
+__global__ void __launch_bounds__(128, PointTune<R>::pair_minb) point_pair_kernel(KArgs<R> a) {
+  point_pair_body<R, TYPE, CHAR>(a, blockIdx.x * (blockDim.x / 2) + (threadIdx.x >> 1) - 2,
+                                 blockIdx.y * blockDim.y + threadIdx.y - 2, threadIdx.x & 1);
+}
+
+// ---------------------------------------------------------------------------
 // compact FD + S2O4 update (Eqs. eq-conservation-law-2d, fd-conservative-flux*,
 // define-averaged-gradient, eq-nodal-update, eq-interface-update).
 // One thread per interior node of grid blockIdx.z.
@@ -625,6 +716,17 @@ cudaError_t launch_nodal(const KArgs<R>& a, cudaStream_t s) {
 template <class R>
 cudaError_t launch_points(const KArgs<R>& a, cudaStream_t s) {
   dim3 b(32, 4);
+  if constexpr (PointTune<R>::pair) {
+    const dim3 bp(16, 4);   // points per block; the block itself is (32, 4) threads
+    const dim3 gA = grid2(a.L.nx + 3, a.L.nyd + 3, bp, 1), gB = grid2(a.L.nxd + 3, a.L.ny + 3, bp, 1);
+    if (a.recon_vars) point_pair_kernel<R, 0, true><<<gA, b, 0, s>>>(a);
+    else point_pair_kernel<R, 0, false><<<gA, b, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (a.recon_vars) point_pair_kernel<R, 1, true><<<gB, b, 0, s>>>(a);
+    else point_pair_kernel<R, 1, false><<<gB, b, 0, s>>>(a);
+    return cudaGetLastError();
+  }
   const dim3 gA = grid2(a.L.nx + 3, a.L.nyd + 3, b, 1), gB = grid2(a.L.nxd + 3, a.L.ny + 3, b, 1);
   if (a.recon_vars) point_kernel<R, 0, true><<<gA, b, 0, s>>>(a);
   else point_kernel<R, 0, false><<<gA, b, 0, s>>>(a);

@@ -49,8 +49,9 @@ def _full():
         "e2e": {"value": 48120321.95150462, "unit": bench.UNIT, "h2d_bytes_per_step": 201326592,
                 "d2h_bytes_per_step": 201326592, "ms_per_step": 43.58},
         "err_vs_oracle": {"vortex64": {"fp64": [1.2345678e-14, 2.3456789e-13], "mixed": [3.4567e-8, 4.5678e-7]},
-                          "tube40x20": {"fp64": [1.2345678e-14, 2.3456789e-13], "mixed": [3.4567e-8, 4.5678e-7]},
-                          "member32": {"mixed": [3.4567e-8, 4.5678e-7]}},
+                          "tube40x20": {"fp64": [1.2345678e-14, 2.3456789e-13], "mixed": [3.4567e-8, 4.5678e-7],
+                                        "spread": [3.4567e-8, 4.5678e-7]},
+                          "member": {"mixed": [3.4567e-8, 4.5678e-7], "n": 33}},
         "ensemble": {"value": 1.1212345e9, "ms_per_step": 22.312345, "members_flagged": 0,
                      "roofline": {"frac": 0.2212345}},
         "viscous_tube": {"fp64": {"value": 4.9123456e7, "nonphysical": False},
@@ -70,7 +71,7 @@ def test_line_has_contract_keys_and_fits_a_short_tail():
     for k in KEYS:
         assert k in line, k
     assert line["roofline"]["frac"] > 0 and line["roofline"]["peak"] > 0
-    assert set(line["err_vs_oracle"]) == {"vortex64", "tube40x20", "member32"}
+    assert set(line["err_vs_oracle"]) == {"vortex64", "tube40x20", "member"}
     text = json.dumps(line, separators=(",", ":"))
     assert len(text) < 1450, len(text)
     assert json.loads(text) == line
