@@ -15,7 +15,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfdcgks.so")
 SOURCES = ["fdcgks_api.cu", "fdcgks_fp64.cu", "fdcgks_mixed.cu", "fdcgks_noalloc.cu", "fdcgks_ensemble.cu", "fdcgks_adjoint.cu",
            "fdcgks_line.cu"]
-HEADERS = ["fdcgks_math.cuh", "fdcgks_internal.cuh", "fdcgks_kernels.cuh", "fdcgks_dual.cuh"]
+HEADERS = ["fdcgks_math.cuh", "fdcgks_internal.cuh", "fdcgks_kernels.cuh", "fdcgks_reverse.cuh"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-lineinfo",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -9,10 +9,9 @@
 //   update:  written out by hand (linear in the fluxes given chi, bilinear in
 //            chi; the reset's Jacobian explicitly), scattering the adjoints of
 //            the point and nodal outputs with atomicAdd;
-//   points, nodes: the local Jacobian transposed times the output adjoint,
-//            its columns from the forward map evaluated on dual numbers
-//            (fdcgks_dual.cuh) seeded one input at a time, scattered into the
-//            adjoint state with atomicAdd;
+//   points, nodes: written out by hand as well (fdcgks_reverse.cuh: the
+//            reverse passes of the GENO reconstructions, the kinetic solve and
+//            the nodal flux), scattered into the adjoint state with atomicAdd;
 //   ghost fill: each ghost's adjoint folded back into its source (y pass,
 //            then x pass, the reverse of the forward order).
 // The forward states are recomputed from checkpoints taken every
@@ -35,16 +34,11 @@
 #include <vector>
 
 #include "../../include/fdcgks.h"
-#include "fdcgks_dual.cuh"
 #include "fdcgks_kernels.cuh"
+#include "fdcgks_reverse.cuh"
 #include "fdcgks_replay.h"
 
 namespace fdk {
-// the dual-number evaluation calls one out-of-line copy of the kinetic solve
-// for both solves of a point (the inlined pair makes the kernel far larger)
-template <int N> struct PointTune<Dual<N>> {
-  static constexpr bool noinline = true;
-};
 // the forward FP64 kernels are instantiated in fdcgks_fp64.cu
 extern template cudaError_t launch_nodal<double>(const KArgs<double>&, cudaStream_t);
 extern template cudaError_t launch_points<double>(const KArgs<double>&, cudaStream_t);
@@ -55,28 +49,28 @@ using namespace fdk;
 
 namespace {
 
-// tangent lanes per dual-number pass: one (wider lanes make the device
-// compiler's optimisation of these kernels take minutes).
-const int AN = 1;
-typedef Dual<AN> DN;
+// ---------------------------------------------------------------------------
+// out-of-line copies of the reverse passes (one code copy per kernel)
+// ---------------------------------------------------------------------------
+__device__ __noinline__ void solve_adj_call(const GasK<double>& gas, int normal, const double* Wl, const double* Wr,
+                                            const double* Wln, const double* Wrn, const double* Wt, bool want_n,
+                                            const IfaceOut<double>& ob, double* Wlb, double* Wrb, double* Wlnb,
+                                            double* Wrnb, double* Wtb) {
+  rev::iface_solve_adj(gas, normal, Wl, Wr, Wln, Wrn, Wt, want_n, ob, Wlb, Wrb, Wlnb, Wrnb, Wtb);
+}
 
-// The local maps are differentiated piece by piece, each piece's Jacobian
-// taken column by column with dual numbers and contracted with the adjoint
-// of its outputs (reverse order of the forward):
-//   point: W~ assembly (linear) <- two kinetic solves (20 inputs each: W^l,
-//          W^r, their normal derivatives, the tangential derivative) <- the
-//          tangential derivatives (means of the other line's derivatives) <-
-//          two line reconstructions, whose components are independent of one
-//          another, so one pass seeds the same (entry, value/gradient) input
-//          of every component of both lines (8 passes);
-//   node:  nodal flux (12 inputs) <- eight node-derivative reconstructions
-//          (independent; 6 passes seed all of them).
-// Branches (GENO saturation, the positivity safeguard) follow the values, so
-// every piece differentiates the branch the forward took.
+__device__ __noinline__ void recon_adj_call(const GenoK<double>& g, const double* Q, const double* Qx, double h,
+                                            double ih, double vlb, double dlb, double chilb, double vrb, double drb,
+                                            double chirb, double* Qb, double* Qxb) {
+  rev::recon_interface_adj(g, Q, Qx, h, ih, vlb, dlb, chilb, vrb, drb, chirb, Qb, Qxb);
+}
 
 // ---------------------------------------------------------------------------
 // point map adjoint: inputs are the 64 values (2 lines x 4 entries x (4 W +
-// 4 gradients along the line)) the point reads; outputs its 50 values
+// 4 gradients along the line)) the point reads; outputs its 50 values.
+// Reverse order of point_compute: W~ assembly (linear) <- two kinetic solves
+// <- tangential derivatives (means) <- two line reconstructions, each step
+// by its hand-written reverse pass (fdcgks_reverse.cuh).
 // ---------------------------------------------------------------------------
 template <int TYPE>
 __global__ void __launch_bounds__(128) point_vjp_kernel(KArgs<double> a, const double* __restrict__ Pa,
@@ -117,49 +111,25 @@ __global__ void __launch_bounds__(128) point_vjp_kernel(KArgs<double> a, const d
   }
 
   // adjoints of the solves' outputs from the point outputs (W~ of Eq. eq:W-model-2d)
-  double ao[2][6][4];                                   // [solve][F, Ft, Wl, Wr, Wlt, Wrt][component]
+  IfaceOut<double> ao[2];
   for (int sv = 0; sv < 2; ++sv) {
     const int b = sv * NPS, o = (1 - sv) * NPS;
     for (int c = 0; c < 4; ++c) {
-      ao[sv][0][c] = wn ? ah[b + PO_F + c] : 0.0;
-      ao[sv][1][c] = ah[b + PO_FT + c];
-      ao[sv][2][c] = wn ? 0.5 * ah[b + PO_WL + c] + 0.25 * (ah[o + PO_WL + c] + ah[o + PO_WR + c]) : 0.0;
-      ao[sv][3][c] = wn ? 0.5 * ah[b + PO_WR + c] + 0.25 * (ah[o + PO_WL + c] + ah[o + PO_WR + c]) : 0.0;
-      ao[sv][4][c] = 0.5 * ah[b + PO_WLT + c] + 0.25 * (ah[o + PO_WLT + c] + ah[o + PO_WRT + c]);
-      ao[sv][5][c] = 0.5 * ah[b + PO_WRT + c] + 0.25 * (ah[o + PO_WLT + c] + ah[o + PO_WRT + c]);
+      ao[sv].F[c] = wn ? ah[b + PO_F + c] : 0.0;
+      ao[sv].Ft[c] = ah[b + PO_FT + c];
+      ao[sv].Wl[c] = wn ? 0.5 * ah[b + PO_WL + c] + 0.25 * (ah[o + PO_WL + c] + ah[o + PO_WR + c]) : 0.0;
+      ao[sv].Wr[c] = wn ? 0.5 * ah[b + PO_WR + c] + 0.25 * (ah[o + PO_WL + c] + ah[o + PO_WR + c]) : 0.0;
+      ao[sv].Wlt[c] = 0.5 * ah[b + PO_WLT + c] + 0.25 * (ah[o + PO_WLT + c] + ah[o + PO_WRT + c]);
+      ao[sv].Wrt[c] = 0.5 * ah[b + PO_WRT + c] + 0.25 * (ah[o + PO_WLT + c] + ah[o + PO_WRT + c]);
     }
   }
 
-  // solves: adjoint of their 20 inputs, one dual pass per input
-  const GasK<DN> gas = dual_gas<AN>(a.gas);
-  double av[2][4][4] = {}, at[2][4];
-  for (int sv = 0; sv < 2; ++sv) {
-#pragma unroll 1
-    for (int m = 0; m < 20; ++m) {
-      DN in[5][4];
-      for (int q = 0; q < 4; ++q) {
-        in[0][q] = DN(v[sv][0][q]);
-        in[1][q] = DN(v[sv][2][q]);
-        in[2][q] = DN(v[sv][1][q]);
-        in[3][q] = DN(v[sv][3][q]);
-        in[4][q] = DN(tg[sv][q]);
-      }
-      in[m / 4][m % 4].d[0] = 1.0;
-      IfaceOut<DN> out;
-      iface_solve_call(gas, sv == 0 ? n0 : 1 - n0, in[0], in[1], in[2], in[3], in[4], wn, out);
-      double acc = 0.0;
-      for (int c = 0; c < 4; ++c) {
-        acc += out.Ft[c].d[0] * ao[sv][1][c] + out.Wlt[c].d[0] * ao[sv][4][c] + out.Wrt[c].d[0] * ao[sv][5][c];
-        if (wn) acc += out.F[c].d[0] * ao[sv][0][c] + out.Wl[c].d[0] * ao[sv][2][c] + out.Wr[c].d[0] * ao[sv][3][c];
-      }
-      const int grp = m / 4, c = m % 4;                 // Wl, Wr, Wln, Wrn, Wt
-      if (grp == 0) av[sv][0][c] += acc;
-      else if (grp == 1) av[sv][2][c] += acc;
-      else if (grp == 2) av[sv][1][c] += acc;
-      else if (grp == 3) av[sv][3][c] += acc;
-      else at[sv][c] = acc;
-    }
-  }
+  // solves: their reverse passes give the adjoints of W^l, W^r, the normal
+  // derivatives and the tangential derivative
+  double av[2][4][4] = {}, at[2][4] = {};
+  for (int sv = 0; sv < 2; ++sv)
+    solve_adj_call(a.gas, sv == 0 ? n0 : 1 - n0, v[sv][0], v[sv][2], v[sv][1], v[sv][3], tg[sv], wn, ao[sv],
+                   av[sv][0], av[sv][2], av[sv][1], av[sv][3], at[sv]);
   // the tangential derivative of each solve is the mean of the other line's derivatives
   for (int c = 0; c < 4; ++c) {
     av[1][1][c] += 0.5 * at[0][c];
@@ -167,32 +137,14 @@ __global__ void __launch_bounds__(128) point_vjp_kernel(KArgs<double> a, const d
     av[0][1][c] += 0.5 * at[1][c];
     av[0][3][c] += 0.5 * at[1][c];
   }
-  const double achi[2] = {ah[PO_CHI], ah[NPS + PO_CHI]};
-
-  // line reconstructions: pass q seeds entry q % 4, value (q < 4) or gradient, of every component
-  const GenoK<DN> geno = dual_geno<AN>(a.geno);
+  // line reconstructions
   double ax[64] = {};
-#pragma unroll 1
-  for (int q = 0; q < 8; ++q) {
-    const int es = q % 4, kind = q / 4;
-    for (int l = 0; l < 2; ++l) {
-      DN vl[4], dl[4], vr[4], dr[4], ch;
-      recon_line_ld(
-          geno,
-          [&](int ll, int e, int f) -> DN {
-            DN r(x[ll * 32 + e * 8 + f]);
-            if (e == es && (f >= 4) == (kind == 1)) r.d[0] = 1.0;
-            return r;
-          },
-          l, DN(hl[l]), DN(ihl[l]), vl, dl, vr, dr, ch);
-      for (int c = 0; c < 4; ++c) {
-        double g = vl[c].d[0] * av[l][0][c] + dl[c].d[0] * av[l][1][c] + vr[c].d[0] * av[l][2][c] +
-                   dr[c].d[0] * av[l][3][c];
-        if (c == 0) g += ch.d[0] * achi[l];
-        ax[l * 32 + es * 8 + (kind == 0 ? c : 4 + c)] += g;
-      }
-    }
-  }
+  for (int l = 0; l < 2; ++l)
+    rev::recon_line_adj(a.geno, x + 32 * l, hl[l], ihl[l], av[l], ah[l * NPS + PO_CHI], ax + 32 * l,
+                        [&](const double* Q, const double* Qx, double vlb, double dlb, double chilb, double vrb,
+                            double drb, double chirb, double* Qb, double* Qxb) {
+                          recon_adj_call(a.geno, Q, Qx, hl[l], ihl[l], vlb, dlb, chilb, vrb, drb, chirb, Qb, Qxb);
+                        });
   for (int s = 0; s < 64; ++s)
     if (ax[s] != 0.0) atomicAdd(Sa + addr(s), ax[s]);
 }
@@ -219,6 +171,12 @@ FD_HD void nodal_unslot(int s, int& e, int& f) {
   e = 1 + (s - 12) / 8;
   const int r = (s - 12) % 8;
   f = (e <= 2 || r < 4) ? r : r + 4;
+}
+
+__device__ __noinline__ void nodal_adj_call(const GasK<double>& gas, const double* W, const double* Wx,
+                                            const double* Wy, const double* ah, double* Wb, double* Wxb,
+                                            double* Wyb) {
+  rev::nodal_flux_adj(gas, W, Wx, Wy, ah, ah + 4, ah + 8, ah + 12, Wb, Wxb, Wyb);
 }
 
 __global__ void __launch_bounds__(128) nodal_vjp_kernel(KArgs<double> a, const double* __restrict__ NFa, double* Sa) {
@@ -254,47 +212,24 @@ __global__ void __launch_bounds__(128) nodal_vjp_kernel(KArgs<double> a, const d
       D[d][c] = recon_node(a.geno, q, gq, a.h[d], a.ih[d]);
     }
   }
-  // nodal flux: adjoint of its 12 inputs (W, W_x, W_y), one pass each
-  const GasK<DN> gas = dual_gas<AN>(a.gas);
-  double aW[4], aD[2][4];
-#pragma unroll 1
-  for (int m = 0; m < 12; ++m) {
-    DN w[4], dx[4], dy[4];
-    for (int c = 0; c < 4; ++c) {
-      w[c] = DN(W[c]);
-      dx[c] = DN(D[0][c]);
-      dy[c] = DN(D[1][c]);
-    }
-    (m < 4 ? w[m] : m < 8 ? dx[m - 4] : dy[m - 8]).d[0] = 1.0;
-    DN F[4], G[4], Ft[4], Gt[4];
-    nodal_flux(gas, w, dx, dy, F, G, Ft, Gt);
-    double acc = 0.0;
-    for (int c = 0; c < 4; ++c)
-      acc += F[c].d[0] * ah[c] + G[c].d[0] * ah[4 + c] + Ft[c].d[0] * ah[8 + c] + Gt[c].d[0] * ah[12 + c];
-    if (m < 4) aW[m] = acc;
-    else aD[(m - 4) / 4][m % 4] = acc;
-  }
-  // node derivatives: pass q seeds stencil entry q % 3, value (q < 3) or gradient, of all eight
-  const GenoK<DN> geno = dual_geno<AN>(a.geno);
+  // nodal flux reverse pass: adjoints of W, W_x, W_y
+  double aW[4] = {0, 0, 0, 0}, aD[2][4] = {};
+  nodal_adj_call(a.gas, W, D[0], D[1], ah, aW, aD[0], aD[1]);
+  // node derivatives reverse passes
   double ax[NODAL_IN] = {};
   for (int c = 0; c < 4; ++c) ax[nodal_slot(0, c)] += aW[c];
-#pragma unroll 1
-  for (int q = 0; q < 6; ++q) {
-    const int es = q % 3, kind = q / 3;
-    for (int d = 0; d < 2; ++d)
-      for (int c = 0; c < 4; ++c) {
-        const int em = 1 + 2 * d, ep = 2 + 2 * d, gf = 4 + 4 * d + c;
-        const int ent[3] = {em, 0, ep};
-        DN qv[3], gv[3];
-        for (int t = 0; t < 3; ++t) {
-          qv[t] = DN(X(ent[t], c));
-          gv[t] = DN(X(ent[t], gf));
-        }
-        (kind == 0 ? qv[es] : gv[es]).d[0] = 1.0;
-        const DN r = recon_node(geno, qv, gv, DN(a.h[d]), DN(a.ih[d]));
-        ax[nodal_slot(ent[es], kind == 0 ? c : gf)] += r.d[0] * aD[d][c];
+  for (int d = 0; d < 2; ++d)
+    for (int c = 0; c < 4; ++c) {
+      const int em = 1 + 2 * d, ep = 2 + 2 * d, gf = 4 + 4 * d + c;
+      const int ent[3] = {em, 0, ep};
+      const double q[3] = {X(em, c), W[c], X(ep, c)}, gq[3] = {X(em, gf), X(0, gf), X(ep, gf)};
+      double qb[3] = {0.0, 0.0, 0.0}, gqb[3] = {0.0, 0.0, 0.0};
+      rev::recon_node_adj(a.geno, q, gq, a.h[d], a.ih[d], aD[d][c], qb, gqb);
+      for (int t = 0; t < 3; ++t) {
+        ax[nodal_slot(ent[t], c)] += qb[t];
+        ax[nodal_slot(ent[t], gf)] += gqb[t];
       }
-  }
+    }
   for (int s = 0; s < NODAL_IN; ++s)
     if (ax[s] != 0.0) atomicAdd(Sa + addr(s), ax[s]);
 }

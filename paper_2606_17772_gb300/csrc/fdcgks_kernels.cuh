@@ -177,16 +177,10 @@ __global__ void __launch_bounds__(128, PointTune<R>::nodal_minb) nodal_kernel(KA
 
 // Positivity safeguard of the interface states (the paper describes none): a
 // reconstructed state with non-positive or non-finite density or pressure
-// (rho > 0 and 2 E rho > m_x^2 + m_y^2 fail) is replaced by the state of the
-// node on its side (line entries 1 and 2) with zero normal slope, and the
-// interface's chi by 0, so its compact flux takes the low-order form.
-// Never triggered by smooth data.
-template <class R>
-FD_HD bool physical_state(const R W[4]) {
-  return W[0] > R(0) && R(2) * W[3] * W[0] > W[1] * W[1] + W[2] * W[2] && W[0] < R(INFINITY) &&
-         W[3] < R(INFINITY);
-}
-
+// (physical_state, fdcgks_math.cuh) is replaced by the state of the node on
+// its side (line entries 1 and 2) with zero normal slope, and the interface's
+// chi by 0, so its compact flux takes the low-order form.  Never triggered by
+// smooth data.
 // the safeguard applied to the left/right states of line l
 template <class R, class LD>
 FD_HD void positivity_fix(LD ld, int l, R vl[4], R dl[4], R vr[4], R dr[4], R& chi) {

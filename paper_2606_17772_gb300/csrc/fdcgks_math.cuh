@@ -249,6 +249,14 @@ FD_HD void recon_interface(const GenoK<R>& g, const R Q[4], const R Qx[4], R h, 
   }
 }
 
+// rho > 0 and 2 E rho > m_x^2 + m_y^2 (positive pressure), both finite: the
+// test of the positivity safeguard of the interface states
+template <class R>
+FD_HD bool physical_state(const R W[4]) {
+  return W[0] > R(0) && R(2) * W[3] * W[0] > W[1] * W[1] + W[2] * W[2] && W[0] < R(INFINITY) &&
+         W[3] < R(INFINITY);
+}
+
 // derivative at the middle node of a 3-point line (Sec. 3.1 Eq.
 // 6th-compact-recons; App. C3 with the Sec. 3.2 sub-stencil order)
 template <class R>

@@ -1,13 +1,13 @@
-// Forward-mode dual numbers over FP64 for the adjoint of the FD-CGKS step.
+// Forward-mode dual numbers over FP64: test instrumentation for the
+// hand-written reverse passes of csrc/fdcgks_reverse.cuh.
 //
 // Dual<N> carries a value and N directional derivatives.  Instantiating the
 // device arithmetic of fdcgks_math.cuh (reconstruction, kinetic solves,
 // nodal flux) on Dual<N> evaluates, besides the value, the derivatives of
-// every output with respect to N seeded inputs; the adjoint kernels use this
-// to form the local Jacobians of the point and nodal computations column by
-// column and contract them with the output adjoints.  Branches (GENO
-// saturation, the positivity safeguard) follow the values, so the derivative
-// is that of the branch the forward step took.
+// every output with respect to N seeded inputs: the Jacobian columns the CPU
+// tests contract with output adjoints to check the reverse passes.  Branches
+// (GENO saturation, the positivity safeguard) follow the values, so the
+// derivative is that of the branch the forward step took.
 #pragma once
 
 #include "fdcgks_math.cuh"
