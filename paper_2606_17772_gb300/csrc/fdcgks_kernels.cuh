@@ -47,16 +47,19 @@
 #endif
 // FDK_POINT_PAIR_F32 / _F64  1: two threads per interface point (one line and
 //                  one solve each, coupled by warp shuffles; point_pair_kernel),
-//                  0: one thread per point (point_kernel)
-// FDK_POINT_PAIR_MINB_F32 / _F64  minimum resident blocks per SM of the pair kernel
+//                  0: one thread per point (point_kernel).  On the 1024^2 vortex
+//                  the pair form takes the mixed point phase from 1.019 to
+//                  0.903 ms per step and the FP64 one from 32.06 to 31.41 ms
+// FDK_POINT_PAIR_MINB_F32 / _F64  minimum resident blocks per SM of the pair
+//                  kernel (FP32: 2, 3, 4, 5 gave 1.43, 1.06, 0.915, 0.903 ms)
 #ifndef FDK_POINT_PAIR_F32
 #define FDK_POINT_PAIR_F32 1
 #endif
 #ifndef FDK_POINT_PAIR_F64
-#define FDK_POINT_PAIR_F64 0
+#define FDK_POINT_PAIR_F64 1
 #endif
 #ifndef FDK_POINT_PAIR_MINB_F32
-#define FDK_POINT_PAIR_MINB_F32 4
+#define FDK_POINT_PAIR_MINB_F32 5
 #endif
 #ifndef FDK_POINT_PAIR_MINB_F64
 #define FDK_POINT_PAIR_MINB_F64 1
