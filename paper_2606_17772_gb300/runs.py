@@ -12,7 +12,8 @@ JSON summary:
   * Woodward-Colella blast waves (Sec. 5.3) to t = 0.038 with the
     one-dimensional scheme: density and pressure along the tube;
   * the isentropic vortex once around the periodic box on 128^2 ... 1024^2:
-    errors against the exact solution and the observed order;
+    errors against the exact solution and the observed order (initial data and
+    exact solution the sum of the vortex's periodic images, images = 1);
   * the adjoint workload: the gradient of a density misfit through 500 steps
     of the 256^2 vortex, checked along 16 directions by central differences.
 
@@ -188,7 +189,9 @@ def adjoint_window(n=256, nsteps=500, ndir=16, checkpoint_every=50, variant="lin
     "linear": linear reconstruction with tau = 0.05 dt, where the differences
     are in their linear regime; "geno": the App. D GENO constants, where the
     vortex's far field puts them out of it (the errors are reported, not a
-    check).  On a mixed-precision solver the trajectory is the mixed run."""
+    check).  Along the first direction the difference step is swept from 1e-2
+    to 1e-9 (times n), which shows whether the map is smooth at that scale.
+    On a mixed-precision solver the trajectory is the mixed run."""
     import torch
     kw = dict(geno_variant=2, tau_c1=0.05, tau_c2=0.0) if variant == "linear" else dict(geno_variant=1)
     case = inputs.vortex(n, strength=strength, **kw)
@@ -227,18 +230,27 @@ def adjoint_window(n=256, nsteps=500, ndir=16, checkpoint_every=50, variant="lin
         torch.cuda.synchronize()
         t_adjoint = time.perf_counter() - t0
         drng = np.random.default_rng(2)
-        rel = []
-        for _ in range(ndir):
+        rel, sweep = [], []
+        for k in range(ndir):
             d = torch.from_numpy(drng.standard_normal(S0[0].shape)).cuda()
             d /= d.norm()
             eps = 1e-8 * n
             fd = (J(S0[0] + eps * d) - J(S0[0] - eps * d)) / (2 * eps)
             ad = float((g[0] * d).sum())
             rel.append(abs(ad - fd) / abs(fd))
+            if k == 0:
+                # step-size sweep along the first direction: in the linear regime the
+                # difference error falls as eps^2 until rounding takes over; where the
+                # map is not smooth at the scale of eps it does not settle
+                for e in (1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8, 1e-9):
+                    ee = e * n
+                    fde = (J(S0[0] + ee * d) - J(S0[0] - ee * d)) / (2 * ee)
+                    sweep.append([e, abs(ad - fde) / abs(ad)])
     return {"case": "adjoint", "n": n, "steps": nsteps, "checkpoint_every": checkpoint_every, "variant": variant,
             "precision": "mixed" if precision == fdcgks.MIXED else "fp64", "dt": dt, "J": J0,
             "forward_s": t_forward, "adjoint_s": t_adjoint, "gradient_norm": float(g[0].norm()),
-            "fd_rel_err": rel, "fd_rel_err_max": max(rel) if rel else None}
+            "fd_rel_err": rel, "fd_rel_err_max": max(rel) if rel else None,
+            "step_sweep_rel_err": sweep}
 
 
 def main():
@@ -259,6 +271,10 @@ def main():
                     help="GENO constants: 0 Sec. 3.2 text, 1 App. D, 2 linear (default: the case's)")
     ap.add_argument("--tau-c1", type=float, default=None, help="collision time constant c1 (default: the case's)")
     ap.add_argument("--tau-c2", type=float, default=None, help="collision time constant c2 (default: the case's)")
+    ap.add_argument("--images", type=int, default=None,
+                    help="vortex_convergence: periodic images summed in the initial data (default 1)")
+    ap.add_argument("--grids", default=None, help="vortex_convergence: comma-separated grid sizes")
+    ap.add_argument("--precisions", default="fp64,mixed", help="vortex_convergence: fp64 and/or mixed")
     ap.add_argument("--out", default=None, help="write the JSON summary here (default: stdout)")
     a = ap.parse_args()
     from . import build
@@ -270,7 +286,10 @@ def main():
         res = adjoint_window(a.nx or 256, a.steps, a.dirs, variant=a.variant, precision=prec,
                              cfl=a.cfl if a.cfl != 0.4 else 0.2)
     elif a.case == "vortex_convergence":
-        res = vortex_convergence(t_end=a.t_end or 10.0, cfl=a.cfl if a.cfl != 0.4 else 0.2, **opt)
+        ns = tuple(int(x) for x in a.grids.split(",")) if a.grids else (128, 256, 512, 1024)
+        precs = tuple(fdcgks.MIXED if x == "mixed" else fdcgks.FP64 for x in a.precisions.split(","))
+        res = vortex_convergence(ns=ns, precisions=precs, t_end=a.t_end or 10.0, cfl=a.cfl if a.cfl != 0.4 else 0.2,
+                                 images=1 if a.images is None else a.images, **opt)
     elif a.case == "viscous_tube":
         res = viscous_shock_tube(a.nx or 1000, a.ny or 500, prec, a.t_end or 1.0, a.cfl, **opt)
     elif a.case == "double_mach":
