@@ -61,8 +61,8 @@ __device__ __noinline__ void solve_adj_call(const GasK<double>& gas, int normal,
 
 __device__ __noinline__ void recon_adj_call(const GenoK<double>& g, const double* Q, const double* Qx, double h,
                                             double ih, double vlb, double dlb, double chilb, double vrb, double drb,
-                                            double chirb, double* Qb, double* Qxb) {
-  rev::recon_interface_adj(g, Q, Qx, h, ih, vlb, dlb, chilb, vrb, drb, chirb, Qb, Qxb);
+                                            double chirb, double* Qb, double* Qxb, double fscale) {
+  rev::recon_interface_adj(g, Q, Qx, h, ih, vlb, dlb, chilb, vrb, drb, chirb, Qb, Qxb, fscale);
 }
 
 // ---------------------------------------------------------------------------
@@ -70,11 +70,14 @@ __device__ __noinline__ void recon_adj_call(const GenoK<double>& g, const double
 // 4 gradients along the line)) the point reads; outputs its 50 values.
 // Reverse order of point_compute: W~ assembly (linear) <- two kinetic solves
 // <- tangential derivatives (means) <- two line reconstructions, each step
-// by its hand-written reverse pass (fdcgks_reverse.cuh).
+// by its hand-written reverse pass (fdcgks_reverse.cuh).  fscale > 0 (mixed
+// contexts): GENO's path function takes the FP32 path's rounding floor
+// (64 u max|Q|)^2, so that the reverse pass linearises the map the mixed
+// step computes, in which data varying below the floor count as smooth.
 // ---------------------------------------------------------------------------
 template <int TYPE>
 __global__ void __launch_bounds__(128) point_vjp_kernel(KArgs<double> a, const double* __restrict__ Pa,
-                                                        double* Sa) {
+                                                        double* Sa, double fscale) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x - 2, j = blockIdx.y * blockDim.y + threadIdx.y - 2;
   const Layout& L = a.L;
   const int imax = TYPE == 0 ? L.nx : L.nxd, jmax = TYPE == 0 ? L.nyd : L.ny;
@@ -101,9 +104,11 @@ __global__ void __launch_bounds__(128) point_vjp_kernel(KArgs<double> a, const d
 
   // forward values of the reconstructions and tangential derivatives
   double v[2][4][4], chi[2];                            // v[line][vl, dl, vr, dr][component]
-  for (int l = 0; l < 2; ++l)
-    recon_line_ld(a.geno, [&](int ll, int e, int f) -> double { return x[ll * 32 + e * 8 + f]; }, l, hl[l], ihl[l],
-                  v[l][0], v[l][1], v[l][2], v[l][3], chi[l]);
+  for (int l = 0; l < 2; ++l) {
+    double cl0, cr0;
+    bool fl, fr;
+    rev::recon_line_fwd(a.geno, x + 32 * l, hl[l], ihl[l], fscale, v[l], chi[l], cl0, cr0, fl, fr);
+  }
   double tg[2][4];
   for (int c = 0; c < 4; ++c) {
     tg[0][c] = 0.5 * (v[1][1][c] + v[1][3][c]);
@@ -143,8 +148,10 @@ __global__ void __launch_bounds__(128) point_vjp_kernel(KArgs<double> a, const d
     rev::recon_line_adj(a.geno, x + 32 * l, hl[l], ihl[l], av[l], ah[l * NPS + PO_CHI], ax + 32 * l,
                         [&](const double* Q, const double* Qx, double vlb, double dlb, double chilb, double vrb,
                             double drb, double chirb, double* Qb, double* Qxb) {
-                          recon_adj_call(a.geno, Q, Qx, hl[l], ihl[l], vlb, dlb, chilb, vrb, drb, chirb, Qb, Qxb);
-                        });
+                          recon_adj_call(a.geno, Q, Qx, hl[l], ihl[l], vlb, dlb, chilb, vrb, drb, chirb, Qb, Qxb,
+                                         fscale);
+                        },
+                        fscale);
   for (int s = 0; s < 64; ++s)
     if (ax[s] != 0.0) atomicAdd(Sa + addr(s), ax[s]);
 }
@@ -179,7 +186,8 @@ __device__ __noinline__ void nodal_adj_call(const GasK<double>& gas, const doubl
   rev::nodal_flux_adj(gas, W, Wx, Wy, ah, ah + 4, ah + 8, ah + 12, Wb, Wxb, Wyb);
 }
 
-__global__ void __launch_bounds__(128) nodal_vjp_kernel(KArgs<double> a, const double* __restrict__ NFa, double* Sa) {
+__global__ void __launch_bounds__(128) nodal_vjp_kernel(KArgs<double> a, const double* __restrict__ NFa, double* Sa,
+                                                        double fscale) {
   const int g = blockIdx.z;
   const int i = blockIdx.x * blockDim.x + threadIdx.x - 1, j = blockIdx.y * blockDim.y + threadIdx.y - 1;
   const Layout& L = a.L;
@@ -209,7 +217,7 @@ __global__ void __launch_bounds__(128) nodal_vjp_kernel(KArgs<double> a, const d
     for (int d = 0; d < 2; ++d) {
       const int em = 1 + 2 * d, ep = 2 + 2 * d, gf = 4 + 4 * d + c;
       const double q[3] = {X(em, c), W[c], X(ep, c)}, gq[3] = {X(em, gf), X(0, gf), X(ep, gf)};
-      D[d][c] = recon_node(a.geno, q, gq, a.h[d], a.ih[d]);
+      D[d][c] = recon_node(a.geno, q, gq, a.h[d], a.ih[d], fscale);
     }
   }
   // nodal flux reverse pass: adjoints of W, W_x, W_y
@@ -224,7 +232,7 @@ __global__ void __launch_bounds__(128) nodal_vjp_kernel(KArgs<double> a, const d
       const int ent[3] = {em, 0, ep};
       const double q[3] = {X(em, c), W[c], X(ep, c)}, gq[3] = {X(em, gf), X(0, gf), X(ep, gf)};
       double qb[3] = {0.0, 0.0, 0.0}, gqb[3] = {0.0, 0.0, 0.0};
-      rev::recon_node_adj(a.geno, q, gq, a.h[d], a.ih[d], aD[d][c], qb, gqb);
+      rev::recon_node_adj(a.geno, q, gq, a.h[d], a.ih[d], aD[d][c], qb, gqb, fscale);
       for (int t = 0; t < 3; ++t) {
         ax[nodal_slot(ent[t], c)] += qb[t];
         ax[nodal_slot(ent[t], gf)] += gqb[t];
@@ -515,6 +523,8 @@ cudaError_t adjoint_step(const Work& w, double dt, const double* Aout, double* A
   const dim3 gu = grid2(mx, my, b, 2), gn = grid2(mx + 2, my + 2, b, 2);
   const dim3 gA = grid2(L.nx + 3, L.nyd + 3, b, 1), gB = grid2(L.nxd + 3, L.ny + 3, b, 1);
   cudaError_t e;
+  // the FP32 path's GENO rounding floor (64 u, u = 2^-24) for mixed contexts
+  const double fscale = w.v.p.precision == FDCGKS_MIXED ? 64.0 * 5.9604644775390625e-8 : 0.0;
   for (int stage = 1; stage >= 0; --stage) {
     const KArgs<double> a = stage_args(w, dt, stage);
     double* target = stage == 1 ? w.As : Ain;   // adjoint of this stage's input state
@@ -525,11 +535,11 @@ cudaError_t adjoint_step(const Work& w, double dt, const double* Aout, double* A
     if ((e = cudaMemsetAsync(target, 0, w.fs, s)) != cudaSuccess) return e;
     update_adj_kernel<<<gu, b, 0, s>>>(a, stage, aout, w.Aacc, w.AgB, Ain, w.PAa, w.PBa, w.NFa);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    point_vjp_kernel<0><<<gA, b, 0, s>>>(a, w.PAa, target);
+    point_vjp_kernel<0><<<gA, b, 0, s>>>(a, w.PAa, target, fscale);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    point_vjp_kernel<1><<<gB, b, 0, s>>>(a, w.PBa, target);
+    point_vjp_kernel<1><<<gB, b, 0, s>>>(a, w.PBa, target, fscale);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    nodal_vjp_kernel<<<gn, b, 0, s>>>(a, w.NFa, target);
+    nodal_vjp_kernel<<<gn, b, 0, s>>>(a, w.NFa, target, fscale);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = fold_ghosts(w, target)) != cudaSuccess) return e;
   }

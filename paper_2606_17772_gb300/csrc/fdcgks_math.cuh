@@ -143,8 +143,11 @@ FD_HD R geno_chi(const GenoK<R>& g, R IS0, R IS1, R IS2, R floor = R(0)) {
   } else {
     // alpha = 2 aH/(aH + aL), aH = 1 + (tau/h)^r, aL = 1 + (tau/l)^r, written
     // over the common denominator h^r l^r; tanh(C alpha) rounds to 1 when
-    // C alpha > z_sat, which is tested before dividing
-    R hr = rpow(ISH + g.eps_a, g.r), lr = rpow(ISL + g.eps_a, g.r), tr = rpow(tau, g.r);
+    // C alpha > z_sat, which is tested before dividing.  A floor is added to
+    // eps_a only when one is given (the FP64 linearisation of a mixed run)
+    R ea = g.eps_a;
+    if (floor != R(0)) ea = ea + floor;
+    R hr = rpow(ISH + ea, g.r), lr = rpow(ISL + ea, g.r), tr = rpow(tau, g.r);
     R num = R(2) * (hr + tr) * lr;
     R den = (hr + tr) * lr + (lr + tr) * hr;
     if (g.C * num > R(TanhSat<R>::z) * den) return g.inv_tanhC;
@@ -176,17 +179,31 @@ FD_HD void geno_weights(const GenoK<R>& g, const R d[3], R IS0, R IS1, R IS2, R 
   }
 }
 
+// The floor of an FP64 evaluation: (fscale max|Q|)^2 when fscale is given
+// (fscale = 64 u reproduces the FP32 path's floor in FP64, for the reverse
+// pass of a mixed run), else none; the FP32 path always takes its own.
+template <class R>
+FD_HD R geno_floor_of(R qmax, R fscale) {
+  if (IsF32<R>::v) return geno_floor(qmax);
+  if (fscale != R(0)) {
+    const R e = fscale * qmax;
+    return e * e;
+  }
+  return R(0);
+}
+
 // left and right states at the interface between Q[1] and Q[2] of a 4-point
 // line, with averaged gradients Qx[0..3] of the same 4 nodes (Sec. 3.1 Eq.
-// 7th-compact-recons; App. C1 and C2).  h: spacing, ih = 1/h.
+// 7th-compact-recons; App. C1 and C2).  h: spacing, ih = 1/h; fscale: see
+// geno_floor_of.
 template <class R>
 FD_HD void recon_interface(const GenoK<R>& g, const R Q[4], const R Qx[4], R h, R ih,
-                           R& vl, R& dl, R& chil, R& vr, R& dr, R& chir) {
+                           R& vl, R& dl, R& chil, R& vr, R& dr, R& chir, R fscale = R(0)) {
   const R c64 = R(1.0 / 64.0), c30 = R(1.0 / 30.0);
   // shared high-order derivative (identical for left and right)
   R PHx = -((Q[0] + R(45) * Q[1] - R(45) * Q[2] - Q[3]) * ih + R(9) * (Qx[1] + Qx[2])) * c30;
   R dq12 = (Q[2] - Q[1]) * ih;    // q2x = q3x (left), q2x = q3x (right)
-  const R fl = geno_floor(s_max(s_max(s_abs(Q[0]), s_abs(Q[1])), s_max(s_abs(Q[2]), s_abs(Q[3]))));
+  const R fl = geno_floor_of(s_max(s_max(s_abs(Q[0]), s_abs(Q[1])), s_max(s_abs(Q[2]), s_abs(Q[3]))), fscale);
   // ---- left state (App. C1) ----
   {
     R PH = ((R(7) * Q[0] + R(35) * Q[1] + R(21) * Q[2] + Q[3]) + (Qx[0] + R(22) * Qx[1] - R(7) * Qx[2]) * h) * c64;
@@ -260,7 +277,7 @@ FD_HD bool physical_state(const R W[4]) {
 // derivative at the middle node of a 3-point line (Sec. 3.1 Eq.
 // 6th-compact-recons; App. C3 with the Sec. 3.2 sub-stencil order)
 template <class R>
-FD_HD R recon_node(const GenoK<R>& g, const R Q[3], const R Qx[3], R h, R ih) {
+FD_HD R recon_node(const GenoK<R>& g, const R Q[3], const R Qx[3], R h, R ih, R fscale = R(0)) {
   R PHx = (R(9) * (Q[0] - Q[2]) * ih + (Qx[0] + R(46) * Qx[1] + Qx[2])) * R(1.0 / 30.0);
   R qx0 = (Q[2] - Q[0]) * R(0.5) * ih;                         // central
   R qx1 = R(2) * (Q[1] - Q[0]) * ih - Qx[0];                     // {Q_{j-1}, Q_j, Q_{x,j-1}}
@@ -274,7 +291,7 @@ FD_HD R recon_node(const GenoK<R>& g, const R Q[3], const R Qx[3], R h, R ih) {
   t = Q[2] - Q[1] - Qx[2] * h;
   u = R(2) * (Q[2] - Q[1]) - Qx[2] * h;
   R IS2 = R(13.0 / 3.0) * t * t + u * u;
-  R chi = geno_chi(g, IS0, IS1, IS2, geno_floor(s_max(s_abs(Q[1]), s_max(s_abs(Q[0]), s_abs(Q[2])))));
+  R chi = geno_chi(g, IS0, IS1, IS2, geno_floor_of(s_max(s_abs(Q[1]), s_max(s_abs(Q[0]), s_abs(Q[2]))), fscale));
   if (chi == R(1)) return PHx;
   R w[3];
   geno_weights(g, g.d_node, IS0, IS1, IS2, w);

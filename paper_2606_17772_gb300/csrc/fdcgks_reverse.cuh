@@ -39,14 +39,17 @@ FD_HD void min_adj(R a, R b, R yb, R& ab, R& bb) {
 // ---------------------------------------------------------------------------
 // GENO (Sec. 3.2)
 // ---------------------------------------------------------------------------
-// adjoint of geno_chi (FP64 product form): chib -> ISb[3]
-FD_HD void geno_chi_adj(const GenoK<R>& g, const R IS[3], R chib, R ISb[3]) {
+// adjoint of geno_chi (FP64 product form) with the floor fl added to eps_a:
+// chib -> ISb[3], flb
+FD_HD void geno_chi_adj(const GenoK<R>& g, const R IS[3], R fl, R chib, R ISb[3], R& flb) {
   if (g.linear || chib == 0.0) return;
   const R m_lo = s_min(IS[1], IS[2]), ISL = s_min(IS[0], m_lo);
   const R m_hi = s_max(IS[1], IS[2]), ISH = s_max(IS[0], m_hi);
   const R D = 0.5 * (IS[1] + IS[2]) - IS[0];
   const R tau = s_abs(D);
-  const R H = ISH + g.eps_a, Lo = ISL + g.eps_a;
+  R ea = g.eps_a;
+  if (fl != 0.0) ea = ea + fl;
+  const R H = ISH + ea, Lo = ISL + ea;
   const R hr = rpow(H, g.r), lr = rpow(Lo, g.r), tr = rpow(tau, g.r);
   const R A = (hr + tr) * lr, B = (lr + tr) * hr;
   const R num = 2.0 * A, den = A + B;
@@ -62,6 +65,7 @@ FD_HD void geno_chi_adj(const GenoK<R>& g, const R IS[3], R chib, R ISb[3]) {
   const R Hb = hrb * dpow * (g.r == 3 ? H * H : H), Lob = lrb * dpow * (g.r == 3 ? Lo * Lo : Lo);
   const R taub = trb * dpow * (g.r == 3 ? tau * tau : tau);
   const R Db = taub * sgn0(D);
+  if (fl != 0.0) flb += Hb + Lob;
   ISb[0] -= Db;
   ISb[1] += 0.5 * Db;
   ISb[2] += 0.5 * Db;
@@ -93,10 +97,11 @@ FD_HD void geno_weights_adj(const GenoK<R>& g, const R d[3], const R IS[3], cons
 // The GENO blend of one side: value v = chi PH + (1 - chi) PL, derivative
 // d = chi PHx + (1 - chi) PLx, PL = sum w_k q_k, PLx = w0 qx0 + (w1 + w2) dq12.
 // Given vb, db and the adjoint of chi, returns the adjoints of PH, PHx, q[3],
-// qx0, dq12 and IS[3].
-FD_HD void geno_blend_adj(const GenoK<R>& g, const R dk[3], const R IS[3], R PH, R PHx, const R q[3], R qx0, R dq12,
-                          R vb, R db, R chib, R& PHb, R& PHxb, R qb[3], R& qx0b, R& dq12b, R ISb[3]) {
-  const R chi = geno_chi(g, IS[0], IS[1], IS[2]);
+// qx0, dq12, IS[3] and the floor fl of the path function.
+FD_HD void geno_blend_adj(const GenoK<R>& g, const R dk[3], const R IS[3], R fl, R PH, R PHx, const R q[3], R qx0,
+                          R dq12, R vb, R db, R chib, R& PHb, R& PHxb, R qb[3], R& qx0b, R& dq12b, R ISb[3],
+                          R& flb) {
+  const R chi = geno_chi(g, IS[0], IS[1], IS[2], fl);
   if (chi == 1.0) {
     // the forward skips the blend; chi's derivative is zero there
     PHb += vb;
@@ -121,7 +126,33 @@ FD_HD void geno_blend_adj(const GenoK<R>& g, const R dk[3], const R IS[3], R PH,
   qx0b += PLxb * w[0];
   dq12b += PLxb * (w[1] + w[2]);
   geno_weights_adj(g, dk, IS, wb, ISb);
-  geno_chi_adj(g, IS, chib_t, ISb);
+  geno_chi_adj(g, IS, fl, chib_t, ISb, flb);
+}
+
+// floor of the path function from max |Q| (geno_floor_of with fscale): its
+// adjoint flb goes to the entry of largest magnitude (ties: shared, as for
+// the dual numbers' nested max)
+FD_HD void floor_adj4(const R Q[4], R fscale, R flb, R Qb[4]) {
+  if (flb == 0.0 || fscale == 0.0) return;
+  const R a0 = s_abs(Q[0]), a1 = s_abs(Q[1]), a2 = s_abs(Q[2]), a3 = s_abs(Q[3]);
+  const R m01 = s_max(a0, a1), m23 = s_max(a2, a3), qmax = s_max(m01, m23);
+  const R qb = flb * 2.0 * fscale * fscale * qmax;
+  R m01b = 0.0, m23b = 0.0, ab[4] = {0.0, 0.0, 0.0, 0.0};
+  max_adj(m01, m23, qb, m01b, m23b);
+  max_adj(a0, a1, m01b, ab[0], ab[1]);
+  max_adj(a2, a3, m23b, ab[2], ab[3]);
+  for (int k = 0; k < 4; ++k) Qb[k] += ab[k] * sgn0(Q[k]);
+}
+FD_HD void floor_adj3(const R Q[3], R fscale, R flb, R Qb[3]) {
+  if (flb == 0.0 || fscale == 0.0) return;
+  // qmax = max(|Q1|, max(|Q0|, |Q2|)) as in recon_node
+  const R a0 = s_abs(Q[0]), a1 = s_abs(Q[1]), a2 = s_abs(Q[2]);
+  const R m02 = s_max(a0, a2), qmax = s_max(a1, m02);
+  const R qb = flb * 2.0 * fscale * fscale * qmax;
+  R m02b = 0.0, ab[3] = {0.0, 0.0, 0.0};
+  max_adj(a1, m02, qb, ab[1], m02b);
+  max_adj(a0, a2, m02b, ab[0], ab[2]);
+  for (int k = 0; k < 3; ++k) Qb[k] += ab[k] * sgn0(Q[k]);
 }
 
 // 13/3 t^2 + u^2 with t = a - b - x h, u = 2 (a - b) - x h (the sub-stencil
@@ -139,11 +170,14 @@ FD_HD void is_three_adj(R t, R u, R ISb, R& tb, R& ub) {
   ub = 0.5 * u * ISb;
 }
 
-// adjoint of recon_interface (FP64): output adjoints vlb, dlb, chilb, vrb,
-// drb, chirb -> Qb[4], Qxb[4] (added)
+// adjoint of recon_interface (FP64, path-function floor from fscale as in
+// geno_floor_of): output adjoints vlb, dlb, chilb, vrb, drb, chirb -> Qb[4],
+// Qxb[4] (added)
 FD_HD void recon_interface_adj(const GenoK<R>& g, const R Q[4], const R Qx[4], R h, R ih, R vlb, R dlb, R chilb,
-                               R vrb, R drb, R chirb, R Qb[4], R Qxb[4]) {
+                               R vrb, R drb, R chirb, R Qb[4], R Qxb[4], R fscale = 0.0) {
   const R c64 = 1.0 / 64.0, c30 = 1.0 / 30.0;
+  const R fl = geno_floor_of(s_max(s_max(s_abs(Q[0]), s_abs(Q[1])), s_max(s_abs(Q[2]), s_abs(Q[3]))), fscale);
+  R flb = 0.0;
   const R PHx = -((Q[0] + 45.0 * Q[1] - 45.0 * Q[2] - Q[3]) * ih + 9.0 * (Qx[1] + Qx[2])) * c30;
   const R dq12 = (Q[2] - Q[1]) * ih;
   R PHxb = 0.0, dq12b = 0.0;
@@ -161,7 +195,8 @@ FD_HD void recon_interface_adj(const GenoK<R>& g, const R Q[4], const R Qx[4], R
     const R t2 = Q[1] - 2.0 * Q[2] + Q[3], u2 = 3.0 * Q[1] - 4.0 * Q[2] + Q[3];
     IS[2] = (13.0 / 12.0) * t2 * t2 + 0.25 * u2 * u2;
     R PHb = 0.0, qb[3] = {0.0, 0.0, 0.0}, qx0b = 0.0, ISb[3] = {0.0, 0.0, 0.0};
-    geno_blend_adj(g, g.d_iface, IS, PH, PHx, q, qx0, dq12, vlb, dlb, chilb, PHb, PHxb, qb, qx0b, dq12b, ISb);
+    geno_blend_adj(g, g.d_iface, IS, fl, PH, PHx, q, qx0, dq12, vlb, dlb, chilb, PHb, PHxb, qb, qx0b, dq12b, ISb,
+                   flb);
     // PH
     Qb[0] += 7.0 * c64 * PHb; Qb[1] += 35.0 * c64 * PHb; Qb[2] += 21.0 * c64 * PHb; Qb[3] += c64 * PHb;
     Qxb[0] += h * c64 * PHb; Qxb[1] += 22.0 * h * c64 * PHb; Qxb[2] -= 7.0 * h * c64 * PHb;
@@ -193,7 +228,8 @@ FD_HD void recon_interface_adj(const GenoK<R>& g, const R Q[4], const R Qx[4], R
     const R t2 = Q[0] - 2.0 * Q[1] + Q[2], u2 = 3.0 * Q[2] - 4.0 * Q[1] + Q[0];
     IS[2] = (13.0 / 12.0) * t2 * t2 + 0.25 * u2 * u2;
     R PHb = 0.0, qb[3] = {0.0, 0.0, 0.0}, qx0b = 0.0, ISb[3] = {0.0, 0.0, 0.0};
-    geno_blend_adj(g, g.d_iface, IS, PH, PHx, q, qx0, dq12, vrb, drb, chirb, PHb, PHxb, qb, qx0b, dq12b, ISb);
+    geno_blend_adj(g, g.d_iface, IS, fl, PH, PHx, q, qx0, dq12, vrb, drb, chirb, PHb, PHxb, qb, qx0b, dq12b, ISb,
+                   flb);
     Qb[0] += c64 * PHb; Qb[1] += 21.0 * c64 * PHb; Qb[2] += 35.0 * c64 * PHb; Qb[3] += 7.0 * c64 * PHb;
     Qxb[1] += 7.0 * h * c64 * PHb; Qxb[2] -= 22.0 * h * c64 * PHb; Qxb[3] -= h * c64 * PHb;
     Qb[3] += -1.25 * qb[0] - 0.125 * qb[1] + 3.0 * ih * qx0b;
@@ -219,10 +255,12 @@ FD_HD void recon_interface_adj(const GenoK<R>& g, const R Q[4], const R Qx[4], R
   Qxb[1] -= 9.0 * c30 * PHxb; Qxb[2] -= 9.0 * c30 * PHxb;
   Qb[2] += ih * dq12b;
   Qb[1] -= ih * dq12b;
+  floor_adj4(Q, fscale, flb, Qb);
 }
 
-// adjoint of recon_node (FP64): rb -> Qb[3], Qxb[3] (added)
-FD_HD void recon_node_adj(const GenoK<R>& g, const R Q[3], const R Qx[3], R h, R ih, R rb, R Qb[3], R Qxb[3]) {
+// adjoint of recon_node (FP64, floor from fscale): rb -> Qb[3], Qxb[3] (added)
+FD_HD void recon_node_adj(const GenoK<R>& g, const R Q[3], const R Qx[3], R h, R ih, R rb, R Qb[3], R Qxb[3],
+                          R fscale = 0.0) {
   const R c30 = 1.0 / 30.0;
   const R PHx = (9.0 * (Q[0] - Q[2]) * ih + (Qx[0] + 46.0 * Qx[1] + Qx[2])) * c30;
   const R qx[3] = {(Q[2] - Q[0]) * 0.5 * ih, 2.0 * (Q[1] - Q[0]) * ih - Qx[0], 2.0 * (Q[2] - Q[1]) * ih - Qx[2]};
@@ -234,8 +272,9 @@ FD_HD void recon_node_adj(const GenoK<R>& g, const R Q[3], const R Qx[3], R h, R
   t = Q[2] - Q[1] - Qx[2] * h;
   u = 2.0 * (Q[2] - Q[1]) - Qx[2] * h;
   IS[2] = (13.0 / 3.0) * t * t + u * u;
-  R PHxb = 0.0, qxb[3] = {0.0, 0.0, 0.0}, ISb[3] = {0.0, 0.0, 0.0};
-  const R chi = geno_chi(g, IS[0], IS[1], IS[2]);
+  R PHxb = 0.0, qxb[3] = {0.0, 0.0, 0.0}, ISb[3] = {0.0, 0.0, 0.0}, flb = 0.0;
+  const R fl = geno_floor_of(s_max(s_abs(Q[1]), s_max(s_abs(Q[0]), s_abs(Q[2]))), fscale);
+  const R chi = geno_chi(g, IS[0], IS[1], IS[2], fl);
   if (chi == 1.0) {
     PHxb = rb;
   } else {
@@ -247,8 +286,9 @@ FD_HD void recon_node_adj(const GenoK<R>& g, const R Q[3], const R Qx[3], R h, R
     const R wb[3] = {PLxb * qx[0], PLxb * qx[1], PLxb * qx[2]};
     for (int k = 0; k < 3; ++k) qxb[k] = PLxb * w[k];
     geno_weights_adj(g, g.d_node, IS, wb, ISb);
-    geno_chi_adj(g, IS, rb * (PHx - PLx), ISb);
+    geno_chi_adj(g, IS, fl, rb * (PHx - PLx), ISb, flb);
   }
+  floor_adj3(Q, fscale, flb, Qb);
   Qb[0] += 9.0 * c30 * ih * PHxb;
   Qb[2] -= 9.0 * c30 * ih * PHxb;
   Qxb[0] += c30 * PHxb; Qxb[1] += 46.0 * c30 * PHxb; Qxb[2] += c30 * PHxb;
@@ -269,18 +309,37 @@ FD_HD void recon_node_adj(const GenoK<R>& g, const R Q[3], const R Qx[3], R h, R
 // value and right derivative of component c; chib that of the line's chi
 // (the smaller of the two sides' chi of rho, 0 where the safeguard acts).
 // Adds to xb[32].  radj(Q, Qx, vlb, dlb, chilb, vrb, drb, chirb, Qb, Qxb)
-// runs recon_interface_adj for one component (an out-of-line copy on the GPU).
-template <class RADJ>
-FD_HD void recon_line_adj(const GenoK<R>& g, const R* x, R h, R ih, const R vb[4][4], R chib, R* xb, RADJ radj) {
-  R v[4][4], cl0 = 0.0, cr0 = 0.0;
+// runs recon_interface_adj for one component (an out-of-line copy on the GPU)
+// with the same fscale (the path-function floor, geno_floor_of).
+// The forward of that line (recon_line_ld's arithmetic, with the floor):
+// v[0..3][c] = left value, left derivative, right value, right derivative;
+// chi of the flux; cl0, cr0 the two sides' chi of rho; fixl / fixr whether
+// the safeguard replaced a side.
+FD_HD void recon_line_fwd(const GenoK<R>& g, const R* x, R h, R ih, R fscale, R v[4][4], R& chi, R& cl0, R& cr0,
+                          bool& fixl, bool& fixr) {
   for (int c = 0; c < 4; ++c) {
     const R Q[4] = {x[c], x[8 + c], x[16 + c], x[24 + c]};
     const R Qx[4] = {x[4 + c], x[12 + c], x[20 + c], x[28 + c]};
     R cl, cr;
-    recon_interface(g, Q, Qx, h, ih, v[0][c], v[1][c], cl, v[2][c], v[3][c], cr);
+    recon_interface(g, Q, Qx, h, ih, v[0][c], v[1][c], cl, v[2][c], v[3][c], cr, fscale);
     if (c == 0) { cl0 = cl; cr0 = cr; }
   }
-  const bool fixl = !physical_state(v[0]), fixr = !physical_state(v[2]);
+  chi = s_min(cl0, cr0);
+  fixl = !physical_state(v[0]);
+  fixr = !physical_state(v[2]);
+  for (int c = 0; c < 4; ++c) {
+    if (fixl) { v[0][c] = x[8 + c]; v[1][c] = 0.0; }
+    if (fixr) { v[2][c] = x[16 + c]; v[3][c] = 0.0; }
+  }
+  if (fixl || fixr) chi = 0.0;
+}
+
+template <class RADJ>
+FD_HD void recon_line_adj(const GenoK<R>& g, const R* x, R h, R ih, const R vb[4][4], R chib, R* xb, RADJ radj,
+                          R fscale = 0.0) {
+  R v[4][4], chi, cl0, cr0;
+  bool fixl, fixr;
+  recon_line_fwd(g, x, h, ih, fscale, v, chi, cl0, cr0, fixl, fixr);
   R chilb = 0.0, chirb = 0.0;
   if (!fixl && !fixr) min_adj(cl0, cr0, chib, chilb, chirb);
   for (int c = 0; c < 4; ++c) {

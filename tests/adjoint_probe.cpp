@@ -79,42 +79,46 @@ void probe_solve_vjp(double gamma, double mu, double Pr, double c1, double c2, d
   }
 }
 
-// in = Q[4], Qx[4]; ob = vl, dl, chil, vr, dr, chir adjoints
-void probe_recon_iface_vjp(int variant, double h, const double* in, const double* ob, double* rev, double* dual) {
+// in = Q[4], Qx[4]; ob = vl, dl, chil, vr, dr, chir adjoints; fscale: the
+// path-function floor (0: none)
+void probe_recon_iface_vjp(int variant, double h, double fscale, const double* in, const double* ob, double* rev,
+                           double* dual) {
   const GenoK<double> g = geno_of(variant);
   for (int k = 0; k < 8; ++k) rev[k] = 0.0;
-  rev::recon_interface_adj(g, in, in + 4, h, 1.0 / h, ob[0], ob[1], ob[2], ob[3], ob[4], ob[5], rev, rev + 4);
+  rev::recon_interface_adj(g, in, in + 4, h, 1.0 / h, ob[0], ob[1], ob[2], ob[3], ob[4], ob[5], rev, rev + 4,
+                           fscale);
   const GenoK<D1> gd = dual_geno<1>(g);
   for (int m = 0; m < 8; ++m) {
     D1 x[8];
     for (int k = 0; k < 8; ++k) x[k] = D1(in[k]);
     x[m].d[0] = 1.0;
     D1 vl, dl, cl, vr, dr, cr;
-    recon_interface(gd, x, x + 4, D1(h), D1(1.0 / h), vl, dl, cl, vr, dr, cr);
+    recon_interface(gd, x, x + 4, D1(h), D1(1.0 / h), vl, dl, cl, vr, dr, cr, D1(fscale));
     dual[m] = vl.d[0] * ob[0] + dl.d[0] * ob[1] + cl.d[0] * ob[2] + vr.d[0] * ob[3] + dr.d[0] * ob[4] +
               cr.d[0] * ob[5];
   }
 }
 
 // in = Q[3], Qx[3]; ob = adjoint of the node derivative
-void probe_recon_node_vjp(int variant, double h, const double* in, double ob, double* rev, double* dual) {
+void probe_recon_node_vjp(int variant, double h, double fscale, const double* in, double ob, double* rev,
+                          double* dual) {
   const GenoK<double> g = geno_of(variant);
   for (int k = 0; k < 6; ++k) rev[k] = 0.0;
-  rev::recon_node_adj(g, in, in + 3, h, 1.0 / h, ob, rev, rev + 3);
+  rev::recon_node_adj(g, in, in + 3, h, 1.0 / h, ob, rev, rev + 3, fscale);
   const GenoK<D1> gd = dual_geno<1>(g);
   for (int m = 0; m < 6; ++m) {
     D1 x[6];
     for (int k = 0; k < 6; ++k) x[k] = D1(in[k]);
     x[m].d[0] = 1.0;
-    dual[m] = recon_node(gd, x, x + 3, D1(h), D1(1.0 / h)).d[0] * ob;
+    dual[m] = recon_node(gd, x, x + 3, D1(h), D1(1.0 / h), D1(fscale)).d[0] * ob;
   }
 }
 
 // one 4-point line of the point kernel (recon_line_ld with the positivity
 // safeguard): in = x[e * 8 + f] (32); ob = vl[4], dl[4], vr[4], dr[4], chi (17);
 // *acted: bit 0 / bit 1 set where the safeguard replaced the left / right state
-void probe_recon_line_vjp(int variant, double h, const double* in, const double* ob, double* rev, double* dual,
-                          int* acted) {
+void probe_recon_line_vjp(int variant, double h, double fscale, const double* in, const double* ob, double* rev,
+                          double* dual, int* acted) {
   const GenoK<double> g = geno_of(variant);
   for (int k = 0; k < 32; ++k) rev[k] = 0.0;
   double vb[4][4];
@@ -123,8 +127,10 @@ void probe_recon_line_vjp(int variant, double h, const double* in, const double*
   rev::recon_line_adj(g, in, h, 1.0 / h, vb, ob[16], rev,
                       [&](const double* Q, const double* Qx, double vlb, double dlb, double chilb, double vrb,
                           double drb, double chirb, double* Qb, double* Qxb) {
-                        rev::recon_interface_adj(g, Q, Qx, h, 1.0 / h, vlb, dlb, chilb, vrb, drb, chirb, Qb, Qxb);
-                      });
+                        rev::recon_interface_adj(g, Q, Qx, h, 1.0 / h, vlb, dlb, chilb, vrb, drb, chirb, Qb, Qxb,
+                                                 fscale);
+                      },
+                      fscale);
   const GenoK<D1> gd = dual_geno<1>(g);
   for (int m = 0; m < 32; ++m) {
     D1 x[32];
@@ -135,7 +141,7 @@ void probe_recon_line_vjp(int variant, double h, const double* in, const double*
     for (int c = 0; c < 4; ++c) {
       const D1 Q[4] = {x[c], x[8 + c], x[16 + c], x[24 + c]}, Qx[4] = {x[4 + c], x[12 + c], x[20 + c], x[28 + c]};
       D1 cl, cr;
-      recon_interface(gd, Q, Qx, D1(h), D1(1.0 / h), vl[c], dl[c], cl, vr[c], dr[c], cr);
+      recon_interface(gd, Q, Qx, D1(h), D1(1.0 / h), vl[c], dl[c], cl, vr[c], dr[c], cr, D1(fscale));
       if (c == 0) chi = s_min(cl, cr);
     }
     const bool badl = !physical_state(vl), badr = !physical_state(vr);

@@ -87,24 +87,37 @@ def _lines(rng, n):
     return rows
 
 
+FLOOR = 64 * 2.0 ** -24          # the FP32 path's floor scale, for the reverse pass of a mixed run
+
+
+@pytest.mark.parametrize("fscale", [0.0, FLOOR])
 @pytest.mark.parametrize("variant", [0, 1, 2])
-def test_reconstruction_reverse_equals_dual_numbers(probe, variant):
+def test_reconstruction_reverse_equals_dual_numbers(probe, variant, fscale):
+    """fscale > 0: the path function with the FP32 path's rounding floor
+    (64 u max|Q|)^2 added to eps_a, evaluated in FP64, including the floor's
+    own dependence on the data."""
     rng = np.random.default_rng(10 + variant)
-    for Q, Qx in _lines(rng, 200):
+    rows = _lines(rng, 200)
+    # data varying by about the floor: there the floor decides chi
+    for t in range(40):
+        rows.append((1.0 + 3e-6 * rng.normal(size=4), 3e-5 * rng.normal(size=4)))
+    for Q, Qx in rows:
         inp = np.concatenate([Q, Qx])
         ob = rng.normal(size=6)
         rev, dual = np.zeros(8), np.zeros(8)
-        probe.probe_recon_iface_vjp(variant, ctypes.c_double(0.07), _p(inp), _p(ob), _p(rev), _p(dual))
+        probe.probe_recon_iface_vjp(variant, ctypes.c_double(0.07), ctypes.c_double(fscale), _p(inp), _p(ob),
+                                    _p(rev), _p(dual))
         _close(rev, dual, 1e-11)
         inp3 = np.concatenate([Q[:3], Qx[:3]])
         rev, dual = np.zeros(6), np.zeros(6)
-        probe.probe_recon_node_vjp(variant, ctypes.c_double(0.07), _p(inp3), ctypes.c_double(ob[0]), _p(rev),
-                                   _p(dual))
+        probe.probe_recon_node_vjp(variant, ctypes.c_double(0.07), ctypes.c_double(fscale), _p(inp3),
+                                   ctypes.c_double(ob[0]), _p(rev), _p(dual))
         _close(rev, dual, 1e-11)
 
 
+@pytest.mark.parametrize("fscale", [0.0, FLOOR])
 @pytest.mark.parametrize("variant", [0, 1])
-def test_line_reverse_with_positivity_safeguard(probe, variant):
+def test_line_reverse_with_positivity_safeguard(probe, variant, fscale):
     """Lines whose reconstructed left or right state has negative pressure
     (the safeguard replaces it by the node state) and ordinary lines."""
     rng = np.random.default_rng(20 + variant)
@@ -119,8 +132,8 @@ def test_line_reverse_with_positivity_safeguard(probe, variant):
         ob = rng.normal(size=17)
         rev, dual = np.zeros(32), np.zeros(32)
         flag = ctypes.c_int()
-        probe.probe_recon_line_vjp(variant, ctypes.c_double(0.05), _p(x), _p(ob), _p(rev), _p(dual),
-                                   ctypes.byref(flag))
+        probe.probe_recon_line_vjp(variant, ctypes.c_double(0.05), ctypes.c_double(fscale), _p(x), _p(ob), _p(rev),
+                                   _p(dual), ctypes.byref(flag))
         _close(rev, dual, 1e-11)
         acted |= flag.value
     assert acted == 3          # the safeguard acted on left and on right states
