@@ -185,7 +185,8 @@ def adjoint_window(n=256, nsteps=500, ndir=16, checkpoint_every=50, variant="lin
     target a run from rho plus 8 seeded Gaussian bumps (sigma 0.5, amplitude
     1e-3), differentiated with respect to the primary W^0 by fdcgks_vjp_steps
     (checkpoints every checkpoint_every steps), and checked along ndir seeded
-    random unit directions against central differences of J.  variant
+    random unit directions against central differences of J (Richardson
+    extrapolated from steps 1e-5 n and 5e-6 n).  variant
     "linear": linear reconstruction with tau = 0.05 dt, where the differences
     are in their linear regime; "geno": the App. D GENO constants, where the
     vortex's far field puts them out of it (the errors are reported, not a
@@ -234,8 +235,13 @@ def adjoint_window(n=256, nsteps=500, ndir=16, checkpoint_every=50, variant="lin
         for k in range(ndir):
             d = torch.from_numpy(drng.standard_normal(S0[0].shape)).cuda()
             d /= d.norm()
-            eps = 1e-8 * n
-            fd = (J(S0[0] + eps * d) - J(S0[0] - eps * d)) / (2 * eps)
+            # central differences at steps e and e/2 combined by Richardson
+            # extrapolation, (4 D(e/2) - D(e)) / 3: the O(e^2) term cancels, so a
+            # step far above rounding (1e-5 n) still gives an O(e^4) error
+            eps = 1e-5 * n
+            d1 = (J(S0[0] + eps * d) - J(S0[0] - eps * d)) / (2 * eps)
+            d2 = (J(S0[0] + 0.5 * eps * d) - J(S0[0] - 0.5 * eps * d)) / eps
+            fd = (4.0 * d2 - d1) / 3.0
             ad = float((g[0] * d).sum())
             rel.append(abs(ad - fd) / abs(fd))
             if k == 0:
