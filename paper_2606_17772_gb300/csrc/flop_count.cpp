@@ -117,6 +117,7 @@ template <int P> CN<P> operator-(const CN<P>& a) {
 template <int P> bool operator>(const CN<P>& a, const CN<P>& b) { return a.v > b.v; }
 template <int P> bool operator<(const CN<P>& a, const CN<P>& b) { return a.v < b.v; }
 template <int P> bool operator==(const CN<P>& a, const CN<P>& b) { return a.v == b.v; }
+template <int P> bool operator!=(const CN<P>& a, const CN<P>& b) { return a.v != b.v; }
 
 namespace fdk {
 template <int P> CN<P> s_sqrt(CN<P> x) { return apply<P>(OP_SQRT, x.ident(), 0, std::sqrt(x.v), cnt::C<P>().sqrt_); }
