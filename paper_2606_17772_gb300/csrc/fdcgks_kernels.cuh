@@ -64,6 +64,13 @@
 #ifndef FDK_POINT_PAIR_MINB_F64
 #define FDK_POINT_PAIR_MINB_F64 1
 #endif
+// FDK_PAIR_PRELOAD_F32  1: a pair-kernel thread loads its line's 32 values (4
+//                  entries x W and the gradient along the line) into registers
+//                  before the first reconstruction, so the loads are not issued
+//                  between the out-of-line reconstruction calls
+#ifndef FDK_PAIR_PRELOAD_F32
+#define FDK_PAIR_PRELOAD_F32 0
+#endif
 
 namespace fdk {
 
@@ -456,13 +463,26 @@ __device__ __forceinline__ void point_pair_body(const KArgs<R>& a, int i, int j,
   const R* S = a.Sr;
   R* P = (TYPE == 0 ? a.PA : a.PB) + pcell(L, i, j) + (long)l * NPS * L.pplane;
   const long pp = L.pplane;
-  point_compute_pair<R, TYPE, CHAR>(
-      a.geno, a.gas, a.h, a.ih, a.want_n != 0, l, mask,
-      [&](int ll, int e, int f) -> R {
-        const int field = f < 4 ? f : pl.gfield[ll] + (f - 4);
-        return S[((long)ll * NFLD + field) * L.plane + pl.base[ll] + e * pl.stride[ll]];
-      },
-      [&](int k, R v) { P[(long)k * pp] = v; });
+  auto st = [&](int k, R v) { P[(long)k * pp] = v; };
+  auto gl = [&](int ll, int e, int f) -> R {
+    const int field = f < 4 ? f : pl.gfield[ll] + (f - 4);
+    return S[((long)ll * NFLD + field) * L.plane + pl.base[ll] + e * pl.stride[ll]];
+  };
+#if FDK_PAIR_PRELOAD_F32
+  if constexpr (IsF32<R>::v) {
+  R xl[32];
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+#pragma unroll
+    for (int f = 0; f < 8; ++f) xl[e * 8 + f] = gl(l, e, f);
+  point_compute_pair<R, TYPE, CHAR>(a.geno, a.gas, a.h, a.ih, a.want_n != 0, l, mask,
+                                    [&](int, int e, int f) -> R { return xl[e * 8 + f]; }, st);
+  } else {
+    point_compute_pair<R, TYPE, CHAR>(a.geno, a.gas, a.h, a.ih, a.want_n != 0, l, mask, gl, st);
+  }
+#else
+  point_compute_pair<R, TYPE, CHAR>(a.geno, a.gas, a.h, a.ih, a.want_n != 0, l, mask, gl, st);
+#endif
 }
 
 // block (32, 4): 16 points per warp row, two lanes each
