@@ -81,15 +81,18 @@ def viscous_shock_tube(nx=1000, ny=500, precision=fdcgks.MIXED, t_end=1.0, cfl=0
 
 
 def vortex_convergence(ns=(128, 256, 512, 1024), precisions=(fdcgks.FP64, fdcgks.MIXED), t_end=10.0, cfl=0.2,
-                       **kw):
+                       dt_h2=False, **kw):
     """The isentropic vortex (strength 5, free stream (1, 1, 1, 1)) advected once
     around the periodic [0, 10]^2 box (t = 10: the exact solution is the
     initial state) on each grid: L1 error of the density against the exact
     solution (mean absolute error over the primary nodes, and the same
     integral over the domain), the observed order between successive grids,
-    and for the mixed path the L1 difference from the FP64 run."""
-    out = {"case": "isentropic vortex, [0,10]^2 periodic, strength 5, to t = %g, CFL %.2f, %s" % (
-        t_end, cfl, json.dumps(kw)), "grids": []}
+    and for the mixed path the L1 difference from the FP64 run.  dt_h2: the
+    CFL number halves with every doubling of the grid from the first one, so
+    that dt ~ h^2 (the paper's accuracy runs) and the time error falls as fast
+    as the spatial error of a sixth-order scheme."""
+    out = {"case": "isentropic vortex, [0,10]^2 periodic, strength 5, to t = %g, CFL %.2f%s, %s" % (
+        t_end, cfl, " x (n0/n) (dt ~ h^2)" if dt_h2 else "", json.dumps(kw)), "grids": []}
     prev = {}
     for n in ns:
         case = inputs.vortex(n, **kw)
@@ -102,7 +105,7 @@ def vortex_convergence(ns=(128, 256, 512, 1024), precisions=(fdcgks.FP64, fdcgks
             with fdcgks.Solver.from_case(case, prec) as s:
                 s.set_state(*S0)
                 w0 = time.perf_counter()
-                t, k = advance(s, t_end, cfl)
+                t, k = advance(s, t_end, cfl * ns[0] / n if dt_h2 else cfl)
                 wall = time.perf_counter() - w0
                 rho[name] = s.get_state(device=False)[0][0]
             err = np.abs(rho[name] - exact)
@@ -281,6 +284,7 @@ def main():
                     help="vortex_convergence: periodic images summed in the initial data (default 1)")
     ap.add_argument("--grids", default=None, help="vortex_convergence: comma-separated grid sizes")
     ap.add_argument("--precisions", default="fp64,mixed", help="vortex_convergence: fp64 and/or mixed")
+    ap.add_argument("--dt-h2", action="store_true", help="vortex_convergence: dt ~ h^2 (CFL halved per doubling)")
     ap.add_argument("--out", default=None, help="write the JSON summary here (default: stdout)")
     a = ap.parse_args()
     from . import build
@@ -295,7 +299,7 @@ def main():
         ns = tuple(int(x) for x in a.grids.split(",")) if a.grids else (128, 256, 512, 1024)
         precs = tuple(fdcgks.MIXED if x == "mixed" else fdcgks.FP64 for x in a.precisions.split(","))
         res = vortex_convergence(ns=ns, precisions=precs, t_end=a.t_end or 10.0, cfl=a.cfl if a.cfl != 0.4 else 0.2,
-                                 images=1 if a.images is None else a.images, **opt)
+                                 dt_h2=a.dt_h2, images=1 if a.images is None else a.images, **opt)
     elif a.case == "viscous_tube":
         res = viscous_shock_tube(a.nx or 1000, a.ny or 500, prec, a.t_end or 1.0, a.cfl, **opt)
     elif a.case == "double_mach":
