@@ -51,7 +51,8 @@
 //                  the pair form takes the mixed point phase from 1.019 to
 //                  0.903 ms per step and the FP64 one from 32.06 to 31.41 ms
 // FDK_POINT_PAIR_MINB_F32 / _F64  minimum resident blocks per SM of the pair
-//                  kernel (FP32: 2, 3, 4, 5 gave 1.43, 1.06, 0.915, 0.903 ms)
+//                  kernel (FP32 without preload: 2, 3, 4, 5 gave 1.43, 1.06,
+//                  0.915, 0.903 ms; with preload 4 and 5 give 0.822 and 0.840)
 #ifndef FDK_POINT_PAIR_F32
 #define FDK_POINT_PAIR_F32 1
 #endif
@@ -59,7 +60,7 @@
 #define FDK_POINT_PAIR_F64 1
 #endif
 #ifndef FDK_POINT_PAIR_MINB_F32
-#define FDK_POINT_PAIR_MINB_F32 5
+#define FDK_POINT_PAIR_MINB_F32 4
 #endif
 #ifndef FDK_POINT_PAIR_MINB_F64
 #define FDK_POINT_PAIR_MINB_F64 1
@@ -67,9 +68,11 @@
 // FDK_PAIR_PRELOAD_F32  1: a pair-kernel thread loads its line's 32 values (4
 //                  entries x W and the gradient along the line) into registers
 //                  before the first reconstruction, so the loads are not issued
-//                  between the out-of-line reconstruction calls
+//                  between the out-of-line reconstruction calls (mixed point
+//                  phase 0.903 -> 0.840 ms per step at 5 blocks/SM, 0.822 at 4;
+//                  the inlined reconstruction at 4 blocks/SM: 0.914)
 #ifndef FDK_PAIR_PRELOAD_F32
-#define FDK_PAIR_PRELOAD_F32 0
+#define FDK_PAIR_PRELOAD_F32 1
 #endif
 
 namespace fdk {
