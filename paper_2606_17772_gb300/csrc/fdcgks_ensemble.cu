@@ -60,9 +60,15 @@ struct PhaseQ {
   const int* mstat;    // member status bits
 };
 
+// tile width of the points phase in the pair form (two lanes per point, so
+// ENS_THREADS / 2 points per tile): 2^min(lbx, 6)
+__host__ __device__ inline int ens_points_lbx(int lbx) { return lbx < 6 ? lbx : 6; }
+
 template <class R, int PH> struct EnsMinB { static constexpr int v = 1; };
 template <class R> struct EnsMinB<R, PH_NODAL> { static constexpr int v = PointTune<R>::nodal_minb; };
-template <class R> struct EnsMinB<R, PH_POINTS> { static constexpr int v = PointTune<R>::minb; };
+template <class R> struct EnsMinB<R, PH_POINTS> {
+  static constexpr int v = PointTune<R>::pair ? PointTune<R>::pair_minb : PointTune<R>::minb;
+};
 template <class R> struct EnsMinB<R, PH_UPDATE> { static constexpr int v = PointTune<R>::update_minb; };
 
 template <class R>
@@ -104,8 +110,18 @@ __global__ void __launch_bounds__(ENS_THREADS, (EnsMinB<R, PH>::v)) ens_phase_ke
       } else if (PH == PH_NODAL) {
         nodal_body(sa, tl.y, i - 1, j - 1);
       } else if (PH == PH_POINTS) {
-        if (tl.y == 0) point_body<R, 0>(sa, i - 2, j - 2);
-        else point_body<R, 1>(sa, i - 2, j - 2);
+        if constexpr (PointTune<R>::pair) {
+          // two lanes per point (point_pair_body): the tile holds ENS_THREADS / 2
+          // points, 2^lbp wide with lbp = min(lbx, 6) (ens_points_lbx)
+          const int lbp = ens_points_lbx(q.lbx), pi = threadIdx.x >> 1;
+          const int pi_x = (tl.z << lbp) + (pi & ((1 << lbp) - 1));
+          const int pj = tl.w * ((ENS_THREADS / 2) >> lbp) + (pi >> lbp);
+          if (tl.y == 0) point_pair_body<R, 0, false>(sa, pi_x - 2, pj - 2, threadIdx.x & 1);
+          else point_pair_body<R, 1, false>(sa, pi_x - 2, pj - 2, threadIdx.x & 1);
+        } else {
+          if (tl.y == 0) point_body<R, 0>(sa, i - 2, j - 2);
+          else point_body<R, 1>(sa, i - 2, j - 2);
+        }
       } else {
         update_body(sa, q.stage == 0 ? UPD_STAGE1 : UPD_STAGE2, tl.y, i, j);
       }
@@ -410,10 +426,22 @@ fdcgks_status build_tiles(fdcgks_ens_t e) {
             break;
           }
           case PH_NODAL: rect(m, g, nxg + 2, nyg + 2, e->cfg.lbx[0]); break;
-          case PH_POINTS:   // kind = point type: A (g = 0) over (nx + 3) x (nyd + 3), B over (nxd + 3) x (ny + 3)
-            if (g == 0) rect(m, 0, L.nx + 3, L.nyd + 3, e->cfg.lbx[1]);
-            else rect(m, 1, L.nxd + 3, L.ny + 3, e->cfg.lbx[1]);
+          case PH_POINTS: {  // kind = point type: A (g = 0) over (nx + 3) x (nyd + 3), B over (nxd + 3) x (ny + 3)
+            const bool pair = e->precision == FDCGKS_MIXED ? PointTune<float>::pair : PointTune<double>::pair;
+            if (pair) {
+              // ENS_THREADS / 2 points per tile, 2^lbp wide
+              const int lbp = ens_points_lbx(e->cfg.lbx[1]);
+              const int bx = 1 << lbp, by = (ENS_THREADS / 2) >> lbp;
+              const int w = g == 0 ? L.nx + 3 : L.nxd + 3, h = g == 0 ? L.nyd + 3 : L.ny + 3;
+              for (int ty = 0; ty < (h + by - 1) / by; ++ty)
+                for (int tx = 0; tx < (w + bx - 1) / bx; ++tx) t.push_back(make_int4(m, g, tx, ty));
+            } else if (g == 0) {
+              rect(m, 0, L.nx + 3, L.nyd + 3, e->cfg.lbx[1]);
+            } else {
+              rect(m, 1, L.nxd + 3, L.ny + 3, e->cfg.lbx[1]);
+            }
             break;
+          }
           case PH_UPDATE: rect(m, g, nxg, nyg, e->cfg.lbx[2]); break;
           case PH_CFL: {
             const long nn = (long)nxg * nyg;
