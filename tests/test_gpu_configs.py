@@ -63,24 +63,28 @@ def _split(errs):
     return w, g
 
 
-def test_viscous_tube_within_oracle_spread():
-    """40 x 20 tube, the oracle's 20 CFL-0.4 steps replayed.  Where the
-    diaphragm meets the no-slip wall the scheme amplifies any perturbation by
-    about 1e10 in these 20 steps (the oracle's own response to a 1e-15
-    relative change of the initial data reaches ~1e-5), so neither path can
-    agree pointwise with the oracle to its rounding.  The bound is the
-    oracle's own spread under a perturbation of the size of each path's
-    rounding: FP64 within max(1e-10, 100 x the spread at 1e-15); the mixed
-    path (FP32 arithmetic, rounding ~6e-8) within 10 x the spread at 1e-7, or
-    its one-step bounds (1e-6 values, 2e-5 gradients) where that is larger."""
-    case = inputs.viscous_shock_tube(40, 20)
+@pytest.mark.parametrize("nx,ny,t_end", [(40, 20, None), (120, 60, 0.006)])
+def test_viscous_tube_within_oracle_spread(nx, ny, t_end):
+    """The viscous tube (Sec. 5.8 constants), the oracle's CFL-0.4 steps
+    replayed: 40 x 20 over 20 steps, and 120 x 60 to t = 0.006, past the
+    time (t ~ 0.002-0.005) at which the 1000 x 500 runs left the physical
+    states with the Sec. 3.2 GENO constants and c2 = 1.  Where the diaphragm
+    meets the no-slip wall the scheme amplifies any perturbation strongly
+    (about 1e10 in 20 steps on the 40 x 20 tube), so neither path can agree
+    pointwise with the oracle to its rounding.  The bound is the oracle's own
+    spread under a perturbation of the size of each path's rounding: FP64
+    within max(1e-10, 100 x the spread at 1e-15); the mixed path (FP32
+    arithmetic, rounding ~6e-8) within 10 x the spread at 1e-7, or its
+    one-step bounds (1e-6 values, 2e-5 gradients) where that is larger."""
+    case = inputs.viscous_shock_tube(nx, ny)
     p = oracle.make_params(**case.oracle_kwargs())
     S0 = case.initial_state()
     S = S0
-    dts = []
-    for _ in range(20):
+    dts, t = [], 0.0
+    while (t_end is None and len(dts) < 20) or (t_end is not None and t < t_end):
         dts.append(oracle.cfl_dt(p, 0.4, S[0], S[2]))
         S = oracle.steps(p, dts[-1], 1, *S)
+        t += dts[-1]
 
     def spread(rel):
         rng = np.random.default_rng(1)
