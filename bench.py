@@ -410,8 +410,7 @@ def run_viscous_tube(args, world):
     case = inputs.viscous_shock_tube(1000, 500)
     nodes = case.nx * case.ny + case.nxd * case.nyd
     out = {"config": {"workload": "viscous shock tube, [0,1]x[0,0.5], 1000x500 (+1001x501 dual), Re 200, "
-                                  "Pr 0.73, no-slip walls, symmetry top, GENO App. D, tau c2 = 25; window "
-                                  "after 10 CFL-0.4 steps",
+                                  "Pr 0.73, no-slip walls, symmetry top; window after 10 CFL-0.4 steps",
                       "node_updates_per_step": nodes}}
     for name, prec, k in (("fp64", fdcgks.FP64, args.vt_steps), ("mixed", fdcgks.MIXED, 10 * args.vt_steps)):
         with fdcgks.Solver.from_case(case, prec) as s:

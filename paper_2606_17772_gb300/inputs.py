@@ -286,18 +286,18 @@ def viscous_shock_tube(nx=1000, ny=500, gamma=1.4, mu=0.005, Pr=0.73, **kw):
     """Sec. 5.8: [0,1] x [0,0.5], diaphragm x = 0.5, (120,0,0,120/gamma) | (1.2,0,0,1.2/gamma).
 
     No-slip adiabatic walls left, right and bottom; symmetry at y = 0.5.
-    GENO constants default to App. D's and the numerical collision time to
-    c2 = 25 (as for the double Mach reflection): on 1000 x 500 both the FP64
-    and the mixed-precision runs then reach t = 1, while with the Sec. 3.2
-    constants and c2 = 1 both leave the physical states by t = 0.005 where the
-    diaphragm meets the no-slip wall.
+    Defaults: the Sec. 3.2 GENO constants and tau c2 = 1.  On 1000 x 500 both
+    precisions leave the physical states with these by t = 0.005 where the
+    diaphragm meets the no-slip wall; geno_variant=1, tau_c2=25.0 carried one
+    FP64 and one mixed run to t = 1, but leave the physical states on coarse
+    grids (40 x 20) within a few steps, so they are a run option, not the
+    default.
     """
     def prim(x, y):
         right = x >= 0.5
         rho = np.where(right, 1.2, 120.0)
         return rho, 0.0, 0.0, rho / gamma
-    kw.setdefault("tau_c2", 25.0)
-    kw.setdefault("geno_variant", 1)
+    kw.setdefault("tau_c2", 1.0)
     return Case("viscous_shock_tube", nx, ny, 0.0, 1.0, 0.0, 0.5,
                 (BC_NOSLIP, BC_NOSLIP, BC_NOSLIP, BC_SYMMETRY), gamma=gamma, mu=mu, Pr=Pr,
                 prim=prim, **kw)

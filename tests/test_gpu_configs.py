@@ -67,8 +67,8 @@ def _split(errs):
 def test_viscous_tube_within_oracle_spread(nx, ny, t_end):
     """The viscous tube (Sec. 5.8 constants), the oracle's CFL-0.4 steps
     replayed: 40 x 20 over 20 steps, and 120 x 60 to t = 0.006, past the
-    time (t ~ 0.002-0.005) at which the 1000 x 500 runs left the physical
-    states with the Sec. 3.2 GENO constants and c2 = 1.  Where the diaphragm
+    time (t ~ 0.002-0.005) at which the 1000 x 500 runs leave the physical
+    states with these constants.  Where the diaphragm
     meets the no-slip wall the scheme amplifies any perturbation strongly
     (about 1e10 in 20 steps on the 40 x 20 tube), so neither path can agree
     pointwise with the oracle to its rounding.  The bound is the oracle's own
