@@ -822,6 +822,14 @@ def main():
         equiv = {k: args.steps for k in ("points", "nodal", "update", "ghost")}
         equiv["cfl"] = 5
         kf = kernel_fractions(work, pms, pn, equiv, peaks, hbm)
+        # measured DRAM bytes per launch (profiles/dram_traffic.json) beside the
+        # algorithmic bytes per launch (a step launches 4 point, 2 nodal, 2 update kernels)
+        rt = "double" if name == "fp64" else "float"
+        for cls, kname, per_step in (("points", "point_pair_kernel<%s>" % rt, 4), ("nodal", "nodal_kernel<%s>" % rt, 2),
+                                     ("update", "update_kernel<%s>" % rt, 2)):
+            if cls in kf:
+                kf[cls]["algorithmic_bytes_per_launch"] = work[cls][2] / per_step
+                kf[cls]["dram_bytes_per_launch"] = profiled_traffic(kname, n)
         results[name] = dict(ms=ms_max, prof_ms=pms, prof_n=pn, launches=launches, clocks=clocks, dt=dt, cnt=cnt,
                              kernels=kf, state=[t.cpu().numpy() for t in out] if rank == 0 else None)
 
@@ -831,7 +839,7 @@ def main():
     step_ms = {k: v for k, v in fp["prof_ms"].items() if k != "cfl"}
     pk = fp["kernels"]["points"]
     roof = {"bound": "alu", "achieved": pk["achieved_tflops"], "peak": peaks["fp64"], "unit": "TFLOP/s",
-            "frac": pk["alu_frac"], "traffic": profiled_traffic("point_kernel<double>", n),
+            "frac": pk["alu_frac"], "traffic": profiled_traffic("point_pair_kernel<double>", n),
             "kernel": "point_kernel<double> (Type A + B interface points)",
             "peak_source": "measured FP64 FMA pipe (csrc/pipe_peak.cu), this run",
             "step_share": step_ms["points"] / max(sum(step_ms.values()), 1e-9)}
