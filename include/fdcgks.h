@@ -132,13 +132,20 @@ fdcgks_status fdcgks_steps(fdcgks_t ctx, double dt, int nsteps);
  * cfl * min(hx,hy)^2 / (8 nu_max), nu = mu/rho.  Synchronizes the stream.
  * The bound is per direction: for smooth flow oblique to the grid, cfl 0.4
  * lets the scheme's grid-scale diagonal modes grow slowly (visible over
- * thousands of steps, first in mixed precision); cfl 0.2 is stable. */
+ * thousands of steps, first in mixed precision); cfl 0.2 is stable.
+ * Evaluated in FP64 (on the joined float-float pairs in a mixed context) at
+ * the nodes that can hold the maxima: a first pass takes FP32 estimates of
+ * every node's rates, a second evaluates the FP64 rates only where the
+ * estimate is unreliable or within a relative 5e-5 of the largest estimate,
+ * which is more than twice the estimates' error; the result equals the
+ * all-node FP64 value. */
 fdcgks_status fdcgks_cfl_dt(fdcgks_t ctx, double cfl, double* dt_out);
 
 /* The two-dimensional form of the same bound: cfl / max over all nodes of
  * both grids of ((|U|+c)/hx + (|V|+c)/hy), with the same viscous bound.  At
  * most the per-direction step, half of it for flow at 45 degrees; cfl 0.4 in
- * this form is stable for smooth oblique flow.  Synchronizes the stream. */
+ * this form is stable for smooth oblique flow.  Synchronizes the stream;
+ * evaluated with the same screening. */
 fdcgks_status fdcgks_cfl_dt_sum(fdcgks_t ctx, double cfl, double* dt_out);
 
 /* Read and clear the device non-physical flag (synchronizes the stream).

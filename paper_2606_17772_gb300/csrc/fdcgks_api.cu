@@ -1,5 +1,7 @@
 // Host runtime and C entry points of the FD-CGKS library: context and device
 // buffers, ghost-layer fill, CFL reduction, stage sequencing of the S2O4 step.
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -243,51 +245,113 @@ __device__ void cfl_rates_sum(double r, double ru, double rv, double E, double g
 }
 
 // the state the CFL reduction reads: FP64 entries, or the mixed path's
-// float-float pairs joined in FP64 (no FP64 copy of the state is made)
+// float-float pairs joined in FP64 (no FP64 copy of the state is made); est
+// gives the FP32 rounding of an entry (the high part of a pair)
 struct StateF64 {
   const double* S;
   __device__ double operator()(long k) const { return S[k]; }
+  __device__ float est(long k) const { return (float)S[k]; }
 };
 struct StatePair {
   const float* hi;
   const float* lo;
   __device__ double operator()(long k) const { return (double)hi[k] + (double)lo[k]; }
+  __device__ float est(long k) const { return hi[k]; }
 };
 
-template <class ST>
-__global__ void cfl_kernel(ST S, Layout L, double gamma, double mu, double ihx, double ihy, int sum, double* out) {
-  double rate = 0.0, numax = 0.0;
-  const long n0 = (long)L.nx * L.ny, n1 = (long)L.nxd * L.nyd;
-  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n0 + n1; t += (long)gridDim.x * blockDim.x) {
-    int g = t < n0 ? 0 : 1;
-    long q = g == 0 ? t : t - n0;
-    int nxg = g == 0 ? L.nx : L.nxd;
-    int i = (int)(q % nxg), j = (int)(q / nxg);
-    const long c0 = (long)g * NFLD * L.plane + cell(L, i, j);
-    const double r = S(c0), ru = S(L.plane + c0), rv = S(2 * L.plane + c0), E = S(3 * L.plane + c0);
-    if (sum)
-      cfl_rates_sum(r, ru, rv, E, gamma, mu, ihx, ihy, rate, numax);
-    else
-      cfl_rates(r, ru, rv, E, gamma, mu, ihx, ihy, rate, numax);
-  }
-  // warp-shuffle max, then across warps in shared memory
+// Work split of the CFL passes: the rows of both grids (primary first), each
+// cut into segments of CFL_SEG nodes; an item is one segment of one row.
+// The FP32 constants of the screening go with it.
+const int CFL_SEG = 1024;
+struct CflGrid {
+  Layout L;
+  int segs;   // segments per row (of the wider grid)
+  double gamma, mu, ihx, ihy;
+  float gf, muf, ihxf, ihyf;
+  int sum;
+};
+
+// Calls f(c0) for the node offset c0 of every node of item `it`
+template <class F>
+__device__ __forceinline__ void cfl_item(const CflGrid& G, int it, F f) {
+  const Layout& L = G.L;
+  const int row = it / G.segs, seg = it - row * G.segs;
+  const int g = row < L.ny ? 0 : 1, j = g == 0 ? row : row - L.ny;
+  const int nxg = g == 0 ? L.nx : L.nxd;
+  const int i1 = min(nxg, (seg + 1) * CFL_SEG);
+  const long base = (long)g * NFLD * L.plane;
+  for (int i = seg * CFL_SEG + threadIdx.x; i < i1; i += blockDim.x) f(base + cell(L, i, j));
+}
+
+// block-wide maxima of two values (>= 0) into thread 0; blockDim.x <= 1024
+template <class T>
+__device__ __forceinline__ void block_max2(T& a, T& b, T* sa, T* sb) {
   for (int o = 16; o > 0; o >>= 1) {
-    rate = fmax(rate, __shfl_xor_sync(0xffffffffu, rate, o));
-    numax = fmax(numax, __shfl_xor_sync(0xffffffffu, numax, o));
+    a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+    b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
   }
-  __shared__ double sr[32], sn[32];
-  int w = threadIdx.x / 32, l = threadIdx.x % 32;
-  if (l == 0) { sr[w] = rate; sn[w] = numax; }
+  const int w = threadIdx.x / 32;
+  if ((threadIdx.x & 31) == 0) { sa[w] = a; sb[w] = b; }
   __syncthreads();
-  if (w == 0) {
-    int nw = blockDim.x / 32;
-    rate = l < nw ? sr[l] : 0.0;
-    numax = l < nw ? sn[l] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) {
-      rate = fmax(rate, __shfl_xor_sync(0xffffffffu, rate, o));
-      numax = fmax(numax, __shfl_xor_sync(0xffffffffu, numax, o));
-    }
-    if (l == 0) { out[2 * blockIdx.x] = rate; out[2 * blockIdx.x + 1] = numax; }
+  if (threadIdx.x == 0)
+    for (int k = 1; k < (int)(blockDim.x / 32); ++k) { a = fmax(a, sa[k]); b = fmax(b, sb[k]); }
+}
+
+// First pass: the largest reliable FP32 estimates (cfl_estimate_f) of the
+// rate and of nu over all nodes, folded into mxf[0..1] (zeroed before) with
+// atomicMax on the bit patterns (non-negative floats order as their bits).
+template <class ST>
+__global__ void cfl_screen_kernel(ST S, CflGrid G, int items, unsigned* mxf) {
+  __shared__ float sa[32], sb[32];
+  float mr = 0.0f, mn = 0.0f;
+  const long P = G.L.plane;
+  for (int it = blockIdx.x; it < items; it += gridDim.x)
+    cfl_item(G, it, [&](long c0) {
+      float rt, nu;
+      bool ok;
+      cfl_estimate_f(S.est(c0), S.est(c0 + P), S.est(c0 + 2 * P), S.est(c0 + 3 * P), G.gf, G.muf, G.ihxf, G.ihyf,
+                     G.sum != 0, rt, nu, ok);
+      if (ok) {
+        mr = fmaxf(mr, rt);
+        mn = fmaxf(mn, nu);
+      }
+    });
+  block_max2(mr, mn, sa, sb);
+  if (threadIdx.x == 0) {
+    if (mr > 0.0f) atomicMax(mxf, __float_as_uint(mr));
+    if (mn > 0.0f) atomicMax(mxf + 1, __float_as_uint(mn));
+  }
+}
+
+// Second pass: per-block maxima of the FP64 rate and nu, evaluated (from the
+// FP64 entries or the joined pairs) only at nodes whose estimate is
+// unreliable or within CFL_SCREEN_MARGIN of the first pass's maxima; the
+// maxima are exactly those of evaluating every node.
+template <class ST>
+__global__ void cfl_kernel(ST S, CflGrid G, int items, const unsigned* mxf, double* out) {
+  __shared__ double sa[32], sb[32];
+  double rate = 0.0, numax = 0.0;
+  const long P = G.L.plane;
+  const float mr = __uint_as_float(mxf[0]), mn = __uint_as_float(mxf[1]);
+  const float tr = mr * (1.0f - CFL_SCREEN_MARGIN);
+  const float tn = mn > 0.0f ? mn * (1.0f - CFL_SCREEN_MARGIN) : INFINITY;   // mu = 0: nu never decides
+  for (int it = blockIdx.x; it < items; it += gridDim.x)
+    cfl_item(G, it, [&](long c0) {
+      float rt, nu;
+      bool ok;
+      cfl_estimate_f(S.est(c0), S.est(c0 + P), S.est(c0 + 2 * P), S.est(c0 + 3 * P), G.gf, G.muf, G.ihxf, G.ihyf,
+                     G.sum != 0, rt, nu, ok);
+      if (ok && rt < tr && nu < tn) return;
+      const double r = S(c0), ru = S(c0 + P), rv = S(c0 + 2 * P), E = S(c0 + 3 * P);
+      if (G.sum)
+        cfl_rates_sum(r, ru, rv, E, G.gamma, G.mu, G.ihx, G.ihy, rate, numax);
+      else
+        cfl_rates(r, ru, rv, E, G.gamma, G.mu, G.ihx, G.ihy, rate, numax);
+    });
+  block_max2(rate, numax, sa, sb);
+  if (threadIdx.x == 0) {
+    out[2 * blockIdx.x] = rate;
+    out[2 * blockIdx.x + 1] = numax;
   }
 }
 
@@ -508,7 +572,8 @@ fdcgks_status fdcgks_create(const fdcgks_params* p, fdcgks_t* out) {
     }
   }
   c->red_blocks = 1024;
-  if (cudaMalloc((void**)&c->red, sizeof(double) * 2 * c->red_blocks) != cudaSuccess) {
+  // per-block maxima, then the two screening maxima (2 unsigned in one more double)
+  if (cudaMalloc((void**)&c->red, sizeof(double) * (2 * c->red_blocks + 1)) != cudaSuccess) {
     fdcgks_destroy(c);
     return fail(nullptr, FDCGKS_ERR_NOMEM, "cudaMalloc of the reduction scratch failed");
   }
@@ -550,20 +615,78 @@ static cudaError_t copy_field(fdcgks_t c, double* dev_plane, const double* src, 
                            c->stream);
 }
 
+// Dense state [grid][field][nyg][nxg] (the four caller arrays back to back:
+// Wp, Gp, Wd, Gd) <-> the padded layout of both grids, on the device.
+// blockIdx.z = grid * NFLD + field; rows strided over gridDim.y.
+__global__ void dense_padded_kernel(double* dense, double* S, Layout L, int to_padded) {
+  const int g = blockIdx.z / NFLD, f = blockIdx.z % NFLD;
+  const int nxg = g == 0 ? L.nx : L.nxd, nyg = g == 0 ? L.ny : L.nyd;
+  const long goff = g == 0 ? 0 : (long)NFLD * L.nx * L.ny;
+  double* Sf = S + ((long)g * NFLD + f) * L.plane;
+  for (int j = blockIdx.y; j < nyg; j += gridDim.y) {
+    double* d = dense + goff + ((long)f * nyg + j) * nxg;
+    double* p = Sf + cell(L, 0, j);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nxg; i += gridDim.x * blockDim.x) {
+      if (to_padded) p[i] = d[i];
+      else d[i] = p[i];
+    }
+  }
+}
+
+// Host state <-> device: the whole state in four contiguous copies through a
+// dense staging area (the point-output buffer, free between steps), and one
+// kernel between the staging area and the padded layout; contiguous copies
+// run at the host link's full rate where per-row (pitched) copies do not.
+// Returns false (nothing done) when the staging area is too small.
+static bool staged_size_ok(fdcgks_t c) {
+  const Layout& L = c->L;
+  const size_t need = sizeof(double) * NFLD * ((size_t)L.nx * L.ny + (size_t)L.nxd * L.nyd);
+  return need <= rsize(c->p) * NPT * (size_t)L.pplane;
+}
+
+static cudaError_t launch_dense_padded(fdcgks_t c, double* dense, int to_padded) {
+  const Layout& L = c->L;
+  const int mx = std::max(L.nx, L.nxd), my = std::max(L.ny, L.nyd);
+  const dim3 grid((unsigned)std::min((mx + 255) / 256, 64), (unsigned)std::min(my, 65535), 2 * NFLD);
+  dense_padded_kernel<<<grid, 256, 0, c->stream>>>(dense, c->S, L, to_padded);
+  return cudaGetLastError();
+}
+
+static cudaError_t host_state_copy(fdcgks_t c, double* const* host, bool to_dev) {
+  const Layout& L = c->L;
+  double* st = (double*)c->PA;
+  const long N0 = (long)L.nx * L.ny, N1 = (long)L.nxd * L.nyd;
+  const long off[4] = {0, 4 * N0, NFLD * N0, NFLD * N0 + 4 * N1};
+  const long len[4] = {4 * N0, 8 * N0, 4 * N1, 8 * N1};
+  cudaError_t e = cudaSuccess;
+  if (!to_dev) e = launch_dense_padded(c, st, 0);
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+    e = to_dev ? cudaMemcpyAsync(st + off[k], host[k], sizeof(double) * len[k], cudaMemcpyHostToDevice, c->stream)
+               : cudaMemcpyAsync(host[k], st + off[k], sizeof(double) * len[k], cudaMemcpyDeviceToHost, c->stream);
+  if (to_dev && e == cudaSuccess) e = launch_dense_padded(c, st, 1);
+  return e;
+}
+
 fdcgks_status fdcgks_set_state(fdcgks_t c, const double* Wp, const double* Gp, const double* Wd, const double* Gd,
                                int on_device) {
   if (!c) return fail(nullptr, FDCGKS_ERR_ARG, "ctx is NULL");
   if (!Wp || !Gp || !Wd || !Gd) return fail(c, FDCGKS_ERR_ARG, "NULL state pointer");
   const Layout& L = c->L;
-  const double* srcW[2] = {Wp, Wd};
-  const double* srcG[2] = {Gp, Gd};
-  for (int g = 0; g < 2; ++g) {
-    int nxg = g == 0 ? L.nx : L.nxd, nyg = g == 0 ? L.ny : L.nyd;
-    long NN = (long)nxg * nyg;
-    double* Sg = c->S + (long)g * NFLD * L.plane;
-    for (int f = 0; f < NFLD; ++f) {
-      const double* src = f < 4 ? srcW[g] + f * NN : srcG[g] + (f - 4) * NN;
-      CUDA_TRY(c, copy_field(c, Sg + (long)f * L.plane, src, nullptr, nxg, nyg, true, on_device));
+  if (!on_device && staged_size_ok(c)) {
+    double* const host[4] = {const_cast<double*>(Wp), const_cast<double*>(Gp), const_cast<double*>(Wd),
+                             const_cast<double*>(Gd)};
+    CUDA_TRY(c, host_state_copy(c, host, true));
+  } else {
+    const double* srcW[2] = {Wp, Wd};
+    const double* srcG[2] = {Gp, Gd};
+    for (int g = 0; g < 2; ++g) {
+      int nxg = g == 0 ? L.nx : L.nxd, nyg = g == 0 ? L.ny : L.nyd;
+      long NN = (long)nxg * nyg;
+      double* Sg = c->S + (long)g * NFLD * L.plane;
+      for (int f = 0; f < NFLD; ++f) {
+        const double* src = f < 4 ? srcW[g] + f * NN : srcG[g] + (f - 4) * NN;
+        CUDA_TRY(c, copy_field(c, Sg + (long)f * L.plane, src, nullptr, nxg, nyg, true, on_device));
+      }
     }
   }
   if (c->Sf) CUDA_TRY(c, launch_split_ff(c->S, c->Sf, c->Slo, 2L * NFLD * L.plane, c->stream));
@@ -588,15 +711,20 @@ fdcgks_status fdcgks_get_state(fdcgks_t c, double* Wp, double* Gp, double* Wd, d
   if (!Wp || !Gp || !Wd || !Gd) return fail(c, FDCGKS_ERR_ARG, "NULL state pointer");
   const Layout& L = c->L;
   CUDA_TRY(c, join_state(c));
-  double* dstW[2] = {Wp, Wd};
-  double* dstG[2] = {Gp, Gd};
-  for (int g = 0; g < 2; ++g) {
-    int nxg = g == 0 ? L.nx : L.nxd, nyg = g == 0 ? L.ny : L.nyd;
-    long NN = (long)nxg * nyg;
-    double* Sg = c->S + (long)g * NFLD * L.plane;
-    for (int f = 0; f < NFLD; ++f) {
-      double* dst = f < 4 ? dstW[g] + f * NN : dstG[g] + (f - 4) * NN;
-      CUDA_TRY(c, copy_field(c, Sg + (long)f * L.plane, nullptr, dst, nxg, nyg, false, on_device));
+  if (!on_device && staged_size_ok(c)) {
+    double* const host[4] = {Wp, Gp, Wd, Gd};
+    CUDA_TRY(c, host_state_copy(c, host, false));
+  } else {
+    double* dstW[2] = {Wp, Wd};
+    double* dstG[2] = {Gp, Gd};
+    for (int g = 0; g < 2; ++g) {
+      int nxg = g == 0 ? L.nx : L.nxd, nyg = g == 0 ? L.ny : L.nyd;
+      long NN = (long)nxg * nyg;
+      double* Sg = c->S + (long)g * NFLD * L.plane;
+      for (int f = 0; f < NFLD; ++f) {
+        double* dst = f < 4 ? dstW[g] + f * NN : dstG[g] + (f - 4) * NN;
+        CUDA_TRY(c, copy_field(c, Sg + (long)f * L.plane, nullptr, dst, nxg, nyg, false, on_device));
+      }
     }
   }
   if (!on_device) CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -631,14 +759,36 @@ static fdcgks_status cfl_dt_impl(fdcgks_t c, double cfl, int sum, double* dt_out
   if (!c || !dt_out) return fail(c, FDCGKS_ERR_ARG, "NULL argument");
   if (!c->has_state) return fail(c, FDCGKS_ERR_STATE, "no state loaded");
   if (!(cfl > 0.0) || !std::isfinite(cfl)) return fail(c, FDCGKS_ERR_ARG, "cfl must be positive and finite");
+  CflGrid G;
+  G.L = c->L;
+  G.segs = (std::max(c->L.nx, c->L.nxd) + CFL_SEG - 1) / CFL_SEG;
+  G.gamma = c->p.gamma;
+  G.mu = c->p.mu;
+  G.ihx = 1.0 / c->hx;
+  G.ihy = 1.0 / c->hy;
+  G.gf = (float)G.gamma;
+  G.muf = (float)G.mu;
+  G.ihxf = (float)G.ihx;
+  G.ihyf = (float)G.ihy;
+  G.sum = sum;
+  const long items = (long)(c->L.ny + c->L.nyd) * G.segs;
+  if (items > INT_MAX) return fail(c, FDCGKS_ERR_ARG, "grid too large for the CFL reduction");
+  unsigned* mxf = (unsigned*)(c->red + 2 * c->red_blocks);
   CUDA_TRY(c, prof_mark(c, KC_CFL, true));
-  if (c->Sf)
-    cfl_kernel<<<c->red_blocks, 256, 0, c->stream>>>(StatePair{c->Sf, c->Slo}, c->L, c->p.gamma, c->p.mu, 1.0 / c->hx,
-                                                     1.0 / c->hy, sum, c->red);
-  else
-    cfl_kernel<<<c->red_blocks, 256, 0, c->stream>>>(StateF64{c->S}, c->L, c->p.gamma, c->p.mu, 1.0 / c->hx,
-                                                     1.0 / c->hy, sum, c->red);
+  CUDA_TRY(c, cudaMemsetAsync(mxf, 0, 2 * sizeof(unsigned), c->stream));
+  if (c->Sf) {
+    const StatePair st{c->Sf, c->Slo};
+    cfl_screen_kernel<<<c->red_blocks, 256, 0, c->stream>>>(st, G, (int)items, mxf);
+    CUDA_TRY(c, cudaGetLastError());
+    cfl_kernel<<<c->red_blocks, 256, 0, c->stream>>>(st, G, (int)items, mxf, c->red);
+  } else {
+    const StateF64 st{c->S};
+    cfl_screen_kernel<<<c->red_blocks, 256, 0, c->stream>>>(st, G, (int)items, mxf);
+    CUDA_TRY(c, cudaGetLastError());
+    cfl_kernel<<<c->red_blocks, 256, 0, c->stream>>>(st, G, (int)items, mxf, c->red);
+  }
   CUDA_TRY(c, cudaGetLastError());
+  c->launches += 2;
   CUDA_TRY(c, prof_mark(c, KC_CFL, false));
   double* h = new double[2 * c->red_blocks];
   cudaError_t e = cudaMemcpyAsync(h, c->red, sizeof(double) * 2 * c->red_blocks, cudaMemcpyDeviceToHost, c->stream);

@@ -137,26 +137,12 @@ __device__ __forceinline__ double state_at(const KArgs<float>& a, long off) {
 }
 
 // FP32 estimate of one node's CFL rate and viscosity from the high parts of
-// the mixed state.  Reliable (relative error below 3e-6 against the FP64
-// formula on the joined pair) while p > 0.05 E: the inputs carry 2^-24
-// relative error, E - rho(U^2+V^2)/2 loses a factor E/p < 20 of it, and
-// the sound speed halves what reaches p.  Otherwise *ok is false.
+// the mixed state (cfl_estimate_f: reliable to 1e-5 while p > 0.05 E)
 __device__ __forceinline__ void cfl_estimate(const float* hi, long c0, long plane, float gf, float muf, float ihxf,
                                              float ihyf, float& rt, float& nu, bool& ok) {
-  const float r = hi[c0], ru = hi[c0 + plane], rv = hi[c0 + 2 * plane], E = hi[c0 + 3 * plane];
-  const float ir = __fdividef(1.0f, r), U = ru * ir, V = rv * ir;
-  const float p = (gf - 1.0f) * (E - 0.5f * r * (U * U + V * V));
-  const float c = sqrtf(fmaxf(gf * p * ir, 0.0f));
-  rt = fmaxf((fabsf(U) + c) * ihxf, (fabsf(V) + c) * ihyf);
-  nu = muf * ir;
-  ok = r > 0.0f && p > 0.05f * E && rt < INFINITY && nu < INFINITY;
+  cfl_estimate_f(hi[c0], hi[c0 + plane], hi[c0 + 2 * plane], hi[c0 + 3 * plane], gf, muf, ihxf, ihyf, false, rt, nu,
+                 ok);
 }
-
-// margin of the screening: a node is evaluated in FP64 when its estimate is
-// within this fraction of the member's largest reliable estimate (more than
-// twice the estimates' error bound, so the nodes holding the FP64 maxima are
-// always evaluated)
-const float SCREEN_MARGIN = 2e-5f;
 
 // mixed path, first pass: each member's largest reliable FP32 estimates,
 // folded with atomicMax on the bit patterns (non-negative floats)
@@ -211,7 +197,7 @@ __global__ void __launch_bounds__(ENS_THREADS) ens_cfl_screen_kernel(const KArgs
 // atomicMax on the bit patterns (both maxima are >= 0, where the order of the
 // patterns is the order of the values).  FP64 path: every node evaluated.
 // Mixed path: the FP64 rates (from the joined float-float pairs) only where
-// the FP32 estimate is unreliable or within SCREEN_MARGIN of the member's
+// the FP32 estimate is unreliable or within CFL_SCREEN_MARGIN of the member's
 // largest estimate (first pass); the maxima are exactly those of evaluating
 // every node.
 template <class R>
@@ -234,8 +220,8 @@ __global__ void __launch_bounds__(ENS_THREADS) ens_cfl_kernel(const KArgs<R>* ar
       float tr = 0.0f, tn = INFINITY;
       if constexpr (IsF32<R>::v) {
         const float mr = __uint_as_float(mxf[2 * m]), mn = __uint_as_float(mxf[2 * m + 1]);
-        tr = mr * (1.0f - SCREEN_MARGIN);
-        if (mn > 0.0f) tn = mn * (1.0f - SCREEN_MARGIN);   // with mu = 0 nu never decides
+        tr = mr * (1.0f - CFL_SCREEN_MARGIN);
+        if (mn > 0.0f) tn = mn * (1.0f - CFL_SCREEN_MARGIN);   // with mu = 0 nu never decides
       }
       for (int k = threadIdx.x; k < CFL_TILE; k += ENS_THREADS) {
         const int n = tl.z + k;

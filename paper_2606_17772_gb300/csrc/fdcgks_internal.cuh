@@ -66,6 +66,35 @@ FD_HD void cfl_rates(double r, double ru, double rv, double E, double gamma, dou
   numax = fmax(numax, mu * ir);
 }
 
+#ifdef __CUDACC__
+// FP32 estimate of one node's CFL rate (the form of cfl_rates, or with sum
+// set the two directions' rates added) and of mu/rho, from FP32 roundings
+// (relative error <= u = 2^-24) of the node's conservative variables; used
+// to screen out the nodes that cannot hold the FP64 maxima.  Reliable, i.e.
+// within a relative 1e-5 of the FP64 formula on the unrounded values, while
+// 1e-30 < rho < 1e30 and p > 0.05 E: U and V carry about 5u, the kinetic
+// energy about 12u of itself, so E - rho (U^2+V^2)/2 carries at most about
+// (u E + 12u (E - p))/p < 250u of p (E/p < 20); the sound speed halves that,
+// giving < 130u ~ 7.8e-6 in the rate.  Otherwise ok is false.
+__device__ __forceinline__ void cfl_estimate_f(float r, float ru, float rv, float E, float gf, float muf, float ihxf,
+                                               float ihyf, bool sum, float& rt, float& nu, bool& ok) {
+  const float ir = __fdividef(1.0f, r), U = ru * ir, V = rv * ir;
+  const float p = (gf - 1.0f) * (E - 0.5f * r * (U * U + V * V));
+  const float c = sqrtf(fmaxf(gf * p * ir, 0.0f));
+  const float ax = (fabsf(U) + c) * ihxf, ay = (fabsf(V) + c) * ihyf;
+  rt = sum ? ax + ay : fmaxf(ax, ay);
+  nu = muf * ir;
+  ok = r > 1e-30f && r < 1e30f && p > 0.05f * E && rt < INFINITY && nu < INFINITY;
+}
+
+// Margin of the screening: a node is evaluated in FP64 when its estimate is
+// not below the largest reliable estimate by more than this fraction.  With
+// the estimates' bound b = 1e-5, (1 - margin)(1 + b)^2 < 1, so a node left
+// out has an FP64 rate below that of the node holding the largest estimate:
+// the maxima are exactly those of evaluating every node.
+const float CFL_SCREEN_MARGIN = 5e-5f;
+#endif
+
 template <class R>
 struct KArgs {
   Layout L;

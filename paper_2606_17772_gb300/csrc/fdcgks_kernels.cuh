@@ -12,7 +12,10 @@
 //                  (caps registers per thread), per compute type
 // FDK_UPDATE_MINB_F32, FDK_NODAL_MINB_F32  the same for the FP32 update and
 //                  nodal kernels (the FP64 kernels are FP64-pipe bound and
-//                  are left uncapped)
+//                  are left uncapped).  1024^2 vortex, ms per mixed step:
+//                  update 4, 5, 6, 8 gave 0.448, 0.411, 0.382, 0.437; nodal
+//                  5, 6, 8, 10, 12, 16 gave 0.303, 0.264, 0.234, 0.221, 0.225,
+//                  0.332
 // FDK_SOLVE_NOINLINE  1: the kinetic solve is an out-of-line function called
 //                  twice (one code copy per kernel), 0: inlined twice.  With the
 //                  reconstruction also out of line (below) the smaller code
@@ -28,7 +31,7 @@
 #define FDK_UPDATE_MINB_F32 6
 #endif
 #ifndef FDK_NODAL_MINB_F32
-#define FDK_NODAL_MINB_F32 8
+#define FDK_NODAL_MINB_F32 10
 #endif
 #ifndef FDK_SOLVE_NOINLINE_F64
 #define FDK_SOLVE_NOINLINE_F64 1
@@ -614,40 +617,49 @@ __device__ __forceinline__ void update_body(const KArgs<R>& a, int mode, int g, 
     float* Al = a.Acc_lo + (long)g * 4 * P;
     float* Bh = a.Gb_hi + (long)g * 8 * P;
     float* Bl = a.Gb_lo + (long)g * 8 * P;
+    // every input pair is loaded before the first store, so that the loads
+    // are issued together (the stores could alias them for the compiler)
+    if (mode == UPD_STAGE1) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      if (mode == UPD_STAGE1) {
-        float wh = Snh[(long)c * P + c0], wl = Snl[(long)c * P + c0];
-        float sh = wh, sl = wl;
-        ff_add(sh, sl, 0.5f * dtr * o.L[c] + 0.125f * dtr * dtr * o.Lt[c]);
-        Wh[c] = sh;
-        Wl[c] = sl;
+      for (int c = 0; c < 4; ++c) {
+        Wh[c] = Snh[(long)c * P + c0];
+        Wl[c] = Snl[(long)c * P + c0];
+      }
+#pragma unroll
+      for (int f = 0; f < 8; ++f) {
+        Gh[f] = a.grad_base ? Snh[(long)(4 + f) * P + c0] : (f < 4 ? o.gbx[f] : o.gby[f - 4]);
+        Gl[f] = a.grad_base ? Snl[(long)(4 + f) * P + c0] : 0.0f;
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float wh = Wh[c], wl = Wl[c];
+        ff_add(Wh[c], Wl[c], 0.5f * dtr * o.L[c] + 0.125f * dtr * dtr * o.Lt[c]);
         float ah = wh, al = wl;
         ff_add(ah, al, dtr * o.L[c] + dtr * dtr * (1.0f / 6.0f) * o.Lt[c]);
         Ah[(long)c * P + c0] = ah;
         Al[(long)c * P + c0] = al;
-        for (int d = 0; d < 2; ++d) {
-          const int f = 4 + 4 * d + c;
-          float bh = a.grad_base ? Snh[(long)f * P + c0] : (d == 0 ? o.gbx[c] : o.gby[c]);
-          float bl = a.grad_base ? Snl[(long)f * P + c0] : 0.0f;
-          Bh[(long)(4 * d + c) * P + c0] = bh;
-          Bl[(long)(4 * d + c) * P + c0] = bl;
-          ff_add(bh, bl, 0.5f * dtr * (d == 0 ? o.gtx[c] : o.gty[c]));
-          Gh[4 * d + c] = bh;
-          Gl[4 * d + c] = bl;
-        }
-      } else {
-        float wh = Ah[(long)c * P + c0], wl = Al[(long)c * P + c0];
-        ff_add(wh, wl, dtr * dtr * (1.0f / 3.0f) * o.Lt[c]);
-        Wh[c] = wh;
-        Wl[c] = wl;
-        for (int d = 0; d < 2; ++d) {
-          float bh = Bh[(long)(4 * d + c) * P + c0], bl = Bl[(long)(4 * d + c) * P + c0];
-          ff_add(bh, bl, dtr * (d == 0 ? o.gtx[c] : o.gty[c]));
-          Gh[4 * d + c] = bh;
-          Gl[4 * d + c] = bl;
-        }
       }
+#pragma unroll
+      for (int f = 0; f < 8; ++f) {
+        Bh[(long)f * P + c0] = Gh[f];
+        Bl[(long)f * P + c0] = Gl[f];
+        ff_add(Gh[f], Gl[f], 0.5f * dtr * (f < 4 ? o.gtx[f] : o.gty[f - 4]));
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        Wh[c] = Ah[(long)c * P + c0];
+        Wl[c] = Al[(long)c * P + c0];
+      }
+#pragma unroll
+      for (int f = 0; f < 8; ++f) {
+        Gh[f] = Bh[(long)f * P + c0];
+        Gl[f] = Bl[(long)f * P + c0];
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) ff_add(Wh[c], Wl[c], dtr * dtr * (1.0f / 3.0f) * o.Lt[c]);
+#pragma unroll
+      for (int f = 0; f < 8; ++f) ff_add(Gh[f], Gl[f], dtr * (f < 4 ? o.gtx[f] : o.gty[f - 4]));
     }
     if (xwall || ywall) {
       float ke = 0.5f * (Wh[1] * Wh[1] + Wh[2] * Wh[2]) / Wh[0];
@@ -677,25 +689,35 @@ __device__ __forceinline__ void update_body(const KArgs<R>& a, int mode, int g, 
     double* Og = a.Sout + (long)g * NFLD * P;
     double* Ag = a.Wacc + (long)g * 4 * P;
     double* Bg = a.gB + (long)g * 8 * P;
-    double Wnew[4];
+    double Wnew[4], Gnew[8];
+    // inputs first, then the stores (see the mixed branch)
+    if (mode == UPD_STAGE1) {
+      double Wn[4], Gb[8];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      if (mode == UPD_STAGE1) {
-        double Wn = Sng[(long)c * P + c0];
-        double dL = (double)o.L[c], dLt = (double)o.Lt[c];
-        Wnew[c] = Wn + 0.5 * dt * dL + 0.125 * dt * dt * dLt;
-        Ag[(long)c * P + c0] = Wn + dt * dL + dt * dt / 6.0 * dLt;
-        double bx = a.grad_base ? Sng[(long)(4 + c) * P + c0] : (double)o.gbx[c];
-        double by = a.grad_base ? Sng[(long)(8 + c) * P + c0] : (double)o.gby[c];
-        Bg[(long)c * P + c0] = bx;
-        Bg[(long)(4 + c) * P + c0] = by;
-        Og[(long)(4 + c) * P + c0] = bx + 0.5 * dt * (double)o.gtx[c];
-        Og[(long)(8 + c) * P + c0] = by + 0.5 * dt * (double)o.gty[c];
-      } else {
-        Wnew[c] = Ag[(long)c * P + c0] + dt * dt / 3.0 * (double)o.Lt[c];
-        Og[(long)(4 + c) * P + c0] = Bg[(long)c * P + c0] + dt * (double)o.gtx[c];
-        Og[(long)(8 + c) * P + c0] = Bg[(long)(4 + c) * P + c0] + dt * (double)o.gty[c];
+      for (int c = 0; c < 4; ++c) Wn[c] = Sng[(long)c * P + c0];
+#pragma unroll
+      for (int f = 0; f < 8; ++f)
+        Gb[f] = a.grad_base ? Sng[(long)(4 + f) * P + c0] : (double)(f < 4 ? o.gbx[f] : o.gby[f - 4]);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const double dL = (double)o.L[c], dLt = (double)o.Lt[c];
+        Wnew[c] = Wn[c] + 0.5 * dt * dL + 0.125 * dt * dt * dLt;
+        Ag[(long)c * P + c0] = Wn[c] + dt * dL + dt * dt / 6.0 * dLt;
       }
+#pragma unroll
+      for (int f = 0; f < 8; ++f) {
+        Bg[(long)f * P + c0] = Gb[f];
+        Gnew[f] = Gb[f] + 0.5 * dt * (double)(f < 4 ? o.gtx[f] : o.gty[f - 4]);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) Wnew[c] = Ag[(long)c * P + c0];
+#pragma unroll
+      for (int f = 0; f < 8; ++f) Gnew[f] = Bg[(long)f * P + c0];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) Wnew[c] = Wnew[c] + dt * dt / 3.0 * (double)o.Lt[c];
+#pragma unroll
+      for (int f = 0; f < 8; ++f) Gnew[f] = Gnew[f] + dt * (double)(f < 4 ? o.gtx[f] : o.gty[f - 4]);
     }
     if (xwall || ywall) {
       double ke = 0.5 * (Wnew[1] * Wnew[1] + Wnew[2] * Wnew[2]) / Wnew[0];
@@ -703,10 +725,12 @@ __device__ __forceinline__ void update_body(const KArgs<R>& a, int mode, int g, 
       Wnew[2] = 0.0;
       Wnew[3] -= ke;
     }
-    if (xwall) { Og[(long)(8 + 1) * P + c0] = 0.0; Og[(long)(8 + 2) * P + c0] = 0.0; }
-    if (ywall) { Og[(long)(4 + 1) * P + c0] = 0.0; Og[(long)(4 + 2) * P + c0] = 0.0; }
+    if (xwall) { Gnew[5] = 0.0; Gnew[6] = 0.0; }   // y-gradients of rho U, rho V
+    if (ywall) { Gnew[1] = 0.0; Gnew[2] = 0.0; }   // x-gradients of rho U, rho V
 #pragma unroll
     for (int c = 0; c < 4; ++c) Og[(long)c * P + c0] = Wnew[c];
+#pragma unroll
+    for (int f = 0; f < 8; ++f) Og[(long)(4 + f) * P + c0] = Gnew[f];
     // positivity of density and pressure (no trap: a flag the host reads)
     double p = Wnew[3] - 0.5 * (Wnew[1] * Wnew[1] + Wnew[2] * Wnew[2]) / Wnew[0];
     if (!(Wnew[0] > 0.0) || !(p > 0.0)) atomicOr(a.flag, 1);

@@ -381,19 +381,34 @@ FD_HD void mpsi(const Tab<R>& T, R o[4]) {
   o[3] = R(0.5) * (mm<a + 2, b, c>(T) + mm<a, b + 2, c>(T) + mm<a, b, c + 1>(T));
 }
 
-// <s u^a v^b psi> for a slope polynomial s = s0 + s1 u + s2 v + s3 psi_4
+// <s u^a v^b psi> for a slope polynomial s = s0 + s1 u + s2 v + s3 psi_4,
+// psi_4 = (u^2 + v^2 + xi^2)/2.  The moments factor, <u^p v^q xi^2m> =
+// u[p] v[q] xi[m], so with h = s3/2 the slope-weighted moment is
+//   <s u^p v^q> = v[q] U(p) + u[p] V(q),
+//   U(p) = (s0 + h xi[1]) u[p] + s1 u[p+1] + h u[p+2],  V(q) = s2 v[q+1] + h v[q+2],
+//   <s u^p v^q xi^2> = xi[1] (v[q] U'(p) + u[p] V(q)) + h xi[2] u[p] v[q],
+//   U'(p) = s0 u[p] + s1 u[p+1] + h u[p+2],
+// and the psi components are <s u^a v^b (1, u, v)> and half the sum of
+// <s u^(a+2) v^b>, <s u^a v^(b+2)> and <s u^a v^b xi^2>.
+template <int p, class R>
+FD_HD R slope_u(const Tab<R>& T, R c0, R s1, R h) { return c0 * T.u[p] + s1 * T.u[p + 1] + h * T.u[p + 2]; }
+template <int q, class R>
+FD_HD R slope_v(const Tab<R>& T, R s2, R h) { return s2 * T.v[q + 1] + h * T.v[q + 2]; }
+template <int p, int q, class R>
+FD_HD R slope_uv(const Tab<R>& T, R c0, const R s[4], R h) {
+  return T.v[q] * slope_u<p>(T, c0, s[1], h) + T.u[p] * slope_v<q>(T, s[2], h);
+}
+
 template <int a, int b, class R>
 FD_HD void mslope(const Tab<R>& T, const R s[4], R o[4]) {
-  R t0[4], t1[4], t2[4], ta[4], tb[4], tc[4];
-  mpsi<a, b, 0>(T, t0);
-  mpsi<a + 1, b, 0>(T, t1);
-  mpsi<a, b + 1, 0>(T, t2);
-  mpsi<a + 2, b, 0>(T, ta);
-  mpsi<a, b + 2, 0>(T, tb);
-  mpsi<a, b, 1>(T, tc);
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-    o[k] = s[0] * t0[k] + s[1] * t1[k] + s[2] * t2[k] + R(0.5) * s[3] * (ta[k] + tb[k] + tc[k]);
+  const R h = R(0.5) * s[3];
+  const R c0 = s[0] + h * T.xi[1];
+  const R sx = T.xi[1] * (T.v[b] * slope_u<a>(T, s[0], s[1], h) + T.u[a] * slope_v<b>(T, s[2], h)) +
+               h * T.xi[2] * T.u[a] * T.v[b];
+  o[0] = slope_uv<a, b>(T, c0, s, h);
+  o[1] = slope_uv<a + 1, b>(T, c0, s, h);
+  o[2] = slope_uv<a, b + 1>(T, c0, s, h);
+  o[3] = R(0.5) * (slope_uv<a + 2, b>(T, c0, s, h) + slope_uv<a, b + 2>(T, c0, s, h) + sx);
 }
 
 // slope s with <s psi> = r (r = dW / rho), closed form of the 4x4 moment system

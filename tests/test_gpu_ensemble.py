@@ -13,6 +13,7 @@ the oracle directly.
 import numpy as np
 import pytest
 
+import oracle
 from gpu_util import field_errors, oracle_run
 from paper_2606_17772_gb300 import fdcgks, inputs
 
@@ -138,10 +139,12 @@ def hypersonic_strip():
 @pytest.mark.parametrize("precision", [fdcgks.FP64, fdcgks.MIXED])
 def test_device_cfl_step_equals_host_formula(precision):
     """The first CFL step of every member equals fdcgks_cfl_dt on the same
-    state (the mixed path screens nodes in FP32 and evaluates the candidates
-    in FP64: the maxima, hence dt, must still be those over all nodes)."""
+    state and the oracle's all-node FP64 value (the mixed ensemble and the
+    single contexts screen nodes in FP32 and evaluate the candidates in FP64:
+    the maxima, hence dt, must still be those over all nodes)."""
     cases = members() + [hypersonic_strip(), inputs.viscous_shock_tube(40, 20), inputs.sod_strip(64, 3)]
     with make_ensemble(cases, precision) as ens:
+        states = [member_state(ens, m) for m in range(len(cases))]
         ens.run(1, cfl=0.37)
         _, last, st = ens.status()
     for m, c in enumerate(cases):
@@ -149,6 +152,10 @@ def test_device_cfl_step_equals_host_formula(precision):
             s.set_state(*c.initial_state())
             ref = s.cfl_dt(0.37)
         assert last[m] == pytest.approx(ref, rel=1e-15), (m, last[m], ref)
+        # and the all-node FP64 value of the oracle on the member's own state
+        St = states[m]
+        full = oracle.cfl_dt(oracle.make_params(**c.oracle_kwargs()), 0.37, St[0], St[2])
+        assert last[m] == pytest.approx(full, rel=1e-14), (m, last[m], full)
 
 
 def test_member_matches_oracle():
