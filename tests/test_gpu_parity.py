@@ -253,6 +253,33 @@ def test_host_and_device_state_round_trip():
             assert np.array_equal(a, b.cpu().numpy())
 
 
+@pytest.mark.parametrize("precision", [fdcgks.FP64, fdcgks.MIXED])
+@pytest.mark.parametrize("nx,ny,bc", [(13, 9, (3, 3, 2, 2)), (16, 12, (0, 0, 0, 0)), (7, 30, (1, 2, 0, 0))])
+def test_host_copies_equal_device_copies(precision, nx, ny, bc):
+    """Host state goes through one contiguous copy per array and a device
+    kernel into the padded layout (both directions); it must give exactly
+    what the device-pointer path gives, after a step too (the staging area
+    is the point-output buffer, overwritten by every step)."""
+    case = inputs.random_smooth(nx, ny, seed=11, bc=bc)
+    S = case.initial_state()
+    Sd = [torch.from_numpy(a).cuda() for a in S]
+    out = {}
+    for path in ("host", "device"):
+        with fdcgks.Solver.from_case(case, precision) as s:
+            s.set_state(*(S if path == "host" else Sd))
+            a = [np.asarray(t) for t in s.get_state(device=False)] if path == "host" else \
+                [t.cpu().numpy() for t in s.get_state()]
+            s.step(1e-3)
+            b = [np.asarray(t) for t in s.get_state(device=False)] if path == "host" else \
+                [t.cpu().numpy() for t in s.get_state()]
+            out[path] = a + b
+    for x, y in zip(out["host"], out["device"]):
+        assert np.array_equal(x, y)
+    if precision == fdcgks.FP64:
+        for x, y in zip(S, out["host"][:4]):
+            assert np.array_equal(x, y)
+
+
 def test_split_run_equals_straight_run():
     """Checkpoint/resume through get_state/set_state is bit-exact."""
     case = inputs.vortex(24)
