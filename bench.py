@@ -408,33 +408,46 @@ def run_ensemble(args, world, rank, local, peaks=None):
 
 
 def run_viscous_tube(args, world):
-    """Viscous shock tube (Sec. 5.8) at 1000 x 500: throughput of a window of
-    steps after the first CFL steps, FP64 and mixed (the time step held at the
-    CFL value at the start of the window)."""
+    """Viscous shock tube (Sec. 5.8) at 1000 x 500 with the workload's own
+    constants: throughput of a window of steps after the first 10, FP64 and
+    mixed, each step with its own CFL-0.4 time step (host loop, as in a run to
+    t = 1)."""
     import torch
     from paper_2606_17772_gb300 import fdcgks, inputs
     case = inputs.viscous_shock_tube(1000, 500)
     nodes = case.nx * case.ny + case.nxd * case.nyd
     out = {"config": {"workload": "viscous shock tube, [0,1]x[0,0.5], 1000x500 (+1001x501 dual), Re 200, "
-                                  "Pr 0.73, no-slip walls, symmetry top; window after 10 CFL-0.4 steps",
+                                  "Pr 0.73, no-slip walls, symmetry top, Sec. 3.2 GENO, tau c2 = 1; window "
+                                  "after 10 steps, a CFL-0.4 step each step (host loop)",
                       "node_updates_per_step": nodes}}
     for name, prec, k in (("fp64", fdcgks.FP64, args.vt_steps), ("mixed", fdcgks.MIXED, 10 * args.vt_steps)):
         with fdcgks.Solver.from_case(case, prec) as s:
             s.set_state(*case.initial_state())
+            t = 0.0
             for _ in range(10):
-                s.step(s.cfl_dt(0.4))
-            dt = s.cfl_dt(0.4)
+                dt = s.cfl_dt(0.4)
+                s.step(dt)
+                t += dt
             torch.cuda.synchronize()
             barrier(world)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            s.steps(dt, k)
+            done, failed = 0, False
+            for _ in range(k):
+                try:
+                    dt = s.cfl_dt(0.4)          # raises once the state has no finite wave speed
+                except fdcgks.FdcgksError:
+                    failed = True
+                    break
+                s.step(dt)
+                t += dt
+                done += 1
             e1.record()
             torch.cuda.synchronize()
             ms = max_over_ranks(e0.elapsed_time(e1), world)
-            bad = s.check()
-        out[name] = {"value": nodes * k * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / k, "steps": k,
-                     "dt": dt, "nonphysical": bool(bad)}
+            bad = failed or s.check()
+        out[name] = {"value": nodes * max(done, 1) * world / (ms / 1e3), "unit": UNIT,
+                     "ms_per_step": ms / max(done, 1), "steps": done, "t_end": t, "nonphysical": bool(bad)}
     return out
 
 

@@ -57,19 +57,16 @@ FD_HD float s_div(float a, float b) {
 #endif
 }
 
-// erfc(x) given ex2 = exp(-x^2), which the caller has already computed.
-// FP64: the library function.  FP32: Abramowitz & Stegun, Handbook of
-// Mathematical Functions, Eq. 7.1.26 (Hastings' rational approximation of
-// erf, absolute error <= 1.5e-7), erfc(|x|) = t (a1 + t(a2 + ...)) exp(-x^2)
-// with t = 1/(1 + p |x|), and erfc(x) = 2 - erfc(-x) for x < 0.
+// erfc(x); ex2 = exp(-x^2) is what the caller has already computed, for an
+// evaluation that would reuse it.  Both precisions call the library function:
+// CUDA's erfcf keeps a few ulp of relative accuracy where erfc is small, while
+// an absolute-error approximation (e.g. Abramowitz & Stegun 7.1.26, |error|
+// <= 1.5e-7, written as a polynomial times exp(-x^2)) is off by up to 1e-3
+// relative there.  That inconsistency between the half-space moments of the
+// two sides seeded a grid-scale mode across the strong shock of the 1000 x 500
+// viscous shock tube in the mixed path, which the library function does not.
 FD_HD double s_erfc_e(double x, double ex2) { (void)ex2; return erfc(x); }
-FD_HD float s_erfc_e(float x, float ex2) {
-  float ax = fabsf(x);
-  float t = s_div(1.0f, 1.0f + 0.3275911f * ax);
-  float poly = t * (0.254829592f + t * (-0.284496736f + t * (1.421413741f + t * (-1.453152027f + t * 1.061405429f))));
-  float r = poly * ex2;
-  return x >= 0.0f ? r : 2.0f - r;
-}
+FD_HD float s_erfc_e(float x, float ex2) { (void)ex2; return erfcf(x); }
 
 // value at which tanh(z) rounds to exactly 1 in the compute type
 template <class R> struct TanhSat;

@@ -268,36 +268,48 @@ def test_mixed_adjoint_against_differences_of_the_mixed_step():
 
 
 
-def test_mixed_adjoint_follows_the_mixed_step_in_a_far_field():
-    """Where the data vary below the FP32 path's rounding floor (a vortex's far
-    field), the mixed step treats them as smooth and its derivative differs
-    from the FP64 step's.  The mixed context's reverse pass takes the same
-    floor, so its directional derivative is nearer the median of central
-    differences of the mixed run (which scatter with the run's FP32 rounding)
-    than the FP64 context's adjoint is."""
+def test_mixed_adjoint_takes_the_rounding_floor():
+    """The mixed context's reverse pass linearises GENO with the FP32 path's
+    rounding floor (its reverse functions are checked against dual numbers of
+    the floored function on the host, tests/test_adjoint_host.py).  Through
+    the C ABI on a 32^2 vortex over 3 steps: for a direction confined to the
+    far field (r > 4.5), where the data vary below the floor, the floored
+    linearisation differs from the FP64 one by more than 10 %; for a direction
+    in the core (r < 2), where they vary far above it, the two agree to 1e-3.
+    Central differences of the mixed run itself cannot decide between the two
+    in the far field: at steps small enough to stay below the floor they
+    scatter by a factor of about 2 with the run's FP32 rounding (printed)."""
     case = inputs.vortex(32)
     S0 = case.initial_state()
     with fdcgks.Solver.from_case(case) as s:
         s.set_state(*S0)
         dt = s.cfl_dt(0.2)
     X, Y = case.node_xy(False)
-    far = np.hypot(X - 5.0, Y - 5.0) > 4.5
+    r = np.hypot(X - 5.0, Y - 5.0)
     rng = np.random.default_rng(3)
-    v = [np.zeros_like(a) for a in S0]
-    v[0] = rng.standard_normal(S0[0].shape) * far[None] * np.abs(S0[0]).max(axis=(1, 2))[:, None, None]
     seed = [rng.standard_normal(a.shape) for a in S0]
+    scale = np.abs(S0[0]).max(axis=(1, 2))[:, None, None]
+    dirs = {}
+    for name, mask in (("far", r > 4.5), ("core", r < 2.0)):
+        v = [np.zeros_like(a) for a in S0]
+        v[0] = rng.standard_normal(S0[0].shape) * mask[None] * scale
+        dirs[name] = v
     n = 3
     ad = {}
     for prec in (fdcgks.FP64, fdcgks.MIXED):
         with fdcgks.Solver.from_case(case, prec) as s:
             g = [t.cpu().numpy() for t in s.vjp_steps(dt, n, dev(S0), dev(seed), checkpoint_every=2)]
-            ad[prec] = dot(g, v)
+            ad[prec] = {k: dot(g, v) for k, v in dirs.items()}
             if prec == fdcgks.MIXED:
                 fds = []
+                v = dirs["far"]
                 for eps in (1e-5, 3e-6, 1e-6, 3e-7, 1e-7):
                     p = run(s, [a + eps * b for a, b in zip(S0, v)], dt, n)
                     m = run(s, [a - eps * b for a, b in zip(S0, v)], dt, n)
                     fds.append(dot(seed, [(x - y) / (2 * eps) for x, y in zip(p, m)]))
-    med = float(np.median(fds))
-    print("far field: mixed-run differences", fds, "mixed adjoint", ad[fdcgks.MIXED], "FP64 adjoint", ad[fdcgks.FP64])
-    assert abs(ad[fdcgks.MIXED] - med) < abs(ad[fdcgks.FP64] - med)
+    print("far field: mixed-run differences", fds, "mixed adjoint", ad[fdcgks.MIXED]["far"],
+          "FP64 adjoint", ad[fdcgks.FP64]["far"])
+    far64, farmx = ad[fdcgks.FP64]["far"], ad[fdcgks.MIXED]["far"]
+    assert abs(farmx - far64) > 0.1 * abs(far64), (farmx, far64)
+    core64, coremx = ad[fdcgks.FP64]["core"], ad[fdcgks.MIXED]["core"]
+    assert abs(coremx - core64) < 1e-3 * abs(core64), (coremx, core64)

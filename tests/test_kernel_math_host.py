@@ -1,8 +1,8 @@
 """The kernels' arithmetic (csrc/fdcgks_math.cuh) compiled for the host and
 checked against the oracle without a GPU: interface solves, nodal fluxes and
-reconstructions in FP64, and the FP32 erfc approximation of the mixed path
-against its published error bound (Abramowitz & Stegun 7.1.26: |error| of erf
-<= 1.5e-7, so the same absolute bound for erfc)."""
+reconstructions in FP64, and the FP32 erfc of the mixed path to a relative
+accuracy of a few FP32 ulp over the whole range, including the tail where erfc
+is small (an absolute-error approximation is not enough there)."""
 import ctypes
 import os
 import subprocess
@@ -71,14 +71,16 @@ def test_fp64_reconstruction_matches_oracle(probe, variant):
     np.testing.assert_allclose(out, ref, rtol=1e-12, atol=1e-12)
 
 
-def test_fp32_erfc_within_published_bound(probe):
-    x = np.ascontiguousarray(np.linspace(-6.0, 6.0, 4801))
+def test_fp32_erfc_relative_accuracy(probe):
+    """Relative error below 1e-6 from x = -6 to 9 (erfc from 2 down to 4e-37):
+    the half-space moments of the kinetic solve need relative accuracy where
+    erfc is small, which an absolute bound of 1.5e-7 does not give."""
+    x = np.ascontiguousarray(np.linspace(-6.0, 9.0, 6001))
     out = np.zeros_like(x)
     probe.probe_erfc32(len(x), _p(x), _p(out))
     xf = x.astype(np.float32).astype(np.float64)
-    err = np.abs(out - special.erfc(xf))
-    # 1.5e-7 from the approximation plus FP32 rounding of values up to 2
-    assert err.max() < 1.5e-7 + 4 * 2.0 * np.finfo(np.float32).eps
+    ref = special.erfc(xf)
+    assert np.max(np.abs(out - ref) / ref) < 1e-6
 
 
 @pytest.mark.parametrize("variant", [0, 1])
