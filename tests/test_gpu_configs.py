@@ -126,3 +126,19 @@ def test_mixed_ensemble_member_within_stated_error():
         assert st[0] == 0
     w, g = _split(field_errors(got, ref))
     assert w < 1e-5 and g < 2e-4, (w, g)
+
+
+def test_mixed_full_size_tube_passes_the_shock_wall_corner():
+    """The 1000 x 500 viscous tube with the default constants in mixed
+    precision, CFL-0.4 steps to t = 0.006: past the time (t = 0.0024-0.0047)
+    at which a grid-scale mode across the shock made this run leave the
+    physical states while the FP32 erfc was an absolute-error approximation
+    (half-space moments off by up to 1e-3 relative where erfc is small)."""
+    from paper_2606_17772_gb300 import runs
+    case = inputs.viscous_shock_tube(1000, 500)
+    with fdcgks.Solver.from_case(case, fdcgks.MIXED) as s:
+        s.set_state(*case.initial_state())
+        t, n = runs.advance(s, 0.006, 0.4, check_every=25)
+        assert t == pytest.approx(0.006) and n > 400
+        W = s.get_state(device=False)
+        assert np.all(np.isfinite(W[0])) and W[0][0].min() > 0.5
