@@ -231,9 +231,9 @@ cudaError_t fdk::launch_validate(const double* S, const Layout& L, double gamma,
   return cudaGetLastError();
 }
 
-// per-block maxima of (|U|+c)/hx, (|V|+c)/hy (as one rate) and nu = mu/rho
 // the rates of cfl_rates added over the directions, (|U|+c)/hx + (|V|+c)/hy
-// (the two-dimensional form of the CFL bound)
+// (the two-dimensional form of the CFL bound), and nu = mu/rho, folded into
+// running maxima
 __device__ void cfl_rates_sum(double r, double ru, double rv, double E, double gamma, double mu, double ihx,
                               double ihy, double& rate, double& numax) {
   const double ir = 1.0 / r;
