@@ -457,33 +457,79 @@ FD_HD void mpsi_adj(const Tab<R>& T, const R ob[4], TabB& Tb) {
   mm_adj<a, b, c + 1>(T, 0.5 * ob[3], Tb);
 }
 
-// o = <s u^a v^b psi> (mslope): sb += ..., Tb += ...
+// o = <s u^a v^b psi> (mslope, factored form): sb += ..., Tb += ...
+// Forward, with h = s3/2, c0 = s0 + h xi[1]:
+//   U(p) = c0 u[p] + s1 u[p+1] + h u[p+2],  V(q) = s2 v[q+1] + h v[q+2],
+//   S(p,q) = v[q] U(p) + u[p] V(q),  U'(a) = s0 u[a] + s1 u[a+1] + h u[a+2],
+//   Sx = xi[1] (v[b] U'(a) + u[a] V(b)) + h xi[2] u[a] v[b],
+//   o = (S(a,b), S(a+1,b), S(a,b+1), (S(a+2,b) + S(a,b+2) + Sx)/2).
+// Reverse: the weights of the S terms give the adjoints of U, V and the
+// tables; those of U, U', V give the adjoints of the slope and the tables.
 template <int a, int b>
 FD_HD void mslope_adj(const Tab<R>& T, const R s[4], const R ob[4], TabB& Tb, R sb[4]) {
-  R t0[4], t1[4], t2[4], ta[4], tb[4], tc[4];
-  mpsi<a, b, 0>(T, t0);
-  mpsi<a + 1, b, 0>(T, t1);
-  mpsi<a, b + 1, 0>(T, t2);
-  mpsi<a + 2, b, 0>(T, ta);
-  mpsi<a, b + 2, 0>(T, tb);
-  mpsi<a, b, 1>(T, tc);
-  R x[4];
-  for (int k = 0; k < 4; ++k) {
-    sb[0] += ob[k] * t0[k];
-    sb[1] += ob[k] * t1[k];
-    sb[2] += ob[k] * t2[k];
-    sb[3] += 0.5 * ob[k] * (ta[k] + tb[k] + tc[k]);
+  const R h = 0.5 * s[3], x1 = T.xi[1], x2 = T.xi[2];
+  const R c0 = s[0] + h * x1;
+  R U[3], V[3];                                   // U(a + k), V(b + k)
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    U[k] = c0 * T.u[a + k] + s[1] * T.u[a + k + 1] + h * T.u[a + k + 2];
+    V[k] = s[2] * T.v[b + k + 1] + h * T.v[b + k + 2];
   }
-  for (int k = 0; k < 4; ++k) x[k] = s[0] * ob[k];
-  mpsi_adj<a, b, 0>(T, x, Tb);
-  for (int k = 0; k < 4; ++k) x[k] = s[1] * ob[k];
-  mpsi_adj<a + 1, b, 0>(T, x, Tb);
-  for (int k = 0; k < 4; ++k) x[k] = s[2] * ob[k];
-  mpsi_adj<a, b + 1, 0>(T, x, Tb);
-  for (int k = 0; k < 4; ++k) x[k] = 0.5 * s[3] * ob[k];
-  mpsi_adj<a + 2, b, 0>(T, x, Tb);
-  mpsi_adj<a, b + 2, 0>(T, x, Tb);
-  mpsi_adj<a, b, 1>(T, x, Tb);
+  const R Up = s[0] * T.u[a] + s[1] * T.u[a + 1] + h * T.u[a + 2];
+  R Ub[3] = {0.0, 0.0, 0.0}, Vb[3] = {0.0, 0.0, 0.0}, c0b = 0.0, hb = 0.0, Upb = 0.0;
+  // S(a + dp, b + dq) with weight w
+  auto S_adj = [&](int dp, int dq, R w) {
+    Ub[dp] += w * T.v[b + dq];
+    Tb.v[b + dq] += w * U[dp];
+    Tb.u[a + dp] += w * V[dq];
+    Vb[dq] += w * T.u[a + dp];
+  };
+  const R w3 = 0.5 * ob[3];
+  S_adj(0, 0, ob[0]);
+  S_adj(1, 0, ob[1]);
+  S_adj(0, 1, ob[2]);
+  S_adj(2, 0, w3);
+  S_adj(0, 2, w3);
+  // Sx with weight w3
+  {
+    const R inner = T.v[b] * Up + T.u[a] * V[0];
+    Tb.xi[1] += w3 * inner;
+    const R wi = w3 * x1;
+    Upb += wi * T.v[b];
+    Tb.v[b] += wi * Up;
+    Tb.u[a] += wi * V[0];
+    Vb[0] += wi * T.u[a];
+    const R uv = T.u[a] * T.v[b];
+    hb += w3 * x2 * uv;
+    Tb.xi[2] += w3 * h * uv;
+    Tb.u[a] += w3 * h * x2 * T.v[b];
+    Tb.v[b] += w3 * h * x2 * T.u[a];
+  }
+  // U(a + k), V(b + k), U'(a)
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    c0b += Ub[k] * T.u[a + k];
+    sb[1] += Ub[k] * T.u[a + k + 1];
+    hb += Ub[k] * T.u[a + k + 2];
+    Tb.u[a + k] += Ub[k] * c0;
+    Tb.u[a + k + 1] += Ub[k] * s[1];
+    Tb.u[a + k + 2] += Ub[k] * h;
+    sb[2] += Vb[k] * T.v[b + k + 1];
+    hb += Vb[k] * T.v[b + k + 2];
+    Tb.v[b + k + 1] += Vb[k] * s[2];
+    Tb.v[b + k + 2] += Vb[k] * h;
+  }
+  sb[0] += Upb * T.u[a];
+  sb[1] += Upb * T.u[a + 1];
+  hb += Upb * T.u[a + 2];
+  Tb.u[a] += Upb * s[0];
+  Tb.u[a + 1] += Upb * s[1];
+  Tb.u[a + 2] += Upb * h;
+  // c0 = s0 + h xi[1], h = s3 / 2
+  sb[0] += c0b;
+  hb += c0b * x1;
+  Tb.xi[1] += c0b * h;
+  sb[3] += 0.5 * hb;
 }
 
 // s = slope_solve(g, r): sb -> rb, gb (added)
