@@ -134,16 +134,10 @@ template <int P> CN<P> s_abs(CN<P> x) {
 template <int P> CN<P> s_min(CN<P> a, CN<P> b) { return a.v < b.v ? a : b; }
 template <int P> CN<P> s_max(CN<P> a, CN<P> b) { return a.v > b.v ? a : b; }
 template <int P> CN<P> s_div(CN<P> a, CN<P> b) { return a / b; }
-// erfc given exp(-x^2): FP64 calls erfc, FP32 evaluates the rational approximation
+// erfc given exp(-x^2): one erfc in either precision (the kernels call the
+// library's erfcx or erfcf)
 inline CD s_erfc_e(CD x, CD e) { (void)e; return s_erfc(x); }
-inline CF s_erfc_e(CF x, CF ex2) {
-  CF ax = s_abs(x);
-  CF t = CF(1.0f) / (CF(1.0f) + CF(0.3275911f) * ax);
-  CF poly = t * (CF(0.254829592f) + t * (CF(-0.284496736f) + t * (CF(1.421413741f) +
-            t * (CF(-1.453152027f) + t * CF(1.061405429f)))));
-  CF r = poly * ex2;
-  return x.v >= 0.0f ? r : CF(2.0f) - r;
-}
+inline CF s_erfc_e(CF x, CF e) { (void)e; return s_erfc(x); }
 }  // namespace fdk
 
 #include "fdcgks_math.cuh"
