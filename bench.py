@@ -658,7 +658,9 @@ def kernel_work(case, cnt, precision):
       update  stage 1 reads 25 + 25 point values, 16 nodal fluxes and W^n,
               writes the stage state (12), the S2O4 accumulator (4) and the
               gradient base (8); stage 2 reads 13 + 13, 8, the accumulator and
-              base, writes the state (12) (float-float pairs count both halves);
+              base, writes the state (12) (float-float pairs count both halves;
+              a gradient base re-evaluated from the interface solution is an
+              FP32 value, its low half 0 and not stored);
       ghost   3 ghost layers of 12 fields of both grids, read and write;
       cfl     4 conservative fields of every node (FP64, or both halves)."""
     r = 8 if precision == 0 else 4
@@ -672,9 +674,11 @@ def kernel_work(case, cnt, precision):
     u1, u2 = fl("update_stage1"), fl("update_stage2")
     # FP64: stage 1 reads 50 + 16 + 4, writes 24; stage 2 reads 26 + 8 + 4 + 8, writes 12.
     # mixed: stage 1 reads 66 floats and the W^n pairs (8), writes the stage state's high
-    # parts (12) and the accumulator and base pairs (24); stage 2 reads 34 floats and
-    # those pairs (24), writes the state pairs (24)
-    upd_bytes = (94 + 58) * 8 if precision == 0 else ((66 + 8 + 36) + (34 + 24 + 24)) * 4
+    # parts (12), the accumulator pairs (8) and the gradient base (8 high parts; pairs,
+    # 16, when the base is the state's own gradients); stage 2 reads 34 floats, the
+    # accumulator and the base, writes the state pairs (24)
+    base = 16 if case.grad_base else 8
+    upd_bytes = (94 + 58) * 8 if precision == 0 else ((66 + 8 + 20 + base) + (34 + 8 + base + 24)) * 4
     ghosts = sum(2 * GH * ny + 2 * GH * (nx + 2 * GH) for nx, ny in ((case.nx, case.ny), (case.nxd, case.nyd)))
     work = {
         "points": (pts * (p1[0] + p2[0]), pts * (p1[1] + p2[1]), pts * (16 + 50 + 16 + 26) * r),

@@ -639,10 +639,12 @@ __device__ __forceinline__ void update_body(const KArgs<R>& a, int mode, int g, 
         Ah[(long)c * P + c0] = ah;
         Al[(long)c * P + c0] = al;
       }
+      // the gradient base: re-evaluated gradients are FP32 values (low part 0,
+      // not stored); a base taken from the state keeps its low part
 #pragma unroll
       for (int f = 0; f < 8; ++f) {
         Bh[(long)f * P + c0] = Gh[f];
-        Bl[(long)f * P + c0] = Gl[f];
+        if (a.grad_base) Bl[(long)f * P + c0] = Gl[f];
         ff_add(Gh[f], Gl[f], 0.5f * dtr * (f < 4 ? o.gtx[f] : o.gty[f - 4]));
       }
     } else {
@@ -654,7 +656,7 @@ __device__ __forceinline__ void update_body(const KArgs<R>& a, int mode, int g, 
 #pragma unroll
       for (int f = 0; f < 8; ++f) {
         Gh[f] = Bh[(long)f * P + c0];
-        Gl[f] = Bl[(long)f * P + c0];
+        Gl[f] = a.grad_base ? Bl[(long)f * P + c0] : 0.0f;
       }
 #pragma unroll
       for (int c = 0; c < 4; ++c) ff_add(Wh[c], Wl[c], dtr * dtr * (1.0f / 3.0f) * o.Lt[c]);
