@@ -654,7 +654,8 @@ def kernel_work(case, cnt, precision):
     the mixed path's FP32 arrays and float-float halves):
       points  reads W and the line's averaged gradient of both grids (16 r),
               writes 25 values per solve at stage 1, 13 at stage 2;
-      nodal   reads W and both gradients (12 r), writes F, G, F_t, G_t (16 r);
+      nodal   reads W and both gradients (12 r), writes F, G, F_t, G_t (16 r)
+              at stage 1 and F_t, G_t (8 r) at stage 2;
       update  stage 1 reads 25 + 25 point values, 16 nodal fluxes and W^n,
               writes the stage state (12), the S2O4 accumulator (4) and the
               gradient base (8); stage 2 reads 13 + 13, 8, the accumulator and
@@ -670,7 +671,7 @@ def kernel_work(case, cnt, precision):
         c = cnt[name]
         return c["fp64"], c["fp32"]
     p1, p2 = fl("point_stage1"), fl("point_stage2")
-    nd = fl("node")
+    nd, nd2 = fl("node"), fl("node_stage2")
     u1, u2 = fl("update_stage1"), fl("update_stage2")
     # FP64: stage 1 reads 50 + 16 + 4, writes 24; stage 2 reads 26 + 8 + 4 + 8, writes 12.
     # mixed: stage 1 reads 66 floats and the W^n pairs (8), writes the stage state's high
@@ -682,7 +683,7 @@ def kernel_work(case, cnt, precision):
     ghosts = sum(2 * GH * ny + 2 * GH * (nx + 2 * GH) for nx, ny in ((case.nx, case.ny), (case.nxd, case.nyd)))
     work = {
         "points": (pts * (p1[0] + p2[0]), pts * (p1[1] + p2[1]), pts * (16 + 50 + 16 + 26) * r),
-        "nodal": (2 * nodes * nd[0], 2 * nodes * nd[1], 2 * nodes * 28 * r),
+        "nodal": (nodes * (nd[0] + nd2[0]), nodes * (nd[1] + nd2[1]), nodes * (28 + 20) * r),
         "update": (nodes * (u1[0] + u2[0]), nodes * (u1[1] + u2[1]), nodes * upd_bytes),
         "ghost": (0.0, 0.0, 2 * ghosts * 12 * 2 * r),
         "cfl": (0.0, 0.0, nodes * 32.0),

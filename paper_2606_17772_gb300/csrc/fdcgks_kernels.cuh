@@ -142,10 +142,11 @@ __device__ __noinline__ void iface_solve_call(const GasK<R>& gas, int normal, co
 // One node: GENO node derivatives along x and y, then the nodal flux.
 // ld(e, f): field f (0-3 W, 4-7 x-gradient, 8-11 y-gradient) of node e (0 the
 // node, 1/2 its x neighbours -/+, 3/4 its y neighbours -/+); st(k, v): output
-// k (F[4], G[4], F_t[4], G_t[4]).  Shared by the kernel (loads from the state)
-// and its adjoint (seeded dual numbers).
+// k (F[4], G[4], F_t[4], G_t[4]); want_n = false (second S2O4 stage): F_t and
+// G_t only, F and G are neither computed nor stored.
 template <class R, class LD, class ST>
-FD_HD void nodal_compute(const GenoK<R>& geno, const GasK<R>& gas, const R h[2], const R ih[2], LD ld, ST st) {
+FD_HD void nodal_compute(const GenoK<R>& geno, const GasK<R>& gas, const R h[2], const R ih[2], LD ld, ST st,
+                         bool want_n = true) {
   R W[4], Wx[4], Wy[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
@@ -158,11 +159,13 @@ FD_HD void nodal_compute(const GenoK<R>& geno, const GasK<R>& gas, const R h[2],
     Wy[c] = recon_node(geno, qy, gyv, h[1], ih[1]);
   }
   R F[4], G[4], Ft[4], Gt[4];
-  nodal_flux(gas, W, Wx, Wy, F, G, Ft, Gt);
+  nodal_flux(gas, W, Wx, Wy, F, G, Ft, Gt, want_n);
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    st(c, F[c]);
-    st(4 + c, G[c]);
+    if (want_n) {
+      st(c, F[c]);
+      st(4 + c, G[c]);
+    }
     st(8 + c, Ft[c]);
     st(12 + c, Gt[c]);
   }
@@ -183,7 +186,7 @@ __device__ __forceinline__ void nodal_body(const KArgs<R>& a, int g, int i, int 
   R* NF = a.NF + (long)g * NNF * L.plane + c0;
   nodal_compute<R>(
       a.geno, a.gas, a.h, a.ih, [&](int e, int f) -> R { return S[(long)f * L.plane + c0 + nodal_offset(L, e)]; },
-      [&](int k, R v) { NF[(long)k * L.plane] = v; });
+      [&](int k, R v) { NF[(long)k * L.plane] = v; }, a.want_n != 0);
 }
 
 template <class R>

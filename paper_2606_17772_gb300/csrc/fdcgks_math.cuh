@@ -695,11 +695,13 @@ FD_HD void iface_solve(const GasK<R>& gas, int normal, const R Wl[4], const R Wr
 
 // ---------------------------------------------------------------------------
 // Nodal flux from smooth local data (Sec. 2.1): f = g(1 - tau(a u + b v + A)),
-// f_t = A g.  Outputs x-flux F, y-flux G and their time derivatives.
+// f_t = A g.  Outputs x-flux F, y-flux G and their time derivatives;
+// want_n = false computes the time derivatives only (F, G are set to 0): the
+// second S2O4 stage uses no other nodal output.
 // ---------------------------------------------------------------------------
 template <class R>
 FD_HD void nodal_flux(const GasK<R>& gas, const R W[4], const R Wx[4], const R Wy[4], R F[4], R G[4], R Ft[4],
-                      R Gt[4]) {
+                      R Gt[4], bool want_n = true) {
   const R K = gas.K;
   Maxw<R> g = maxw_from_W(W, gas.gm1);
   Tab<R> T;
@@ -722,31 +724,37 @@ FD_HD void nodal_flux(const GasK<R>& gas, const R W[4], const R Wx[4], const R W
   R tau = gas.c1_r * gas.dt_r + gas.mu_r * (R(2) * g.lam * g.ir);   // c1 dt + mu/p
 
   R e0[4], ea[4], eb[4], eA[4];
+  // time derivatives f_t = A g
+  mslope<1, 0>(T, A, eA);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) Ft[k] = g.rho * eA[k];
+  mslope<0, 1>(T, A, eA);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) Gt[k] = g.rho * eA[k];
+  // Prandtl correction; int psi f^n = W (compatibility), int psi f_t = Wt
+  Ft[3] += gas.prfix * heat_flux_x(Ft, Wt, g.U, g.V);
+  Gt[3] += gas.prfix * heat_flux_y(Gt, Wt, g.U, g.V);
+  if (!want_n) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) F[k] = G[k] = R(0);
+    return;
+  }
   // x-flux
   mpsi<1, 0, 0>(T, e0);
   mslope<2, 0>(T, a, ea);
   mslope<1, 1>(T, b, eb);
   mslope<1, 0>(T, A, eA);
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    F[k] = g.rho * (e0[k] - tau * (ea[k] + eb[k] + eA[k]));
-    Ft[k] = g.rho * eA[k];
-  }
+  for (int k = 0; k < 4; ++k) F[k] = g.rho * (e0[k] - tau * (ea[k] + eb[k] + eA[k]));
   // y-flux
   mpsi<0, 1, 0>(T, e0);
   mslope<1, 1>(T, a, ea);
   mslope<0, 2>(T, b, eb);
   mslope<0, 1>(T, A, eA);
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    G[k] = g.rho * (e0[k] - tau * (ea[k] + eb[k] + eA[k]));
-    Gt[k] = g.rho * eA[k];
-  }
-  // Prandtl correction; int psi f^n = W (compatibility), int psi f_t = Wt
+  for (int k = 0; k < 4; ++k) G[k] = g.rho * (e0[k] - tau * (ea[k] + eb[k] + eA[k]));
   F[3] += gas.prfix * heat_flux_x(F, W, g.U, g.V);
   G[3] += gas.prfix * heat_flux_y(G, W, g.U, g.V);
-  Ft[3] += gas.prfix * heat_flux_x(Ft, Wt, g.U, g.V);
-  Gt[3] += gas.prfix * heat_flux_y(Gt, Wt, g.U, g.V);
 }
 
 // ---------------------------------------------------------------------------

@@ -228,11 +228,11 @@ void run(int what, int variant, const double* gp, int normal, double h, int n, c
       for (int k = 0; k < 20; ++k) v[k] = R(in[t * 20 + k]);
       IfaceOut<R> o;
       iface_solve(gas, normal, v, v + 4, v + 8, v + 12, v + 16, true, o);
-    } else if (what == 3) {     // nodal flux
+    } else if (what == 3 || what == 5) {     // nodal flux (5: time derivatives only)
       R v[12];
       for (int k = 0; k < 12; ++k) v[k] = R(in[t * 12 + k]);
       R F[4], G[4], Ft[4], Gt[4];
-      nodal_flux(gas, v, v + 4, v + 8, F, G, Ft, Gt);
+      nodal_flux(gas, v, v + 4, v + 8, F, G, Ft, Gt, what == 3);
     } else {                    // compact flux (in: chi, 3 interface, 2 nodal fluxes)
       R x[6];
       for (int k = 0; k < 6; ++k) x[k] = R(in[t * 6 + k]);
@@ -246,7 +246,8 @@ void run(int what, int variant, const double* gp, int normal, double h, int n, c
 extern "C" {
 
 // what: 0 interface reconstruction, 1 node reconstruction, 2 interface solve,
-// 3 nodal flux, 4 compact flux (normal = flux variant).  precision 0: FP64
+// 3 nodal flux, 4 compact flux (normal = flux variant), 5 nodal flux time
+// derivatives only (second stage).  precision 0: FP64
 // compute type, 1: FP32 compute type (its FP64 part counted separately).
 // out[16] = FP64 (add, mul, div, sqrt, exp, erfc, tanh, expm1), then FP32 (same).
 void flop_count(int what, int precision, int variant, const double* gas, int normal, double h, int n,

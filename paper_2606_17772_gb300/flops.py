@@ -105,9 +105,9 @@ def step_counts(case, state, dt, precision=0, nsample=4000, seed=0):
     """Flops of one full S2O4 step, per node update and per point-kernel launch group.
 
     Returns a dict with 'per_node_update' (fp64 / fp32 kind dicts and totals),
-    'point_stage1' / 'point_stage2' (flops of one interface point), 'node'
-    (one node of the nodal kernel), 'update_stage1' / 'update_stage2' (one
-    node of the update kernel), each split into fp64 / fp32, and the unit
+    'point_stage1' / 'point_stage2' (flops of one interface point), 'node' /
+    'node_stage2' (one node of the nodal kernel at stage 1 / 2),
+    'update_stage1' / 'update_stage2' (one node of the update kernel), each split into fp64 / fp32, and the unit
     counts used.
     """
     rng = np.random.default_rng(seed)
@@ -120,6 +120,7 @@ def step_counts(case, state, dt, precision=0, nsample=4000, seed=0):
     solve_in = np.concatenate([W, W * 1.01, 0.1 * np.ones(4), 0.12 * np.ones(4), 0.05 * np.ones(4)])[None]
     solve = _count(2, precision, v, gas, 0, h, solve_in)
     nodal = _count(3, precision, v, gas, 0, h, np.concatenate([W, 0.1 * np.ones(8)])[None])
+    nodal_t = _count(5, precision, v, gas, 0, h, np.concatenate([W, 0.1 * np.ones(8)])[None])
     cflux = _count(4, precision, v, gas, case.flux_variant, h, np.array([[0.7, 1, 2, 3, 1.5, 2.5]]))
 
     def glue(n_r, n_64):
@@ -141,6 +142,7 @@ def step_counts(case, state, dt, precision=0, nsample=4000, seed=0):
     point1 = comb((rec_i, 8), (solve, 2), (glue(16 + 4 * 24 + 20, 0), 1))
     point2 = comb((rec_i, 8), (solve, 2), (glue(16 + 4 * 12 + 20, 0), 1))
     node = comb((rec_n, 8), (nodal, 1))
+    node2 = comb((rec_n, 8), (nodal_t, 1))       # second stage: F_t, G_t only
     # update kernel per node: stage 1 evaluates 8 compact fluxes per component
     # (F, F_t in x and y at both faces), 18 operator/gradient flops in the compute
     # type and 19 FP64 flops of the S2O4 combination; stage 2 evaluates 4 fluxes,
@@ -156,7 +158,7 @@ def step_counts(case, state, dt, precision=0, nsample=4000, seed=0):
         upd1 = comb((cflux, 32), (glue(4 * 18, 4 * 19 + 6), 1))
         upd2 = comb((cflux, 16), (glue(4 * 9, 4 * 8 + 6), 1))
     # per node pair per step: 2 points + 2 nodes + 2 updates in each stage
-    pair = comb((point1, 2), (point2, 2), (node, 4), (upd1, 2), (upd2, 2))
+    pair = comb((point1, 2), (point2, 2), (node, 2), (node2, 2), (upd1, 2), (upd2, 2))
     per_node = {p: {k: pair[p][k] / 2.0 for k in KINDS} for p in ("fp64", "fp32")}
     return {
         "per_node_update": per_node,
@@ -164,6 +166,7 @@ def step_counts(case, state, dt, precision=0, nsample=4000, seed=0):
         "point_stage1": {p: _total(point1[p]) for p in point1},
         "point_stage2": {p: _total(point2[p]) for p in point2},
         "node": {p: _total(node[p]) for p in node},
+        "node_stage2": {p: _total(node2[p]) for p in node2},
         "update_stage1": {p: _total(upd1[p]) for p in upd1},
         "update_stage2": {p: _total(upd2[p]) for p in upd2},
         "units": {"recon_interface": rec_i, "recon_node": rec_n, "iface_solve": solve, "nodal_flux": nodal,
