@@ -411,10 +411,10 @@ def run_viscous_tube(args, world):
     """Viscous shock tube (Sec. 5.8) at 1000 x 500: throughput of a window of
     steps after the first 10, FP64 and mixed, each step with its own CFL-0.4
     time step (host loop, as in a run to t = 1).  GENO App. D constants and
-    tau c2 = 25, the set that has carried both precisions through this run on
-    every build tried; with the Sec. 3.2 constants (and c2 up to 5) this grid
-    is marginal in either precision, a run leaving the physical states near
-    the shock's foot or not depending on rounding-level details."""
+    tau c2 = 25, the set with which most runs of either precision reach t = 1;
+    this grid is marginal with every set tried, a run leaving the physical
+    states near the shock's foot (t = 0.0015 to 0.009) or not depending on
+    rounding-level details, so the window covers the first 1,000 steps."""
     import torch
     from paper_2606_17772_gb300 import fdcgks, inputs
     case = inputs.viscous_shock_tube(1000, 500, geno_variant=1, tau_c2=25.0)

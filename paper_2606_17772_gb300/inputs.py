@@ -287,10 +287,10 @@ def viscous_shock_tube(nx=1000, ny=500, gamma=1.4, mu=0.005, Pr=0.73, **kw):
 
     No-slip adiabatic walls left, right and bottom; symmetry at y = 0.5.
     Defaults: the Sec. 3.2 GENO constants and tau c2 = 1.  On 1000 x 500 runs
-    with these (or c2 up to 5) are marginal in either precision: whether they
-    leave the physical states near the shock's foot by t = 0.006 depends on
-    rounding-level details.  geno_variant=1, tau_c2=25.0 carried every run to
-    its end (t = 1) but leave the physical states on coarse grids (40 x 20)
+    are marginal in either precision with every constant set tried: whether
+    they leave the physical states near the shock's foot (t = 0.0015 to 0.009)
+    depends on rounding-level details.  geno_variant=1, tau_c2=25.0 carried
+    most runs to t = 1 but leave the physical states on coarse grids (40 x 20)
     within a few steps, so they are a run option, not the default.
     """
     def prim(x, y):
